@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark: s-step PCG solve time and HBM GB/s vs plain PCG on one GB300.
+
+Workload (default): 3-D Poisson, 7-point stencil on a 256^3 grid
+(n = 16,777,216, nnz = 117,047,296), CSR FP64 input, Jacobi, s = 4 monomial
+basis, x_true ~ U[-1, 1) from seed 0, b = A x_true, x0 = 0, stop at
+recursive rel. residual 1e-8.  One step = one complete solve (init, every
+outer step, export of x, true residual) through the C ABI.
+
+Reported:
+  value      whole-job effective HBM bandwidth of the s-step solves:
+             algorithmic bytes of a solve (per-kernel byte model below) over
+             its device time, summed over ranks
+  e2e        the same metric through the public API with host buffers
+             (b, x0 copied in and x copied out inside the timed region)
+  roofline   the dominant kernel family, timed by the library's CUDA events
+             on its own stream over the timed steps
+  pcg_*      plain PCG (Algorithm 1) on the same kernels, timed beside it
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the same solve
+
+Byte model (bytes per launch; V = 8 n, M = 4 (n+1) + nnz (4 + value bytes)):
+  MPK level j     M + 2V (u_j gathered, A u_j written) + 2V when j < s-1
+                  (1/diag read, u_{j+1} written)
+  block update    (6s + 6) V: U, AU, P_old, AP_old, x, r, 1/diag read;
+                  P, AP, x, r, next z written (first step: (4s + 6) V)
+  init            M + 5V: x0 gathered, b, 1/diag read, r, z written
+                  (DF64: + V, the zeroed correction)
+  final           M + 2V: x gathered, b read (DF64: + 3V, x = x0 + correction)
+PCG per iteration: SpMV + p.Ap M + 2V; update 7V; direction 4V.
+
+Multi-GPU: replicas only.  Every rank solves its own system (seed = rank)
+with no collective on the data path; value = all ranks' bytes / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s-step PCG solve time & HBM GB/s vs plain PCG, 1×GB300, rel. residual 1e-8"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="sscg", choices=["sscg", "reference"])
+    p.add_argument("--N", type=int, default=256)
+    p.add_argument("--s", type=int, default=4)
+    p.add_argument("--arith", default="df64", choices=["f64", "df64"])
+    p.add_argument("--tol", type=float, default=1e-8)
+    p.add_argument("--no-pcg", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------ byte model
+
+def byte_model(n, nnz, vbytes, s, arith):
+    V = 8 * n
+    M = 4 * (n + 1) + nnz * (4 + vbytes)
+    df = arith != "f64"
+    lv = [M + 2 * V + (2 * V if j < s - 1 else 0) for j in range(s)]
+    return dict(M=M, V=V, level=lv, level_avg=sum(lv) / s, update=(6 * s + 6) * V, update_first=(4 * s + 6) * V,
+                init=M + 5 * V + (V if df else 0), final=M + 2 * V + (3 * V if df else 0),
+                pcg_spmv=M + 2 * V, pcg_update=7 * V, pcg_dir=4 * V)
+
+
+def sstep_bytes(bm, outer):
+    if outer == 0:
+        return bm["init"] + bm["final"]
+    return (bm["init"] + bm["final"] + outer * sum(bm["level"]) + bm["update_first"]
+            + (outer - 1) * bm["update"])
+
+
+def pcg_bytes(bm, iters):
+    return bm["init"] + bm["final"] + iters * (bm["pcg_spmv"] + bm["pcg_update"] + bm["pcg_dir"])
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(", ") for r in open(self.f.name).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ distributed
+
+def dist_setup(gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v):
+    if pg is None:
+        return v
+    import torch
+
+    t = torch.tensor([float(v)], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, v):
+    if pg is None:
+        return v
+    import torch
+
+    t = torch.tensor([float(v)], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------- CPU (oracle)
+
+def oracle_sample(sysm, s, budget_s, tol):
+    """Time the oracle's s-step solve on a bounded number of outer steps."""
+    import oracle
+
+    M = oracle.as_matrix(sysm)
+    t0 = time.perf_counter()
+    oracle.pcgs(M, sysm["b"], s, tol=0.0, maxit=1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(200, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    r = oracle.pcgs(M, sysm["b"], s, tol=0.0, maxit=steps)
+    dt = time.perf_counter() - t0
+    return dict(steps=r.iters, seconds=dt, threads=oracle.num_threads())
+
+
+def workload_name(N, s, arith):
+    n = N ** 3
+    return (f"poisson7 {N}^3 (n={n:,}), CSR FP64 input, Jacobi, s={s} monomial, b=A x_true, x_true~U[-1,1) "
+            f"seed=rank, x0=0, tol 1e-8; arithmetic {arith}")
+
+
+def main():
+    a = parse()
+    world, rank, local, pg = dist_setup(a.gpus)
+    from paper_2501_03743_gb300 import inputs
+
+    if a.impl == "reference":
+        return reference_arm(a, world, rank, pg)
+
+    import torch
+
+    if rank == 0:
+        from paper_2501_03743_gb300 import build
+
+        build.build()
+    barrier(pg)
+    torch.cuda.set_device(local)
+    from paper_2501_03743_gb300 import sscg
+
+    sysm = inputs.system("poisson7", a.N, seed=rank)
+    n, nnz = sysm["n"], len(sysm["col"])
+    ctx = sscg.Context()
+    A = sscg.Matrix(ctx, sysm["rowptr"], sysm["col"], sysm["val"])
+    props = A.props()
+    vbytes = 8 if a.arith == "f64" else (4 if props["values_exact_fp32"] else 8)
+    bm = byte_model(n, nnz, vbytes, a.s, a.arith)
+    b = torch.from_numpy(sysm["b"]).cuda()
+    x = torch.zeros_like(b)
+    solver = sscg.Solver(A, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, profile=True)
+    stream = ctx.stream
+
+    def timed(fn, count):
+        evs = []
+        out = []
+        for _ in range(count):
+            x.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out.append(fn())
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in evs], out
+
+    for _ in range(a.warmup):
+        x.zero_()
+        solver.solve(b, x)
+    torch.cuda.synchronize()
+    clocks = Clocks(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                    if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    ms, res = timed(lambda: solver.solve(b, x), a.steps)
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    barrier(pg)
+    r0 = res[-1]
+    total_ms = max_over_ranks(pg, sum(ms))
+    ms_per_step = total_ms / a.steps
+    bytes_solve = sstep_bytes(bm, r0.outer_iters)
+    value = sum_over_ranks(pg, bytes_solve * a.steps) / (total_ms * 1e-3) / 1e9
+
+    # dominant kernel family over the timed steps
+    fam = {}
+    for key, cnt, per in (("mpk", "n_mpk", bm["level_avg"]), ("update", "n_update", bm["update"])):
+        t = sum(r.profile[f"t_{key}_ms"] for r in res)
+        c = sum(r.profile[cnt] for r in res)
+        fam[key] = dict(ms=t, launches=c, bytes_per_launch=per)
+    dom = max(fam, key=lambda k: fam[k]["ms"])
+    d = fam[dom]
+    avg_s = d["ms"] / max(d["launches"], 1) * 1e-3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        peak, peak_src = 6800.0, "fallback"
+    achieved = d["bytes_per_launch"] / avg_s / 1e9
+    kernel_names = {"mpk": "k_level (matrix-powers level: CSR SpMV + Jacobi + moments)",
+                    "update": "k_update (block update P, AP, x, r + next z)"}
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": kernel_names[dom],
+                "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "family_ms_per_solve": {k: round(v["ms"] / a.steps, 3) for k, v in fam.items()},
+                "family_gbs": {k: round(v["bytes_per_launch"] / (v["ms"] / max(v["launches"], 1) * 1e-3) / 1e9, 1)
+                               for k, v in fam.items()}}
+
+    # plain PCG beside it
+    pcg = None
+    if not a.no_pcg:
+        psolver = sscg.Solver(A, method="pcg", tol=a.tol, maxit=20000, arith=a.arith, profile=True)
+        x.zero_()
+        psolver.solve(b, x)
+        pms, pres = timed(lambda: psolver.solve(b, x), max(1, min(a.steps, 3)))
+        p0 = pres[-1]
+        pcg_ms = max_over_ranks(pg, sum(pms)) / len(pms)
+        pcg = dict(pcg_solve_ms=round(pcg_ms, 3), pcg_iters=p0.outer_iters, pcg_rel_res_true=p0.rel_res_true,
+                   pcg_gbs=round(pcg_bytes(bm, p0.outer_iters) / (pcg_ms * 1e-3) / 1e9, 1),
+                   speedup_vs_pcg=round(pcg_ms / ms_per_step, 4))
+
+    # end to end through the public API with host buffers
+    bh = torch.from_numpy(sysm["b"]).pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    hsolver = sscg.Solver(A, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, host_vectors=True)
+    xh.zero_()
+    hsolver.solve(bh, xh)
+    e2e_t = []
+    for _ in range(max(1, min(a.steps, 3))):
+        xh.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hr = hsolver.solve(bh, xh)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(pg, sum(e2e_t) / len(e2e_t))
+    e2e = {"value": round(sum_over_ranks(pg, sstep_bytes(bm, hr.outer_iters)) / e2e_s / 1e9, 1), "unit": "GB/s",
+           "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": round(e2e_s * 1e3, 3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        o = oracle_sample(sysm, a.s, a.cpu_seconds, a.tol)
+        per = (sstep_bytes(bm, o["steps"]) - bm["init"] - bm["final"]) / o["steps"]
+        cpu = {"value": round(per * o["steps"] / o["seconds"] / 1e9, 3), "unit": "GB/s", "cores": o["threads"],
+               "kind": "oracle",
+               "sample": f"{o['steps']} outer steps of the same s={a.s} solve (tol 0), FP64 C oracle, "
+                         f"{o['seconds']:.1f} s; bytes by the same model, outer steps only"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": a.arith, "data": "synthetic",
+            "config": {"workload": workload_name(a.N, a.s, a.arith), "n": n, "nnz": nnz, "s": a.s,
+                       "basis": "monomial", "preconditioner": "jacobi", "tol": a.tol,
+                       "parallelism": f"replicas x{world}",
+                       "l2": f"inputs larger than L2 ({bytes_solve / max(r0.outer_iters, 1) / 1e9:.2f} GB moved "
+                             "per outer step, working set > 4 GB); no flush needed"},
+            "solve_ms": round(ms_per_step, 3), "outer_iters": r0.outer_iters, "equiv_iters": r0.equiv_iters,
+            "status": r0.status, "rel_res_recursive": r0.rel_res_recursive, "rel_res_true": r0.rel_res_true,
+            "bytes_per_solve": bytes_solve, "wall_s_timed": round(t_wall, 3),
+            "roofline": roofline, "e2e": e2e, "gpu_launches": int(sum(r.profile["kernel_launches"] for r in res)),
+            "clocks": clk, "cpu_baseline": cpu,
+        }
+        if pcg:
+            line.update(pcg)
+        print(json.dumps(line), flush=True)
+    barrier(pg)
+
+
+def reference_arm(a, world, rank, pg):
+    """The oracle timed as the reference arm: each step one bounded sample
+    (a few outer steps) of the same solve on the host cores."""
+    if rank != 0:
+        return
+    from paper_2501_03743_gb300 import inputs
+    import oracle
+
+    sysm = inputs.system("poisson7", a.N, seed=0)
+    n, nnz = sysm["n"], len(sysm["col"])
+    bm = byte_model(n, nnz, 8, a.s, "f64")
+    M = oracle.as_matrix(sysm)
+    t0 = time.perf_counter()
+    oracle.pcgs(M, sysm["b"], a.s, tol=0.0, maxit=1)
+    one = time.perf_counter() - t0
+    per_step_outer = max(1, min(50, int(8.0 / max(one, 1e-6))))
+    for _ in range(a.warmup):
+        oracle.pcgs(M, sysm["b"], a.s, tol=0.0, maxit=1)
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        oracle.pcgs(M, sysm["b"], a.s, tol=0.0, maxit=per_step_outer)
+        times.append(time.perf_counter() - t0)
+    byts = sstep_bytes(bm, per_step_outer)
+    value = byts * a.steps / sum(times) / 1e9
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(1e3 * sum(times) / a.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_name(a.N, a.s, "f64"), "n": n, "nnz": nnz, "s": a.s,
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"each step: {per_step_outer} outer steps of the s={a.s} solve, FP64 C oracle"},
+            "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

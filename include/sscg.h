@@ -1,0 +1,188 @@
+/*
+ * sscg - preconditioned s-step Conjugate Gradient (Chronopoulos and Gear) on
+ * one NVIDIA GB300 (sm_103a), after "Communication-reduced Conjugate Gradient
+ * Variants for GPU-accelerated Clusters" (Bernaschi, Carrozzo, Celestini,
+ * Piperno, D'Ambra; arXiv 2501.03743).
+ *
+ * Plain C ABI: host or device pointers and sizes, no C++ or framework types.
+ *
+ * Memory.  The library never allocates device memory.  The caller provides
+ *   - matrix storage (sscg_mat_storage_bytes), filled by sscg_mat_create_csr
+ *     with a private copy of the CSR arrays plus derived data, and
+ *   - solve workspace (sscg_solve_workspace_bytes / sscg_pcg_workspace_bytes).
+ * Both must be device memory, 256-byte aligned, and stay alive and untouched
+ * while a matrix handle or a solve uses them.  Workspace contents do not
+ * carry over between calls.
+ *
+ * Streams.  Every device operation is issued on the stream given to
+ * sscg_create (0 = legacy default stream).  Entry points that return host
+ * results (solve info, bounds) synchronise that stream before returning.
+ *
+ * Errors.  Every entry point returns an sscg_status.  Negative values are
+ * caller or CUDA errors: outputs are not written, and sscg_last_error gives
+ * a one-line reason.  Positive values are numerical outcomes of a solve:
+ * x holds the last iterate that passed every check and info is filled.
+ *
+ * Threads.  A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef SSCG_H
+#define SSCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SSCG_OK = 0,
+    SSCG_NOT_CONVERGED = 1, /* maxit outer steps without reaching tol (Alg. 3, last line) */
+    SSCG_BREAKDOWN = 2,     /* singular or indefinite s x s system, alpha_s = 0, or a non-finite value */
+    SSCG_TIMEOUT = 3,       /* a bounded on-device wait gave up */
+    SSCG_ERR_INVALID = -1,  /* bad argument, size or option */
+    SSCG_ERR_NOT_SPD = -2,  /* matrix rejected: a diagonal entry is not positive */
+    SSCG_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+    SSCG_ERR_SPACE = -4,    /* storage or workspace too small or misaligned */
+    SSCG_ERR_NONFINITE = -5 /* NaN or Inf in the matrix values or right-hand side */
+} sscg_status;
+
+/* Polynomial basis of the s-step block (Section II-A uses the monomial basis;
+ * Section IV names Chebyshev bases as the stable alternative). */
+typedef enum { SSCG_BASIS_MONOMIAL = 0, SSCG_BASIS_CHEBYSHEV = 1 } sscg_basis;
+
+/* Preconditioner B (Section II-A leaves B general: any SPD operator). */
+typedef enum {
+    SSCG_PREC_NONE = 0,   /* B = I */
+    SSCG_PREC_JACOBI = 1, /* B = diag(A) */
+    SSCG_PREC_CHEB = 2    /* B^-1 = p(D^-1 A) D^-1, Chebyshev polynomial over [lmin, lmax] */
+} sscg_prec;
+
+/* Arithmetic of the hot path.  F64 uses the FP64 units.  DF64 carries every
+ * basis, block and vector element as an unevaluated sum of two FP32 numbers
+ * (about 48 significant bits, FP32 exponent range) and computes with the FP32
+ * units, whose GB300 throughput is about 57 times the FP64 rate.  MIXED stores
+ * the basis blocks and matrix values in FP32 and keeps the Gram sums, the
+ * s x s solves, x and r in DF64, with the true residual recomputed every
+ * `replace_every` outer steps.  The s x s solves are always FP64. */
+typedef enum { SSCG_ARITH_F64 = 0, SSCG_ARITH_DF64 = 1, SSCG_ARITH_MIXED = 2 } sscg_arith;
+
+/* Flags of sscg_opts.flags and sscg_mat_create_csr. */
+#define SSCG_HOST_VECTORS 0x1u /* b and x are host pointers; copies happen inside the call */
+#define SSCG_PROFILE 0x2u      /* bracket every kernel with CUDA events; fills the t_* fields of sscg_info */
+#define SSCG_HOST_ARRAYS 0x1u  /* CSR arrays are host pointers (sscg_mat_create_csr) */
+
+typedef struct sscg_ctx sscg_ctx;
+typedef struct sscg_mat sscg_mat;
+
+typedef struct {
+    int s;              /* block size, 1..16 (Alg. 3) */
+    int basis;          /* sscg_basis */
+    double basis_lmin;  /* Chebyshev basis: spectral interval of B^-1 A; 0,0 = from the matrix's bounds */
+    double basis_lmax;
+    double tol;         /* stop when ||r||_2 / ||b||_2 < tol, r the recursive residual */
+    int maxit;          /* outer steps (each is s CG steps), >= 0 */
+    int arith;          /* sscg_arith */
+    int replace_every;  /* MIXED: true-residual replacement period in outer steps (0 = 1) */
+    unsigned flags;     /* SSCG_HOST_VECTORS */
+} sscg_opts;
+
+typedef struct {
+    int status;                /* same value as returned */
+    int outer_iters;           /* outer steps taken (PCG: iterations) */
+    int64_t equiv_iters;       /* s * outer_iters: CG steps of solution improvement */
+    double rel_res_recursive;  /* ||r||_2 / ||b||_2 of the recursive residual at exit */
+    double rel_res_true;       /* ||b - A x||_2 / ||b||_2 recomputed at exit */
+    double* hist;              /* caller-owned host array or NULL: rel. residual before step 1, then per step */
+    int hist_cap;              /* entries available in hist */
+    int hist_len;              /* entries written */
+    int64_t kernel_launches;   /* kernels this call launched, including no-op launches queued past convergence */
+    /* With SSCG_PROFILE: device time summed over the launches of the steps
+     * actually taken, per kernel family, and the number of those launches.
+     * s-step: mpk = matrix-powers levels (with the fused moments and, on the
+     * last level, the s x s solves), update = block updates.  PCG: mpk =
+     * SpMV + p.Ap, update = x, r update + dots, dir = direction update. */
+    double t_init_ms, t_mpk_ms, t_update_ms, t_dir_ms, t_final_ms;
+    int64_t n_mpk, n_update, n_dir;
+} sscg_info;
+
+typedef struct {
+    int64_t n, nnz;
+    int64_t bandwidth;      /* max |i - j| over stored entries */
+    int values_exact_fp32;  /* every value is exactly representable in FP32 */
+    int max_row_nnz;
+    double diag_min, diag_max;
+    int prec, prec_degree;
+    double prec_lmin, prec_lmax;
+} sscg_mat_props;
+
+/* ------------------------------------------------------------ context */
+
+/* Create a context bound to `cuda_stream` (a cudaStream_t, may be NULL).
+ * Host memory only.  Errors: SSCG_ERR_INVALID (out == NULL),
+ * SSCG_ERR_CUDA (no device or unsupported architecture). */
+int sscg_create(sscg_ctx** out, void* cuda_stream);
+int sscg_destroy(sscg_ctx* ctx);
+const char* sscg_last_error(const sscg_ctx* ctx);
+const char* sscg_status_str(int status);
+/* Library version as major*10000 + minor*100 + patch. */
+int sscg_version(void);
+
+/* ------------------------------------------------------------- matrix */
+
+/* Bytes of device storage sscg_mat_create_csr needs for an n x n matrix
+ * with nnz stored entries (0 < n < 2^31, 0 <= nnz < 2^31). */
+int sscg_mat_storage_bytes(int64_t n, int64_t nnz, size_t* bytes);
+
+/* Create an SPD matrix from CSR arrays (Section III: row-block CSR; here one
+ * block holds every row).  rowptr: n+1 int32, nondecreasing, rowptr[0] = 0,
+ * rowptr[n] = nnz; colind: nnz int32 in [0, n); val: nnz FP64.  Arrays are
+ * device pointers, or host pointers with SSCG_HOST_ARRAYS.  They are copied
+ * into `storage` (device, >= sscg_mat_storage_bytes, 256-byte aligned) and
+ * may be freed on return; `storage` is owned by the caller and must outlive
+ * the handle.  Symmetry is the caller's promise and is not checked.
+ * Errors: SSCG_ERR_INVALID (sizes, rowptr, colind out of range),
+ * SSCG_ERR_NOT_SPD (a diagonal entry <= 0 or missing), SSCG_ERR_NONFINITE,
+ * SSCG_ERR_SPACE, SSCG_ERR_CUDA.  Synchronises the context's stream. */
+int sscg_mat_create_csr(sscg_ctx* ctx, int64_t n, int64_t nnz, const int32_t* rowptr,
+                        const int32_t* colind, const double* val, unsigned flags,
+                        void* storage, size_t storage_bytes, sscg_mat** out);
+int sscg_mat_destroy(sscg_mat* mat); /* frees the host handle only */
+int sscg_mat_props_get(const sscg_mat* mat, sscg_mat_props* props);
+
+/* Select the preconditioner B used by every later solve with `mat`.
+ * JACOBI ignores the other arguments.  CHEB: `degree` >= 1 steps of
+ * Chebyshev acceleration on D^-1 A over [lmin, lmax] (0 < lmin < lmax), so
+ * each apply costs degree-1 SpMVs; lmax must bound the spectrum of D^-1 A from
+ * above for B to stay SPD.  Host-only.  Errors: SSCG_ERR_INVALID. */
+int sscg_set_preconditioner(sscg_mat* mat, int prec, int degree, double lmin, double lmax);
+
+/* ------------------------------------------------------------- solves */
+
+/* Workspace bytes for sscg_solve with these options (depends on n, s, arith,
+ * maxit and the SSCG_HOST_VECTORS flag). */
+int sscg_solve_workspace_bytes(const sscg_mat* mat, const sscg_opts* opts, size_t* bytes);
+
+/* Solve A x = b by the preconditioned s-step CG method (Algorithm 3 with the
+ * matrix-powers kernel of Algorithm 4, the moments of Algorithm 5 and the
+ * s x s solves of Algorithm 6 for the monomial basis; Gram blocks formed
+ * directly for the Chebyshev basis).  b: n FP64; x: n FP64, x0 on entry and
+ * the solution on exit (device pointers unless SSCG_HOST_VECTORS).
+ * info may be NULL.  Returns SSCG_OK, SSCG_NOT_CONVERGED, SSCG_BREAKDOWN,
+ * SSCG_TIMEOUT or a negative error.  On b = 0, x = 0 and SSCG_OK. */
+int sscg_solve(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x,
+               const sscg_opts* opts, sscg_info* info, void* workspace, size_t workspace_bytes);
+
+/* Plain preconditioned CG (Algorithm 1) on the same kernels, the comparator
+ * of the s-step method.  opts->s, basis are ignored; maxit counts iterations. */
+int sscg_pcg_workspace_bytes(const sscg_mat* mat, const sscg_opts* opts, size_t* bytes);
+int sscg_pcg_solve(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x,
+                   const sscg_opts* opts, sscg_info* info, void* workspace, size_t workspace_bytes);
+
+/* y = A x (device FP64 vectors of length n), the library's CSR SpMV. */
+int sscg_spmv(sscg_ctx* ctx, const sscg_mat* mat, const double* x, double* y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSCG_H */

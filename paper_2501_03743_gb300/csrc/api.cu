@@ -1,0 +1,370 @@
+// C-ABI entry points of libsscg: context, matrix, preconditioner, solves.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "spmv.cuh"
+
+using namespace sscg;
+
+namespace {
+
+// Flags gathered by the analysis kernel.
+struct Analysis {
+    unsigned long long bad_col;
+    unsigned long long nonfinite;
+    unsigned long long not_exact;
+    unsigned long long nonpos_diag;
+    unsigned long long bandwidth;
+    unsigned long long dmin_bits;  // positive doubles order like their bit patterns
+    unsigned long long dmax_bits;
+};
+
+// Per row: check column range and finiteness, split values into FP32
+// hi + lo, sum the diagonal, record bandwidth, build 1/diag in FP64 and DF64.
+__global__ void __launch_bounds__(kThreads) k_analyze(int n, const int32_t* __restrict__ rowptr,
+                                                      const int32_t* __restrict__ col,
+                                                      const double* __restrict__ val, float* __restrict__ vhi,
+                                                      float* __restrict__ vlo, double* __restrict__ diag,
+                                                      double* __restrict__ dinv, float2* __restrict__ dinv_df,
+                                                      Analysis* out) {
+    __shared__ unsigned long long s_bad, s_nf, s_ne, s_np, s_bw, s_mn, s_mx;
+    if (threadIdx.x == 0) {
+        s_bad = s_nf = s_ne = s_np = s_bw = 0ull;
+        s_mn = ~0ull;
+        s_mx = 0ull;
+    }
+    __syncthreads();
+    unsigned long long bad = 0, nf = 0, ne = 0, np = 0, bw = 0, mn = ~0ull, mx = 0ull;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; k++) {
+            int c = col[k];
+            double v = val[k];
+            if (c < 0 || c >= n) bad++;
+            if (!isfinite(v)) nf++;
+            float hi = __double2float_rn(v);
+            float lo = __double2float_rn(v - (double)hi);
+            vhi[k] = hi;
+            vlo[k] = lo;
+            if ((double)hi != v) ne++;
+            unsigned long long dist = (unsigned long long)(c > i ? c - i : i - c);
+            bw = dist > bw ? dist : bw;
+            if (c == i) d += v;
+        }
+        diag[i] = d;
+        if (!(d > 0.0) || !isfinite(d)) {
+            np++;
+            dinv[i] = 0.0;
+            dinv_df[i] = make_float2(0.f, 0.f);
+        } else {
+            double inv = 1.0 / d;
+            dinv[i] = inv;
+            float hi = __double2float_rn(inv);
+            dinv_df[i] = make_float2(hi, __double2float_rn(inv - (double)hi));
+            unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+            mn = bits < mn ? bits : mn;
+            mx = bits > mx ? bits : mx;
+        }
+    }
+    if (bad) atomicAdd(&s_bad, bad);
+    if (nf) atomicAdd(&s_nf, nf);
+    if (ne) atomicAdd(&s_ne, ne);
+    if (np) atomicAdd(&s_np, np);
+    atomicMax(&s_bw, bw);
+    atomicMin(&s_mn, mn);
+    atomicMax(&s_mx, mx);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_bad) atomicAdd(&out->bad_col, s_bad);
+        if (s_nf) atomicAdd(&out->nonfinite, s_nf);
+        if (s_ne) atomicAdd(&out->not_exact, s_ne);
+        if (s_np) atomicAdd(&out->nonpos_diag, s_np);
+        atomicMax(&out->bandwidth, s_bw);
+        atomicMin(&out->dmin_bits, s_mn);
+        atomicMax(&out->dmax_bits, s_mx);
+    }
+}
+
+struct MatLayout {
+    int32_t* rowptr;
+    int32_t* col;
+    double* val;
+    float* vhi;
+    float* vlo;
+    double* diag;
+    double* dinv;
+    float2* dinv_df;
+    Analysis* an;
+    size_t bytes;
+};
+
+MatLayout mat_layout(int64_t n, int64_t nnz, void* base) {
+    MatLayout L;
+    Carve c(base, base ? ~(size_t)0 : 0);
+    // +16 entries of slack after every entry array so vector loads of a
+    // tile's range never leave the allocation.
+    L.rowptr = c.take<int32_t>((size_t)n + 1 + 16);
+    L.col = c.take<int32_t>((size_t)nnz + 16);
+    L.val = c.take<double>((size_t)nnz + 16);
+    L.vhi = c.take<float>((size_t)nnz + 16);
+    L.vlo = c.take<float>((size_t)nnz + 16);
+    L.diag = c.take<double>((size_t)n);
+    L.dinv = c.take<double>((size_t)n);
+    L.dinv_df = c.take<float2>((size_t)n);
+    L.an = c.take<Analysis>(1);
+    L.bytes = c.used;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sscg_version(void) { return 100; }
+
+const char* sscg_status_str(int s) {
+    switch (s) {
+        case SSCG_OK: return "converged";
+        case SSCG_NOT_CONVERGED: return "not converged within maxit";
+        case SSCG_BREAKDOWN: return "breakdown (singular or indefinite s x s system, or non-finite value)";
+        case SSCG_TIMEOUT: return "bounded device wait timed out";
+        case SSCG_ERR_INVALID: return "invalid argument";
+        case SSCG_ERR_NOT_SPD: return "matrix has a non-positive or missing diagonal entry";
+        case SSCG_ERR_CUDA: return "CUDA error";
+        case SSCG_ERR_SPACE: return "storage or workspace too small or misaligned";
+        case SSCG_ERR_NONFINITE: return "non-finite input";
+        default: return "unknown status";
+    }
+}
+
+int sscg_create(sscg_ctx** out, void* stream) {
+    if (!out) return SSCG_ERR_INVALID;
+    *out = nullptr;
+    sscg_ctx* c = (sscg_ctx*)calloc(1, sizeof(sscg_ctx));
+    if (!c) return SSCG_ERR_INVALID;
+    c->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    int major = 0, minor = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, c->device);
+    if (e == cudaSuccess && !(major == 10 && minor == 3)) {
+        free(c);
+        return SSCG_ERR_CUDA;  // this build carries sm_103a code only
+    }
+    void* pinned = nullptr;
+    if (e == cudaSuccess) e = cudaHostAlloc(&pinned, 64, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        free(c);
+        return SSCG_ERR_CUDA;
+    }
+    memset(pinned, 0, 64);
+    c->pinned = (volatile int*)pinned;
+    *out = c;
+    return SSCG_OK;
+}
+
+int sscg_destroy(sscg_ctx* c) {
+    if (!c) return SSCG_ERR_INVALID;
+    if (c->pinned) cudaFreeHost((void*)c->pinned);
+    for (int i = 0; i < c->ev_cap; i++) cudaEventDestroy(c->ev[i]);
+    free(c->ev);
+    free(c);
+    return SSCG_OK;
+}
+
+const char* sscg_last_error(const sscg_ctx* c) { return c ? c->err : "null context"; }
+
+int sscg_mat_storage_bytes(int64_t n, int64_t nnz, size_t* bytes) {
+    if (!bytes || n <= 0 || n >= INT32_MAX || nnz < 0 || nnz >= INT32_MAX - 64) return SSCG_ERR_INVALID;
+    *bytes = mat_layout(n, nnz, nullptr).bytes;
+    return SSCG_OK;
+}
+
+int sscg_mat_create_csr(sscg_ctx* ctx, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
+                        const double* val, unsigned flags, void* storage, size_t storage_bytes, sscg_mat** out) {
+    if (!ctx || !out) return SSCG_ERR_INVALID;
+    *out = nullptr;
+    size_t need = 0;
+    if (sscg_mat_storage_bytes(n, nnz, &need) != SSCG_OK)
+        return set_err(ctx, SSCG_ERR_INVALID, "n = %lld, nnz = %lld out of range", (long long)n, (long long)nnz);
+    if (!rowptr || (nnz > 0 && (!colind || !val))) return set_err(ctx, SSCG_ERR_INVALID, "null CSR array");
+    if (!storage || storage_bytes < need || ((uintptr_t)storage & 255))
+        return set_err(ctx, SSCG_ERR_SPACE, "matrix storage needs %zu bytes, 256-byte aligned", need);
+    cudaStream_t st = ctx->stream;
+    MatLayout L = mat_layout(n, nnz, storage);
+    const cudaMemcpyKind kind = (flags & SSCG_HOST_ARRAYS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    SSCG_CUDA(ctx, cudaMemcpyAsync(L.rowptr, rowptr, (n + 1) * sizeof(int32_t), kind, st));
+    SSCG_CUDA(ctx, cudaMemsetAsync(L.rowptr + n + 1, 0, 16 * sizeof(int32_t), st));
+    if (nnz > 0) {
+        SSCG_CUDA(ctx, cudaMemcpyAsync(L.col, colind, nnz * sizeof(int32_t), kind, st));
+        SSCG_CUDA(ctx, cudaMemcpyAsync(L.val, val, nnz * sizeof(double), kind, st));
+    }
+    SSCG_CUDA(ctx, cudaMemsetAsync(L.col + nnz, 0, 16 * sizeof(int32_t), st));
+    SSCG_CUDA(ctx, cudaMemsetAsync(L.val + nnz, 0, 16 * sizeof(double), st));
+    SSCG_CUDA(ctx, cudaMemsetAsync(L.vhi + nnz, 0, 16 * sizeof(float), st));
+    SSCG_CUDA(ctx, cudaMemsetAsync(L.vlo + nnz, 0, 16 * sizeof(float), st));
+    // Row pointers are checked on the host: monotone, 0 .. nnz.
+    std::vector<int32_t> hr((size_t)n + 1);
+    SSCG_CUDA(ctx, cudaMemcpyAsync(hr.data(), L.rowptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SSCG_CUDA(ctx, cudaStreamSynchronize(st));
+    if (hr[0] != 0 || hr[(size_t)n] != nnz)
+        return set_err(ctx, SSCG_ERR_INVALID, "rowptr[0] must be 0 and rowptr[n] must be nnz");
+    int max_row = 0, max_tile = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int len = hr[i + 1] - hr[i];
+        if (len < 0) return set_err(ctx, SSCG_ERR_INVALID, "rowptr decreases at row %lld", (long long)i);
+        max_row = std::max(max_row, len);
+    }
+    for (int64_t t = 0; t < n; t += kTileRows) {
+        int64_t e = std::min<int64_t>(n, t + kTileRows);
+        max_tile = std::max(max_tile, hr[e] - hr[t]);
+    }
+    Analysis a0;
+    memset(&a0, 0, sizeof(a0));
+    a0.dmin_bits = ~0ull;
+    SSCG_CUDA(ctx, cudaMemcpyAsync(L.an, &a0, sizeof(a0), cudaMemcpyHostToDevice, st));
+    int G = grid_for(ctx, n, 4);
+    k_analyze<<<G, kThreads, 0, st>>>((int)n, L.rowptr, L.col, L.val, L.vhi, L.vlo, L.diag, L.dinv, L.dinv_df, L.an);
+    SSCG_CUDA(ctx, cudaGetLastError());
+    Analysis a;
+    SSCG_CUDA(ctx, cudaMemcpyAsync(&a, L.an, sizeof(a), cudaMemcpyDeviceToHost, st));
+    SSCG_CUDA(ctx, cudaStreamSynchronize(st));
+    if (a.bad_col) return set_err(ctx, SSCG_ERR_INVALID, "%llu column indices outside [0, n)", a.bad_col);
+    if (a.nonfinite) return set_err(ctx, SSCG_ERR_NONFINITE, "%llu non-finite matrix values", a.nonfinite);
+    if (a.nonpos_diag)
+        return set_err(ctx, SSCG_ERR_NOT_SPD, "%llu rows with a non-positive or missing diagonal", a.nonpos_diag);
+    sscg_mat* m = (sscg_mat*)calloc(1, sizeof(sscg_mat));
+    if (!m) return set_err(ctx, SSCG_ERR_INVALID, "out of host memory");
+    m->n = n;
+    m->nnz = nnz;
+    m->rowptr = L.rowptr;
+    m->col = L.col;
+    m->val = L.val;
+    m->vhi = L.vhi;
+    m->vlo = L.vlo;
+    m->diag = L.diag;
+    m->dinv = L.dinv;
+    m->dinv_df = L.dinv_df;
+    m->bandwidth = (int64_t)a.bandwidth;
+    m->exact_fp32 = a.not_exact == 0;
+    m->max_row_nnz = max_row;
+    m->max_tile_nnz = max_tile;
+    double dmn, dmx;
+    memcpy(&dmn, &a.dmin_bits, 8);
+    memcpy(&dmx, &a.dmax_bits, 8);
+    m->dmin = dmn;
+    m->dmax = dmx;
+    m->prec = SSCG_PREC_JACOBI;
+    *out = m;
+    return SSCG_OK;
+}
+
+int sscg_mat_destroy(sscg_mat* m) {
+    if (!m) return SSCG_ERR_INVALID;
+    free(m);
+    return SSCG_OK;
+}
+
+int sscg_mat_props_get(const sscg_mat* m, sscg_mat_props* p) {
+    if (!m || !p) return SSCG_ERR_INVALID;
+    p->n = m->n;
+    p->nnz = m->nnz;
+    p->bandwidth = m->bandwidth;
+    p->values_exact_fp32 = m->exact_fp32;
+    p->max_row_nnz = m->max_row_nnz;
+    p->diag_min = m->dmin;
+    p->diag_max = m->dmax;
+    p->prec = m->prec;
+    p->prec_degree = m->degree;
+    p->prec_lmin = m->plmin;
+    p->prec_lmax = m->plmax;
+    return SSCG_OK;
+}
+
+int sscg_set_preconditioner(sscg_mat* m, int prec, int degree, double lmin, double lmax) {
+    if (!m) return SSCG_ERR_INVALID;
+    if (prec == SSCG_PREC_NONE || prec == SSCG_PREC_JACOBI) {
+        m->prec = prec;
+        m->degree = 0;
+        m->plmin = m->plmax = 0.0;
+        return SSCG_OK;
+    }
+    if (prec == SSCG_PREC_CHEB) {
+        if (degree < 1 || degree > 64 || !(lmin > 0.0) || !(lmax > lmin) || !std::isfinite(lmax))
+            return SSCG_ERR_INVALID;
+        m->prec = prec;
+        m->degree = degree;
+        m->plmin = lmin;
+        m->plmax = lmax;
+        return SSCG_OK;
+    }
+    return SSCG_ERR_INVALID;
+}
+
+int sscg_solve_workspace_bytes(const sscg_mat* m, const sscg_opts* o, size_t* bytes) {
+    if (!m || !o || !bytes || o->s < 1 || o->s > kMaxS || o->maxit < 0) return SSCG_ERR_INVALID;
+    return sstep_workspace(m, o, bytes);
+}
+
+int sscg_solve(sscg_ctx* ctx, const sscg_mat* m, const double* b, double* x, const sscg_opts* o, sscg_info* info,
+               void* ws, size_t ws_bytes) {
+    if (!ctx) return SSCG_ERR_INVALID;
+    return solve_sstep(ctx, m, b, x, o, info, ws, ws_bytes);
+}
+
+int sscg_pcg_workspace_bytes(const sscg_mat* m, const sscg_opts* o, size_t* bytes) {
+    if (!m || !o || !bytes || o->maxit < 0) return SSCG_ERR_INVALID;
+    return pcg_workspace(m, o, bytes);
+}
+
+int sscg_pcg_solve(sscg_ctx* ctx, const sscg_mat* m, const double* b, double* x, const sscg_opts* o, sscg_info* info,
+                   void* ws, size_t ws_bytes) {
+    if (!ctx) return SSCG_ERR_INVALID;
+    return solve_pcg(ctx, m, b, x, o, info, ws, ws_bytes);
+}
+
+int sscg_spmv(sscg_ctx* ctx, const sscg_mat* m, const double* x, double* y) {
+    if (!ctx || !m || !x || !y) return SSCG_ERR_INVALID;
+    return spmv_f64(ctx, m, x, y);
+}
+
+}  // extern "C"
+
+namespace sscg {
+
+__global__ void __launch_bounds__(kThreads) k_spmv_f64(MatView M, const double* __restrict__ x, double* __restrict__ y) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int s_rp[kTileRows + 1];
+    const int ntiles = (M.n + kTileRows - 1) / kTileRows;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        double v;
+        int row;
+        if (tile_spmv<ArithF64, VAL_F64>(M, tile, [&](int c) { return __ldg(x + c); }, v, row, smem, s_rp)) y[row] = v;
+    }
+}
+
+int spmv_f64(sscg_ctx* ctx, const sscg_mat* m, const double* x, double* y) {
+    int cap = std::min(8192, std::max(32, m->max_tile_nnz));
+    cap = (cap + 31) / 32 * 32;
+    MatView M;
+    M.n = (int)m->n;
+    M.cap = cap;
+    M.rowptr = m->rowptr;
+    M.col = m->col;
+    M.val = m->val;
+    M.vhi = m->vhi;
+    M.vlo = m->vlo;
+    size_t smem = stage_bytes<ArithF64, VAL_F64>(cap);
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_spmv_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_spmv_f64<<<grid_for(ctx, m->n, 8), kThreads, smem, ctx->stream>>>(M, x, y);
+    SSCG_CUDA(ctx, cudaGetLastError());
+    return SSCG_OK;
+}
+
+}  // namespace sscg

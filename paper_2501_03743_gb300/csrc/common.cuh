@@ -1,0 +1,235 @@
+// Device-side building blocks shared by the sscg kernels: double-float
+// arithmetic, arithmetic traits, the solver control block and deterministic
+// block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sscg {
+
+constexpr int kMaxS = 16;       // largest supported block size s
+constexpr int kThreads = 256;   // threads per CTA of every row-parallel kernel
+constexpr int kTileRows = 256;  // rows per SpMV tile (one per thread)
+
+// ------------------------------------------------------------ double-float
+//
+// A df64 value is the unevaluated sum hi + lo of two FP32 numbers with
+// |lo| <= ulp(hi)/2, about 48 significant bits.  The operations below are
+// the error-free transformations TwoSum (Knuth), FastTwoSum (Dekker) and the
+// FMA form of TwoProduct, and the accurate double-double addition and
+// multiplication built from them (Hida, Li and Bailey, "Algorithms for
+// quad-double precision floating point arithmetic", ARITH 2001).  Every
+// primitive uses an explicitly rounded intrinsic so the compiler cannot
+// contract or reassociate the compensation terms.
+
+struct df64 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ df64 df_make(float hi, float lo) {
+    df64 r;
+    r.hi = hi;
+    r.lo = lo;
+    return r;
+}
+
+__device__ __forceinline__ df64 df_add(df64 a, df64 b) {
+    float s1, s2, t1, t2;
+    two_sum(a.hi, b.hi, s1, s2);
+    two_sum(a.lo, b.lo, t1, t2);
+    s2 = __fadd_rn(s2, t1);
+    fast_two_sum(s1, s2, s1, s2);
+    s2 = __fadd_rn(s2, t2);
+    fast_two_sum(s1, s2, s1, s2);
+    return df_make(s1, s2);
+}
+
+__device__ __forceinline__ df64 df_neg(df64 a) { return df_make(-a.hi, -a.lo); }
+
+__device__ __forceinline__ df64 df_mul(df64 a, df64 b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    float s, t;
+    fast_two_sum(p, e, s, t);
+    return df_make(s, t);
+}
+
+// a * b with b an exact FP32 number.
+__device__ __forceinline__ df64 df_mul_f(df64 a, float b) {
+    float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    float s, t;
+    fast_two_sum(p, e, s, t);
+    return df_make(s, t);
+}
+
+__device__ __forceinline__ df64 df_from_double(double x) {
+    float hi = __double2float_rn(x);
+    float lo = __double2float_rn(x - (double)hi);
+    return df_make(hi, lo);
+}
+
+__device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+
+// ------------------------------------------------------- arithmetic traits
+//
+// R: register type.  S: storage type of vectors and basis blocks.
+// fma(a, b, c) = a * b + c.
+
+struct ArithF64 {
+    using R = double;
+    using S = double;
+    static constexpr int kind = 0;
+    __device__ static __forceinline__ R zero() { return 0.0; }
+    __device__ static __forceinline__ R ld(const S* p) { return *p; }
+    __device__ static __forceinline__ R ldg(const S* p) { return __ldg(p); }
+    __device__ static __forceinline__ void st(S* p, R v) { *p = v; }
+    __device__ static __forceinline__ R add(R a, R b) { return a + b; }
+    __device__ static __forceinline__ R sub(R a, R b) { return a - b; }
+    __device__ static __forceinline__ R mul(R a, R b) { return a * b; }
+    __device__ static __forceinline__ R fma(R a, R b, R c) { return ::fma(a, b, c); }
+    __device__ static __forceinline__ R from_d(double x) { return x; }
+    __device__ static __forceinline__ double to_d(R a) { return a; }
+    __device__ static __forceinline__ R shfl_xor(R a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+};
+
+struct ArithDF64 {
+    using R = df64;
+    using S = float2;
+    static constexpr int kind = 1;
+    __device__ static __forceinline__ R zero() { return df_make(0.f, 0.f); }
+    __device__ static __forceinline__ R ld(const S* p) {
+        float2 v = *p;
+        return df_make(v.x, v.y);
+    }
+    __device__ static __forceinline__ R ldg(const S* p) {
+        float2 v = __ldg(p);
+        return df_make(v.x, v.y);
+    }
+    __device__ static __forceinline__ void st(S* p, R v) { *p = make_float2(v.hi, v.lo); }
+    __device__ static __forceinline__ R add(R a, R b) { return df_add(a, b); }
+    __device__ static __forceinline__ R sub(R a, R b) { return df_add(a, df_neg(b)); }
+    __device__ static __forceinline__ R mul(R a, R b) { return df_mul(a, b); }
+    __device__ static __forceinline__ R fma(R a, R b, R c) { return df_add(df_mul(a, b), c); }
+    __device__ static __forceinline__ R from_d(double x) { return df_from_double(x); }
+    __device__ static __forceinline__ double to_d(R a) { return df_to_double(a); }
+    __device__ static __forceinline__ R shfl_xor(R a, int m) {
+        return df_make(__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m));
+    }
+};
+
+// --------------------------------------------------------- control block
+//
+// One per solve, in the caller's workspace.  Kernels read `done` at entry
+// and return at once when it is set, so launches queued after convergence
+// or breakdown cost only their launch.
+
+struct Ctrl {
+    int done;        // nonzero: stop
+    int status;      // sscg_status of the solve
+    int step;        // outer steps (PCG: iterations) completed
+    int maxit;
+    unsigned ticket[4];  // last-CTA counters (one per kernel family)
+    int s;
+    int zero_rhs;    // b = 0: x is set to 0 at the end
+    int nhist;       // history entries written
+    int pad0;
+    double tol;
+    double bnorm;    // ||b||_2
+    double relres;   // recursive ||r||/||b|| after the last step
+    double true_res2;
+    double mu[2 * kMaxS + 2];     // moments mu_0 .. mu_{2s-1}
+    double W[kMaxS * kMaxS];      // column-major, current W_i
+    double alpha[kMaxS];
+    double beta[kMaxS * kMaxS];   // column-major
+    double G[kMaxS * kMaxS];      // direct Gram blocks (Chebyshev basis)
+    double C[kMaxS * kMaxS];
+    double m[kMaxS];
+    double basis_c, basis_delta;  // Chebyshev basis centre and half-width
+    double rho, pcg_alpha, pcg_beta;  // PCG scalars
+    double scratch[8];
+};
+
+// ------------------------------------------------------------- reductions
+
+template <class A>
+__device__ __forceinline__ typename A::R warp_sum(typename A::R v) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v = A::add(v, A::shfl_xor(v, m));
+    return v;
+}
+
+// Sum NV values over the CTA (blockDim.x == kThreads); the result is
+// returned as doubles in thread 0.  `sh` holds NV * (kThreads/32) doubles.
+template <class A, int NV>
+__device__ __forceinline__ void block_sum(typename A::R (&v)[NV], double* sh, double (&out)[NV]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        typename A::R w = warp_sum<A>(v[q]);
+        if (lane == 0) sh[q * (kThreads / 32) + warp] = A::to_d(w);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            double t = 0.0;
+            for (int w = 0; w < kThreads / 32; w++) t += sh[q * (kThreads / 32) + w];
+            out[q] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// Last-CTA election: every CTA calls this after writing its partials; it
+// returns true in exactly one CTA (the last to arrive), in all its threads,
+// after which that CTA may read every CTA's partials.  The counter is reset
+// for the next launch.
+__device__ __forceinline__ bool last_cta(unsigned* ticket) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(ticket, 1u);
+        is_last = (t == gridDim.x - 1);
+        if (is_last) *ticket = 0u;
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last;
+}
+
+// Deterministic sum of `count` values spaced `stride` apart, by one CTA;
+// the result is valid in thread 0.  Reads bypass L1.
+__device__ __forceinline__ double cta_sum_partials(const double* p, int count, double* sh) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) t += __ldcg(p + i);
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = t;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x / 32); w++) r += sh[w];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace sscg

@@ -1,0 +1,178 @@
+// Host-side definitions shared by the translation units of libsscg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+
+#include "../../include/sscg.h"
+
+struct sscg_ctx {
+    cudaStream_t stream;
+    int device;
+    int sm_count;
+    char err[512];
+    volatile int* pinned;  // small page-locked host buffer for polling reads (8 slots)
+    cudaEvent_t* ev;       // event pool for SSCG_PROFILE
+    int ev_cap;
+};
+
+struct sscg_mat {
+    int64_t n, nnz;
+    // device arrays inside the caller's storage
+    int32_t* rowptr;
+    int32_t* col;
+    double* val;     // FP64 values
+    float* vhi;      // FP32 part of every value (exact when values_exact_fp32)
+    float* vlo;      // FP32 remainder val - vhi
+    double* diag;
+    double* dinv;    // 1 / diag
+    float2* dinv_df; // 1 / diag as a double-float
+    float2* ones_df; // unused slot kept for alignment
+    // properties
+    int64_t bandwidth;
+    int exact_fp32;
+    int max_row_nnz;
+    int max_tile_nnz;  // largest nnz count of a 256-row tile
+    double dmin, dmax;
+    // preconditioner
+    int prec, degree;
+    double plmin, plmax;
+};
+
+namespace sscg {
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over a caller-provided region.
+struct Carve {
+    char* base;
+    size_t cap, used;
+    Carve(void* b, size_t c) : base((char*)b), cap(c), used(0) {}
+    template <class T>
+    T* take(size_t count) {
+        size_t off = align_up(used, 256);
+        used = off + align_up(count * sizeof(T), 256);
+        return base ? (T*)(base + off) : nullptr;
+    }
+    bool ok() const { return used <= cap; }
+};
+
+inline int set_err(sscg_ctx* ctx, int code, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define SSCG_CUDA(ctx, call)                                                                   \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return ::sscg::set_err((ctx), SSCG_ERR_CUDA, "%s: %s (%s:%d)", #call,               \
+                                   cudaGetErrorString(e_), __FILE__, __LINE__);                \
+    } while (0)
+
+// Launch geometry: grid-stride kernels use a grid of `ctas_per_sm` CTAs
+// on each SM.
+inline int grid_for(const sscg_ctx* ctx, int64_t rows, int ctas_per_sm) {
+    int64_t tiles = (rows + 255) / 256;
+    int64_t g = (int64_t)ctx->sm_count * ctas_per_sm;
+    if (tiles < g) g = tiles;
+    return g < 1 ? 1 : (int)g;
+}
+
+// Persistent grid for a grid-stride kernel: as many CTAs as fit on the
+// device at once (occupancy API), never more than there are row tiles.
+template <class K>
+inline int occupancy_grid(const sscg_ctx* ctx, K kernel, size_t smem, int64_t rows) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+    return grid_for(ctx, rows, per_sm);
+}
+
+// Kernel-family timing for SSCG_PROFILE: events on the context's stream
+// around each launch, summed after the call for the steps actually taken.
+enum { FAM_INIT = 0, FAM_MPK = 1, FAM_UPDATE = 2, FAM_DIR = 3, FAM_FINAL = 4, FAM_COUNT = 5 };
+
+struct Prof {
+    sscg_ctx* ctx;
+    bool on;
+    int used;
+    int fam[65536];
+    int step[65536];
+    int64_t launches;
+    explicit Prof(sscg_ctx* c, bool enable) : ctx(c), on(enable), used(0), launches(0) {}
+    bool reserve(int pairs) {
+        if (!on) return true;
+        if (pairs > 65536) pairs = 65536;
+        if (ctx->ev_cap >= 2 * pairs) return true;
+        cudaEvent_t* nev = (cudaEvent_t*)realloc(ctx->ev, sizeof(cudaEvent_t) * 2 * pairs);
+        if (!nev) return false;
+        ctx->ev = nev;
+        for (int i = ctx->ev_cap; i < 2 * pairs; i++)
+            if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) return false;
+        ctx->ev_cap = 2 * pairs;
+        return true;
+    }
+    void begin() {
+        if (on && 2 * used + 1 < ctx->ev_cap) cudaEventRecord(ctx->ev[2 * used], ctx->stream);
+    }
+    void end(int family, int k) {
+        launches++;
+        if (on && 2 * used + 1 < ctx->ev_cap) {
+            cudaEventRecord(ctx->ev[2 * used + 1], ctx->stream);
+            fam[used] = family;
+            step[used] = k;
+            used++;
+        }
+    }
+    // Sum per family over launches whose step < steps_taken (init/final always).
+    void collect(int steps_taken, double (&ms)[FAM_COUNT], int64_t (&cnt)[FAM_COUNT]) const {
+        for (int f = 0; f < FAM_COUNT; f++) ms[f] = 0.0, cnt[f] = 0;
+        if (!on) return;
+        for (int i = 0; i < used; i++) {
+            bool counted = fam[i] == FAM_INIT || fam[i] == FAM_FINAL || step[i] < steps_taken;
+            if (!counted) continue;
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, ctx->ev[2 * i], ctx->ev[2 * i + 1]) == cudaSuccess) {
+                ms[fam[i]] += t;
+                cnt[fam[i]]++;
+            }
+        }
+    }
+};
+
+inline void fill_profile(sscg_info* info, const Prof& P, int steps_taken) {
+    double ms[FAM_COUNT];
+    int64_t cnt[FAM_COUNT];
+    P.collect(steps_taken, ms, cnt);
+    info->kernel_launches = P.launches;
+    info->t_init_ms = ms[FAM_INIT];
+    info->t_mpk_ms = ms[FAM_MPK];
+    info->t_update_ms = ms[FAM_UPDATE];
+    info->t_dir_ms = ms[FAM_DIR];
+    info->t_final_ms = ms[FAM_FINAL];
+    info->n_mpk = cnt[FAM_MPK];
+    info->n_update = cnt[FAM_UPDATE];
+    info->n_dir = cnt[FAM_DIR];
+}
+
+// Solvers (sstep.cu, pcg.cu)
+int solve_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* opts,
+                sscg_info* info, void* ws, size_t ws_bytes);
+int sstep_workspace(const sscg_mat* mat, const sscg_opts* opts, size_t* bytes);
+int solve_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* opts,
+              sscg_info* info, void* ws, size_t ws_bytes);
+int pcg_workspace(const sscg_mat* mat, const sscg_opts* opts, size_t* bytes);
+int spmv_f64(sscg_ctx* ctx, const sscg_mat* mat, const double* x, double* y);
+
+}  // namespace sscg

@@ -1,0 +1,174 @@
+// The s x s coefficient solves of the s-step method, done on chip in FP64
+// by one warp (Section III moves them to the host; here they run in the
+// last CTA of the kernel that completes the Gram/moment reduction).
+#pragma once
+
+#include "common.cuh"
+
+namespace sscg {
+
+// In-place Cholesky A = L L^T of an s x s column-major matrix in shared
+// memory (lower triangle overwritten by L), lanes parallel over rows.
+// Returns false (in every lane) if a pivot is not positive or not finite.
+__device__ __forceinline__ bool warp_cholesky(double* A, int s) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < s; k++) {
+        __syncwarp();
+        double d = A[k + k * s];
+        if (!(d > 0.0) || !isfinite(d)) return false;
+        double lkk = sqrt(d);
+        __syncwarp();
+        if (lane == 0) A[k + k * s] = lkk;
+        if (lane > k && lane < s) A[lane + k * s] = A[lane + k * s] / lkk;
+        __syncwarp();
+        if (lane > k && lane < s) {
+            double lik = A[lane + k * s];
+            for (int j = k + 1; j <= lane; j++) A[lane + j * s] -= lik * A[j + k * s];
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+// Solve L L^T X = B for `nrhs` column-major right-hand sides (in place),
+// lanes parallel over columns.  Returns false if a result is not finite.
+__device__ __forceinline__ bool warp_chol_solve(const double* L, int s, double* B, int nrhs) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    for (int c = lane; c < nrhs; c += 32) {
+        double* b = B + c * s;
+        for (int i = 0; i < s; i++) {
+            double t = b[i];
+            for (int k = 0; k < i; k++) t -= L[i + k * s] * b[k];
+            b[i] = t / L[i + i * s];
+        }
+        for (int i = s - 1; i >= 0; i--) {
+            double t = b[i];
+            for (int k = i + 1; k < s; k++) t -= L[k + i * s] * b[k];
+            b[i] = t / L[i + i * s];
+            ok = ok && isfinite(b[i]);
+        }
+    }
+    __syncwarp();
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Scratch for the solves: 5 s x s matrices and 3 vectors (kMaxS bounds).
+struct SmallScratch {
+    double L[kMaxS * kMaxS];
+    double X[kMaxS * kMaxS];
+    double Wn[kMaxS * kMaxS];
+    double b1[kMaxS * kMaxS];
+    double a[kMaxS];
+    double c[kMaxS];
+};
+
+// Algorithm 6 (SW) for the monomial basis, or its first-step form, by one
+// warp.  Inputs in ctrl: mu[0..2s-1] (vm(k) = mu_{k-1}), and for step > 0
+// the previous W and alpha.  Outputs: W, alpha, beta.  Returns an
+// sscg_status (0 or SSCG_BREAKDOWN).
+//   step 0:  W(a,b) = mu_{a+b+1}, beta = 0, W alpha = (mu_0..mu_{s-1})
+//   step >0: c_t = -(mu_t + sum_{j<t} c_j alpha_prev(s-1-t+j)) / alpha_prev(s-1)
+//            b1(a,b) = -c_{a+b+1-s} (zero when a+b+1 < s), all a, b
+//            W_prev beta = b1;  W = H - b1 beta;  W alpha = m
+// (0-based indices; b1 filled over all (a, b), the consistent reading of
+// Algorithm 6, whose b1 equals -c_i of Section II-A.)
+__device__ int warp_sw_monomial(Ctrl* ctrl, int s, int step, SmallScratch* sc) {
+    const int lane = threadIdx.x & 31;
+    const double* mu = ctrl->mu;
+    if (step == 0) {
+        for (int e = lane; e < s * s; e += 32) {
+            int a = e % s, b = e / s;
+            sc->Wn[e] = mu[a + b + 1];
+            sc->L[e] = mu[a + b + 1];
+            sc->X[e] = 0.0;
+        }
+        if (lane < s) sc->a[lane] = mu[lane];
+        __syncwarp();
+        if (!warp_cholesky(sc->L, s)) return 2;
+        if (!warp_chol_solve(sc->L, s, sc->a, 1)) return 2;
+    } else {
+        double as = ctrl->alpha[s - 1];
+        if (as == 0.0 || !isfinite(as)) return 2;
+        if (lane == 0) {
+            for (int t = 0; t < s; t++) {
+                double v = mu[t];
+                for (int j = 0; j < t; j++) v += sc->c[j] * ctrl->alpha[s - 1 - t + j];
+                sc->c[t] = -v / as;
+            }
+        }
+        __syncwarp();
+        for (int e = lane; e < s * s; e += 32) {
+            int a = e % s, b = e / s;
+            int q = a + b + 1 - s;
+            double v = q >= 0 ? -sc->c[q] : 0.0;
+            sc->b1[e] = v;
+            sc->X[e] = v;
+            sc->L[e] = ctrl->W[e];
+        }
+        __syncwarp();
+        if (!warp_cholesky(sc->L, s)) return 2;          // W_prev
+        if (!warp_chol_solve(sc->L, s, sc->X, s)) return 2;  // beta = W_prev^-1 b1
+        for (int e = lane; e < s * s; e += 32) {
+            int a = e % s, b = e / s;
+            double t = mu[a + b + 1];
+            for (int k = 0; k < s; k++) t -= sc->b1[a + k * s] * sc->X[k + b * s];
+            sc->Wn[e] = t;
+        }
+        __syncwarp();
+        for (int e = lane; e < s * s; e += 32) sc->L[e] = sc->Wn[e];
+        if (lane < s) sc->a[lane] = mu[lane];
+        __syncwarp();
+        if (!warp_cholesky(sc->L, s)) return 2;
+        if (!warp_chol_solve(sc->L, s, sc->a, 1)) return 2;
+    }
+    for (int e = lane; e < s * s; e += 32) {
+        ctrl->W[e] = sc->Wn[e];
+        ctrl->beta[e] = sc->X[e];
+    }
+    if (lane < s) ctrl->alpha[lane] = sc->a[lane];
+    __syncwarp();
+    return 0;
+}
+
+// The same step with Gram blocks formed directly (any basis):
+//   step 0:  W = G, beta = 0;  step > 0: W_prev beta = -C, W = G + C^T beta
+//   W alpha = m.   G, C (column-major, C(l,j) = (A p_l^old) . u_j) and m in ctrl.
+__device__ int warp_sw_gram(Ctrl* ctrl, int s, int step, SmallScratch* sc) {
+    const int lane = threadIdx.x & 31;
+    if (step == 0) {
+        for (int e = lane; e < s * s; e += 32) {
+            sc->Wn[e] = ctrl->G[e];
+            sc->X[e] = 0.0;
+        }
+    } else {
+        for (int e = lane; e < s * s; e += 32) {
+            sc->L[e] = ctrl->W[e];
+            sc->X[e] = -ctrl->C[e];
+        }
+        __syncwarp();
+        if (!warp_cholesky(sc->L, s)) return 2;
+        if (!warp_chol_solve(sc->L, s, sc->X, s)) return 2;
+        for (int e = lane; e < s * s; e += 32) {
+            int i = e % s, j = e / s;
+            double t = ctrl->G[e];
+            for (int l = 0; l < s; l++) t += ctrl->C[l + i * s] * sc->X[l + j * s];
+            sc->Wn[e] = t;
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < s * s; e += 32) sc->L[e] = sc->Wn[e];
+    if (lane < s) sc->a[lane] = ctrl->m[lane];
+    __syncwarp();
+    if (!warp_cholesky(sc->L, s)) return 2;
+    if (!warp_chol_solve(sc->L, s, sc->a, 1)) return 2;
+    for (int e = lane; e < s * s; e += 32) {
+        ctrl->W[e] = sc->Wn[e];
+        ctrl->beta[e] = sc->X[e];
+    }
+    if (lane < s) ctrl->alpha[lane] = sc->a[lane];
+    __syncwarp();
+    return 0;
+}
+
+}  // namespace sscg

@@ -1,0 +1,255 @@
+"""Python binding of libsscg (include/sscg.h): argument marshalling only.
+
+PyTorch supplies device memory (matrix storage, solve workspace, vectors)
+and the CUDA stream; every numerical step runs in the library's kernels.
+There is no CPU fallback: importing this module on a machine without the
+built library, or calling a solve without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsscg.so")
+
+OK, NOT_CONVERGED, BREAKDOWN, TIMEOUT = 0, 1, 2, 3
+ERR_INVALID, ERR_NOT_SPD, ERR_CUDA, ERR_SPACE, ERR_NONFINITE = -1, -2, -3, -4, -5
+BASIS = {"monomial": 0, "chebyshev": 1}
+PREC = {"none": 0, "jacobi": 1, "cheb": 2}
+ARITH = {"f64": 0, "df64": 1, "mixed": 2}
+HOST_VECTORS = 0x1
+HOST_ARRAYS = 0x1
+
+# Every symbol include/sscg.h declares, for the export check.
+EXPORTS = (
+    "sscg_create", "sscg_destroy", "sscg_last_error", "sscg_status_str", "sscg_version",
+    "sscg_mat_storage_bytes", "sscg_mat_create_csr", "sscg_mat_destroy", "sscg_mat_props_get",
+    "sscg_set_preconditioner", "sscg_solve_workspace_bytes", "sscg_solve", "sscg_pcg_workspace_bytes",
+    "sscg_pcg_solve", "sscg_spmv",
+)
+
+
+class SscgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sscg error {code}: {msg}")
+        self.code = code
+
+
+class Opts(C.Structure):
+    _fields_ = [("s", C.c_int), ("basis", C.c_int), ("basis_lmin", C.c_double), ("basis_lmax", C.c_double),
+                ("tol", C.c_double), ("maxit", C.c_int), ("arith", C.c_int), ("replace_every", C.c_int),
+                ("flags", C.c_uint)]
+
+
+class Info(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("equiv_iters", C.c_int64),
+                ("rel_res_recursive", C.c_double), ("rel_res_true", C.c_double), ("hist", C.c_void_p),
+                ("hist_cap", C.c_int), ("hist_len", C.c_int), ("kernel_launches", C.c_int64),
+                ("t_init_ms", C.c_double), ("t_mpk_ms", C.c_double), ("t_update_ms", C.c_double),
+                ("t_dir_ms", C.c_double), ("t_final_ms", C.c_double), ("n_mpk", C.c_int64),
+                ("n_update", C.c_int64), ("n_dir", C.c_int64)]
+
+
+PROFILE = 0x2
+_PROFILE_FIELDS = ("kernel_launches", "t_init_ms", "t_mpk_ms", "t_update_ms", "t_dir_ms", "t_final_ms", "n_mpk",
+                   "n_update", "n_dir")
+
+
+class MatProps(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("bandwidth", C.c_int64), ("values_exact_fp32", C.c_int),
+                ("max_row_nnz", C.c_int), ("diag_min", C.c_double), ("diag_max", C.c_double), ("prec", C.c_int),
+                ("prec_degree", C.c_int), ("prec_lmin", C.c_double), ("prec_lmax", C.c_double)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the built library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libsscg is not built ({p}); run __graft_entry__.build()")
+    L = C.CDLL(p)
+    vp, i64, i32, dbl, sz = C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_size_t
+    P = C.POINTER
+    L.sscg_create.argtypes = [P(vp), vp]
+    L.sscg_destroy.argtypes = [vp]
+    L.sscg_last_error.argtypes = [vp]; L.sscg_last_error.restype = C.c_char_p
+    L.sscg_status_str.argtypes = [i32]; L.sscg_status_str.restype = C.c_char_p
+    L.sscg_mat_storage_bytes.argtypes = [i64, i64, P(sz)]
+    L.sscg_mat_create_csr.argtypes = [vp, i64, i64, vp, vp, vp, C.c_uint, vp, sz, P(vp)]
+    L.sscg_mat_destroy.argtypes = [vp]
+    L.sscg_mat_props_get.argtypes = [vp, P(MatProps)]
+    L.sscg_set_preconditioner.argtypes = [vp, i32, i32, dbl, dbl]
+    L.sscg_solve_workspace_bytes.argtypes = [vp, P(Opts), P(sz)]
+    L.sscg_solve.argtypes = [vp, vp, vp, vp, P(Opts), P(Info), vp, sz]
+    L.sscg_pcg_workspace_bytes.argtypes = [vp, P(Opts), P(sz)]
+    L.sscg_pcg_solve.argtypes = [vp, vp, vp, vp, P(Opts), P(Info), vp, sz]
+    L.sscg_spmv.argtypes = [vp, vp, vp, vp]
+    _lib = L
+    return L
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("sscg needs a CUDA device; there is no CPU fallback")
+    return torch
+
+
+@dataclass
+class SolveResult:
+    status: int
+    outer_iters: int
+    equiv_iters: int
+    rel_res_recursive: float
+    rel_res_true: float
+    hist: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    profile: dict = field(default_factory=dict)
+
+    @property
+    def converged(self) -> bool:
+        return self.status == OK
+
+
+class Context:
+    """A library context bound to one CUDA stream (default: torch's current)."""
+
+    def __init__(self, stream=None):
+        torch = _torch()
+        self.lib = load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        rc = self.lib.sscg_create(C.byref(h), C.c_void_p(self.stream.cuda_stream))
+        if rc != OK:
+            raise SscgError(rc, "sscg_create failed (no sm_103a device?)")
+        self.h = h
+
+    def check(self, rc, allow_positive=False):
+        if rc < 0 or (rc > 0 and not allow_positive):
+            raise SscgError(rc, self.lib.sscg_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sscg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Matrix:
+    """CSR SPD matrix copied into torch-allocated device storage."""
+
+    def __init__(self, ctx: Context, rowptr, col, val):
+        torch = _torch()
+        self.ctx = ctx
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        def dev_tensor(a, dt):
+            if isinstance(a, torch.Tensor):
+                return a.to(device=dev, dtype=dt).contiguous()
+            return torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=dt)
+
+        rp = dev_tensor(rowptr, torch.int32)
+        ci = dev_tensor(col, torch.int32)
+        vv = dev_tensor(val, torch.float64)
+        self.n = rp.numel() - 1
+        self.nnz = ci.numel()
+        nbytes = C.c_size_t()
+        ctx.check(ctx.lib.sscg_mat_storage_bytes(self.n, self.nnz, C.byref(nbytes)))
+        self.storage = torch.empty(nbytes.value, dtype=torch.uint8, device=dev)
+        h = C.c_void_p()
+        ctx.check(ctx.lib.sscg_mat_create_csr(ctx.h, self.n, self.nnz, C.c_void_p(rp.data_ptr()),
+                                              C.c_void_p(ci.data_ptr()), C.c_void_p(vv.data_ptr()), 0,
+                                              C.c_void_p(self.storage.data_ptr()), nbytes.value, C.byref(h)))
+        self.h = h
+        self.prec = "jacobi"
+
+    def props(self) -> dict:
+        p = MatProps()
+        self.ctx.check(self.ctx.lib.sscg_mat_props_get(self.h, C.byref(p)))
+        return {k: getattr(p, k) for k, _ in MatProps._fields_}
+
+    def set_preconditioner(self, kind="jacobi", degree=0, lmin=0.0, lmax=0.0):
+        self.ctx.check(self.ctx.lib.sscg_set_preconditioner(self.h, PREC[kind], int(degree), float(lmin), float(lmax)))
+        self.prec = kind
+
+    def spmv(self, x):
+        torch = _torch()
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        self.ctx.check(self.ctx.lib.sscg_spmv(self.ctx.h, self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())))
+        return y
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.sscg_mat_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_opts(s=4, basis="monomial", tol=1e-8, maxit=1000, arith="df64", basis_bounds=(0.0, 0.0),
+              replace_every=0, host_vectors=False, profile=False) -> Opts:
+    flags = (HOST_VECTORS if host_vectors else 0) | (PROFILE if profile else 0)
+    return Opts(int(s), BASIS[basis], float(basis_bounds[0]), float(basis_bounds[1]), float(tol), int(maxit),
+                ARITH[arith], int(replace_every), flags)
+
+
+class Solver:
+    """Owns the workspace for repeated solves with one matrix and option set."""
+
+    def __init__(self, A: Matrix, method="sstep", **kw):
+        torch = _torch()
+        self.A = A
+        self.method = method
+        self.opts = make_opts(**kw)
+        nbytes = C.c_size_t()
+        fn = A.ctx.lib.sscg_solve_workspace_bytes if method == "sstep" else A.ctx.lib.sscg_pcg_workspace_bytes
+        A.ctx.check(fn(A.h, C.byref(self.opts), C.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=A.storage.device)
+        self.hist = np.zeros(self.opts.maxit + 2)
+
+    def solve(self, b, x) -> SolveResult:
+        """Solve in place: x holds x0 on entry and the solution on exit.
+        b, x: FP64 device tensors, or host numpy/torch arrays when the solver
+        was made with host_vectors=True."""
+        ctx = self.A.ctx
+        info = Info()
+        info.hist = self.hist.ctypes.data_as(C.c_void_p).value
+        info.hist_cap = len(self.hist)
+        fn = ctx.lib.sscg_solve if self.method == "sstep" else ctx.lib.sscg_pcg_solve
+        bp = b.ctypes.data if isinstance(b, np.ndarray) else b.data_ptr()
+        xp = x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
+        rc = fn(ctx.h, self.A.h, C.c_void_p(bp), C.c_void_p(xp), C.byref(self.opts), C.byref(info),
+                C.c_void_p(self.workspace.data_ptr()), self.workspace.numel())
+        ctx.check(rc, allow_positive=True)
+        return SolveResult(info.status, info.outer_iters, info.equiv_iters, info.rel_res_recursive,
+                           info.rel_res_true, self.hist[:info.hist_len].copy(),
+                           {k: getattr(info, k) for k in _PROFILE_FIELDS})
+
+
+def solve(A: Matrix, b, x=None, method="sstep", **kw):
+    """One-shot convenience: returns (x, SolveResult)."""
+    torch = _torch()
+    if x is None:
+        x = torch.zeros_like(b)
+    r = Solver(A, method=method, **kw).solve(b, x)
+    return x, r
