@@ -70,6 +70,7 @@ typedef enum { SSCG_ARITH_F64 = 0, SSCG_ARITH_DF64 = 1, SSCG_ARITH_MIXED = 2 } s
 /* Flags of sscg_opts.flags and sscg_mat_create_csr. */
 #define SSCG_HOST_VECTORS 0x1u /* b and x are host pointers; copies happen inside the call */
 #define SSCG_PROFILE 0x2u      /* bracket every kernel with CUDA events; fills the t_* fields of sscg_info */
+#define SSCG_DIRECT_GRAM 0x4u  /* form the Gram blocks directly even for the monomial basis */
 #define SSCG_HOST_ARRAYS 0x1u  /* CSR arrays are host pointers (sscg_mat_create_csr) */
 
 typedef struct sscg_ctx sscg_ctx;
@@ -181,6 +182,29 @@ int sscg_pcg_solve(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* 
 
 /* y = A x (device FP64 vectors of length n), the library's CSR SpMV. */
 int sscg_spmv(sscg_ctx* ctx, const sscg_mat* mat, const double* x, double* y);
+
+/* -------------------------------------------------- spectral bounds */
+
+/* Workspace bytes for sscg_estimate_bounds with `steps` Lanczos steps. */
+int sscg_bounds_workspace_bytes(const sscg_mat* mat, int steps, size_t* bytes);
+
+/* Extreme Ritz values of B^-1 A (B the matrix's current preconditioner) from
+ * `steps` steps of preconditioned CG on A y = r0 from y = 0: the Lanczos
+ * tridiagonal T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+ * T_{j,j+1} = sqrt(beta_j)/alpha_j, whose extreme eigenvalues (bisection on
+ * the Sturm count, on the device) approach the spectrum's ends from inside.
+ * These are the spectral bounds the Chebyshev basis (Section IV) needs.
+ * r0: device FP64 vector of length n, or NULL for the library's fixed
+ * pseudo-random start (splitmix64, seed 0x5EED5EED).  Errors:
+ * SSCG_ERR_INVALID, SSCG_ERR_SPACE, SSCG_ERR_CUDA; SSCG_BREAKDOWN if CG
+ * stops before the first step. */
+int sscg_estimate_bounds(sscg_ctx* ctx, const sscg_mat* mat, int steps, const double* r0, void* workspace,
+                         size_t workspace_bytes, double* lmin, double* lmax);
+
+/* out[i] = U[-1, 1) draw i of splitmix64 started at `seed`:
+ * z = mix(seed + (i+1) 0x9E3779B97F4A7C15), out = 2 (z >> 11) 2^-53 - 1.
+ * A seeded device generator for start vectors and synthetic inputs. */
+int sscg_uniform(sscg_ctx* ctx, int64_t n, uint64_t seed, double* out);
 
 #ifdef __cplusplus
 }

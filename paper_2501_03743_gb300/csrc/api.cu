@@ -307,15 +307,69 @@ int sscg_set_preconditioner(sscg_mat* m, int prec, int degree, double lmin, doub
     return SSCG_ERR_INVALID;
 }
 
+// The moment recurrence of Algorithm 6 serves the monomial basis with a
+// diagonal preconditioner; every other combination forms the Gram blocks.
+static bool use_gram(const sscg_mat* m, const sscg_opts* o) {
+    return o->basis == SSCG_BASIS_CHEBYSHEV || m->prec == SSCG_PREC_CHEB || (o->flags & SSCG_DIRECT_GRAM);
+}
+
+static bool auto_bounds(const sscg_opts* o) {
+    return o->basis == SSCG_BASIS_CHEBYSHEV && o->basis_lmin == 0.0 && o->basis_lmax == 0.0;
+}
+
 int sscg_solve_workspace_bytes(const sscg_mat* m, const sscg_opts* o, size_t* bytes) {
     if (!m || !o || !bytes || o->s < 1 || o->s > kMaxS || o->maxit < 0) return SSCG_ERR_INVALID;
-    return sstep_workspace(m, o, bytes);
+    if (!use_gram(m, o)) return sstep_workspace(m, o, bytes);
+    gram_workspace(m, o, bytes);
+    if (auto_bounds(o)) {
+        size_t bb = 0;
+        bounds_workspace(m, kAutoBoundSteps, &bb);
+        *bytes = std::max(*bytes, bb);
+    }
+    return SSCG_OK;
 }
 
 int sscg_solve(sscg_ctx* ctx, const sscg_mat* m, const double* b, double* x, const sscg_opts* o, sscg_info* info,
                void* ws, size_t ws_bytes) {
     if (!ctx) return SSCG_ERR_INVALID;
-    return solve_sstep(ctx, m, b, x, o, info, ws, ws_bytes);
+    if (!m || !o || !b || !x) return set_err(ctx, SSCG_ERR_INVALID, "null argument");
+    if (o->s < 1 || o->s > kMaxS) return set_err(ctx, SSCG_ERR_INVALID, "s = %d outside 1..%d", o->s, kMaxS);
+    if (o->maxit < 0 || !(o->tol >= 0.0)) return set_err(ctx, SSCG_ERR_INVALID, "bad maxit or tol");
+    if (o->basis != SSCG_BASIS_MONOMIAL && o->basis != SSCG_BASIS_CHEBYSHEV)
+        return set_err(ctx, SSCG_ERR_INVALID, "unknown basis %d", o->basis);
+    if (o->arith != SSCG_ARITH_F64 && o->arith != SSCG_ARITH_DF64)
+        return set_err(ctx, SSCG_ERR_INVALID, "arith %d not supported", o->arith);
+    if (!use_gram(m, o)) return solve_sstep(ctx, m, b, x, o, info, ws, ws_bytes);
+    double lo = o->basis_lmin, hi = o->basis_lmax;
+    if (auto_bounds(o)) {
+        size_t need = 0;
+        sscg_solve_workspace_bytes(m, o, &need);
+        if (!ws || ws_bytes < need || ((uintptr_t)ws & 255))
+            return set_err(ctx, SSCG_ERR_SPACE, "workspace needs %zu bytes, 256-byte aligned", need);
+        int rc = estimate_bounds(ctx, m, kAutoBoundSteps, nullptr, ws, ws_bytes, &lo, &hi);
+        if (rc != SSCG_OK) return rc;
+        lo *= kAutoBoundLow;
+        hi *= kAutoBoundHigh;
+    }
+    if (o->basis == SSCG_BASIS_CHEBYSHEV && !(hi > lo && lo >= 0.0))
+        return set_err(ctx, SSCG_ERR_INVALID, "Chebyshev basis needs 0 <= basis_lmin < basis_lmax");
+    return solve_gram(ctx, m, b, x, o, info, ws, ws_bytes, lo, hi);
+}
+
+int sscg_bounds_workspace_bytes(const sscg_mat* m, int steps, size_t* bytes) {
+    if (!m || !bytes || steps < 1 || steps > 100000) return SSCG_ERR_INVALID;
+    return bounds_workspace(m, steps, bytes);
+}
+
+int sscg_estimate_bounds(sscg_ctx* ctx, const sscg_mat* m, int steps, const double* r0, void* ws, size_t ws_bytes,
+                         double* lmin, double* lmax) {
+    if (!ctx) return SSCG_ERR_INVALID;
+    return estimate_bounds(ctx, m, steps, r0, ws, ws_bytes, lmin, lmax);
+}
+
+int sscg_uniform(sscg_ctx* ctx, int64_t n, uint64_t seed, double* out) {
+    if (!ctx) return SSCG_ERR_INVALID;
+    return splitmix_uniform(ctx, n, seed, out);
 }
 
 int sscg_pcg_workspace_bytes(const sscg_mat* m, const sscg_opts* o, size_t* bytes) {

@@ -81,10 +81,14 @@ inline int set_err(sscg_ctx* ctx, int code, const char* fmt, ...) {
 
 // Launch geometry: grid-stride kernels use a grid of `ctas_per_sm` CTAs
 // on each SM.
+// Workspaces size their per-CTA partial arrays for this many CTAs.
+constexpr int kMaxGrid = 8 * 160;
+
 inline int grid_for(const sscg_ctx* ctx, int64_t rows, int ctas_per_sm) {
     int64_t tiles = (rows + 255) / 256;
     int64_t g = (int64_t)ctx->sm_count * ctas_per_sm;
     if (tiles < g) g = tiles;
+    if (g > kMaxGrid) g = kMaxGrid;
     return g < 1 ? 1 : (int)g;
 }
 
@@ -174,5 +178,17 @@ int solve_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
               sscg_info* info, void* ws, size_t ws_bytes);
 int pcg_workspace(const sscg_mat* mat, const sscg_opts* opts, size_t* bytes);
 int spmv_f64(sscg_ctx* ctx, const sscg_mat* mat, const double* x, double* y);
+int gram_workspace(const sscg_mat* mat, const sscg_opts* opts, size_t* bytes);
+int solve_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* opts,
+               sscg_info* info, void* ws, size_t ws_bytes, double blo, double bhi);
+int bounds_workspace(const sscg_mat* mat, int steps, size_t* bytes);
+int estimate_bounds(sscg_ctx* ctx, const sscg_mat* mat, int steps, const double* r0, void* ws, size_t ws_bytes,
+                    double* lmin, double* lmax);
+int splitmix_uniform(sscg_ctx* ctx, int64_t n, uint64_t seed, double* out);
+
+// Steps of the Lanczos estimate a Chebyshev-basis solve runs when the caller
+// gives no basis interval, and the widening applied to its Ritz values.
+constexpr int kAutoBoundSteps = 20;
+constexpr double kAutoBoundLow = 0.95, kAutoBoundHigh = 1.05;
 
 }  // namespace sscg

@@ -1,15 +1,23 @@
 // Preconditioned CG (Algorithm 1), the comparator of the s-step method, on
-// the same SpMV tiles and arithmetic.  Per iteration:
+// the same SpMV tiles and arithmetic, and the Lanczos spectral-bound
+// estimate built on it.  Per iteration:
 //   k_pcg_spmv   : s_k = A p_k and p_k . s_k; last CTA forms alpha_k
-//   k_pcg_update : x += alpha p, r -= alpha s, u = B^-1 r, r.r and u.r;
-//                  last CTA forms beta_k and tests convergence
-//   k_pcg_dir    : p_{k+1} = B^-1 r_{k+1} + beta_k p_k
+//   k_pcg_update : x += alpha p, r -= alpha s, ||r||^2 (and, with a diagonal
+//                  B, u = B^-1 r and u . r); last CTA tests convergence and,
+//                  with a diagonal B, forms beta_k
+//   (Chebyshev B: the preconditioner kernels, then k_pcg_rho for u . r, beta_k)
+//   k_pcg_dir    : p_{k+1} = u_{k+1} + beta_k p_k
+// The Lanczos estimate runs k steps from y = 0 on A y = r0 and takes the
+// extreme Ritz values of B^-1 A from the CG coefficients:
+//   T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},  T_{j,j+1} = sqrt(beta_j)/alpha_j
+// (Saad, Iterative Methods for Sparse Linear Systems, Sec. 6.7.3).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 
 #include "common.cuh"
 #include "internal.h"
+#include "prec.cuh"
 #include "spmv.cuh"
 
 namespace sscg {
@@ -19,7 +27,7 @@ namespace {
 __device__ __forceinline__ int done_of(const Ctrl* c) { return __ldcg(&c->done); }
 
 template <class A, int VM>
-__global__ void __launch_bounds__(kThreads) k_pcg_init(MatView M, const typename A::S* __restrict__ dinv,
+__global__ void __launch_bounds__(kThreads) k_pcg_init(MatView M, const typename A::S* __restrict__ dinv, int diag,
                                                        const double* __restrict__ b, const double* __restrict__ x0,
                                                        typename A::S* __restrict__ xw, typename A::S* __restrict__ r,
                                                        typename A::S* __restrict__ p, double* __restrict__ part,
@@ -31,19 +39,22 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(MatView M, const typename
     const int ntiles = (M.n + kTileRows - 1) / kTileRows;
     R bb = A::zero(), rr = A::zero(), ru = A::zero();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        R y;
-        int row;
-        bool live = tile_spmv<A, VM>(M, tile, [&](int c) { return A::from_d(__ldg(x0 + c)); }, y, row, smem, s_rp);
+        R y = A::zero();
+        int row = tile * kTileRows + threadIdx.x;
+        bool live = row < M.n;
+        if (x0) live = tile_spmv<A, VM>(M, tile, [&](int c) { return A::from_d(__ldg(x0 + c)); }, y, row, smem, s_rp);
         if (live) {
             R bi = A::from_d(b[row]);
             R ri = A::sub(bi, y);
-            R ui = dinv ? A::mul(A::ld(dinv + row), ri) : ri;
             if (xw) A::st(xw + row, A::zero());  // DF64 iterate holds x - x0
             A::st(r + row, ri);
-            A::st(p + row, ui);
             bb = A::fma(bi, bi, bb);
             rr = A::fma(ri, ri, rr);
-            ru = A::fma(ri, ui, ru);
+            if (diag) {
+                R ui = dinv ? A::mul(A::ld(dinv + row), ri) : ri;
+                A::st(p + row, ui);
+                ru = A::fma(ri, ui, ru);
+            }
         }
     }
     R v[3] = {bb, rr, ru};
@@ -126,13 +137,13 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv(MatView M, const typename
 }
 
 template <class A>
-__global__ void __launch_bounds__(kThreads) k_pcg_update(int n, typename A::S* __restrict__ x,
+__global__ void __launch_bounds__(kThreads) k_pcg_update(int n, int diag, typename A::S* __restrict__ x,
                                                          typename A::S* __restrict__ r,
                                                          const typename A::S* __restrict__ p,
                                                          const typename A::S* __restrict__ q,
                                                          const typename A::S* __restrict__ dinv,
                                                          double* __restrict__ part, Ctrl* ctrl,
-                                                         double* __restrict__ hist) {
+                                                         double* __restrict__ hist, double* __restrict__ coef) {
     using R = typename A::R;
     if (done_of(ctrl)) return;
     __shared__ double red[2 * (kThreads / 32)];
@@ -144,9 +155,11 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, typename A::S* _
         R ri = A::sub(A::ld(r + i), A::mul(alpha, A::ld(q + i)));
         A::st(x + i, xi);
         A::st(r + i, ri);
-        R ui = dinv ? A::mul(A::ld(dinv + i), ri) : ri;
         rr = A::fma(ri, ri, rr);
-        ru = A::fma(ri, ui, ru);
+        if (diag) {
+            R ui = dinv ? A::mul(A::ld(dinv + i), ri) : ri;
+            ru = A::fma(ri, ui, ru);
+        }
     }
     R v[2] = {rr, ru};
     double out[2];
@@ -163,8 +176,12 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, typename A::S* _
     if (threadIdx.x == 0) {
         int step = ctrl->step + 1;
         double rel = sqrt(srr) / ctrl->bnorm;
-        ctrl->pcg_beta = sru / ctrl->rho;
-        ctrl->rho = sru;
+        if (coef) coef[2 * (step - 1)] = ctrl->pcg_alpha;
+        if (diag) {
+            ctrl->pcg_beta = sru / ctrl->rho;
+            ctrl->rho = sru;
+            if (coef) coef[2 * (step - 1) + 1] = ctrl->pcg_beta;
+        }
         ctrl->step = step;
         ctrl->relres = rel;
         hist[step] = rel;
@@ -182,16 +199,57 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, typename A::S* _
     }
 }
 
+// rho = r . u with u = B^-1 r from the preconditioner kernels.  first: set
+// rho; otherwise beta_k = rho_new / rho (recorded in coef).
 template <class A>
-__global__ void __launch_bounds__(kThreads) k_pcg_dir(int n, typename A::S* __restrict__ p,
+__global__ void __launch_bounds__(kThreads) k_pcg_rho(int n, const typename A::S* __restrict__ r,
+                                                      const typename A::S* __restrict__ u, int first,
+                                                      double* __restrict__ part, Ctrl* ctrl,
+                                                      double* __restrict__ coef) {
+    using R = typename A::R;
+    if (done_of(ctrl)) return;
+    __shared__ double red[kThreads / 32];
+    R ru = A::zero();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        ru = A::fma(A::ld(r + i), A::ld(u + i), ru);
+    R v[1] = {ru};
+    double out[1];
+    block_sum<A, 1>(v, red, out);
+    if (threadIdx.x == 0) part[blockIdx.x] = out[0];
+    if (!last_cta(&ctrl->ticket[3])) return;
+    __shared__ double sh[32];
+    double t = cta_sum_partials(part, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        if (first) {
+            ctrl->rho = t;
+        } else {
+            ctrl->pcg_beta = t / ctrl->rho;
+            ctrl->rho = t;
+            if (coef) coef[2 * (ctrl->step - 1) + 1] = ctrl->pcg_beta;
+        }
+        if (!(t > 0.0) || !isfinite(t)) {
+            ctrl->status = 2;
+            ctrl->done = 1;
+        }
+    }
+}
+
+template <class A>
+__global__ void __launch_bounds__(kThreads) k_pcg_dir(int n, int diag, typename A::S* __restrict__ p,
                                                       const typename A::S* __restrict__ r,
+                                                      const typename A::S* __restrict__ u,
                                                       const typename A::S* __restrict__ dinv, const Ctrl* ctrl) {
     using R = typename A::R;
     if (done_of(ctrl)) return;
     const R beta = A::from_d(ctrl->pcg_beta);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        R ri = A::ld(r + i);
-        R ui = dinv ? A::mul(A::ld(dinv + i), ri) : ri;
+        R ui;
+        if (diag) {
+            R ri = A::ld(r + i);
+            ui = dinv ? A::mul(A::ld(dinv + i), ri) : ri;
+        } else {
+            ui = A::ld(u + i);
+        }
         A::st(p + i, A::fma(beta, A::ld(p + i), ui));
     }
 }
@@ -232,27 +290,90 @@ __global__ void __launch_bounds__(kThreads) k_pcg_true_res(MatView M, const doub
     if (threadIdx.x == 0) ctrl->true_res2 = t;
 }
 
+// splitmix64 in counter form: draw i of the generator started at `seed` is
+// mix(seed + (i+1) * 0x9E3779B97F4A7C15); U[-1,1) = 2 (z >> 11) 2^-53 - 1.
+__global__ void k_splitmix_uniform(int n, unsigned long long seed, double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        out[i] = (double)(z >> 11) * 0x1p-52 - 1.0;
+    }
+}
+
+// Number of eigenvalues of the tridiagonal (d, e) below x (Sturm count).
+__device__ int sturm_count(int k, const double* d, const double* e, double x) {
+    int cnt = 0;
+    double q = d[0] - x;
+    if (q < 0.0) cnt++;
+    for (int i = 1; i < k; i++) {
+        if (q == 0.0) q = 1e-300;
+        q = d[i] - x - e[i - 1] * e[i - 1] / q;
+        if (q < 0.0) cnt++;
+    }
+    return cnt;
+}
+
+// Extreme Ritz values from k CG steps (coef: alpha_j, beta_j pairs) by
+// bisection on the Sturm count of the Lanczos tridiagonal (one thread).
+__global__ void k_ritz(const double* __restrict__ coef, int k, double* __restrict__ dwork, Ctrl* ctrl) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double* d = dwork;
+    double* e = dwork + k;
+    for (int j = 0; j < k; j++) {
+        double a = coef[2 * j];
+        d[j] = 1.0 / a + (j > 0 ? coef[2 * (j - 1) + 1] / coef[2 * (j - 1)] : 0.0);
+        if (j + 1 < k) e[j] = sqrt(coef[2 * j + 1]) / a;
+    }
+    double lo = d[0], hi = d[0];
+    for (int i = 0; i < k; i++) {
+        double rad = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < k ? fabs(e[i]) : 0.0);
+        lo = fmin(lo, d[i] - rad);
+        hi = fmax(hi, d[i] + rad);
+    }
+    double span = hi - lo + 1e-300;
+    lo -= 1e-12 * span;
+    hi += 1e-12 * span;
+    for (int which = 0; which < 2; which++) {
+        int target = which == 0 ? 1 : k;
+        double l = lo, h = hi;
+        for (int it = 0; it < 200 && h - l > 1e-15 * (fabs(l) + fabs(h)); it++) {
+            double mid = 0.5 * (l + h);
+            if (sturm_count(k, d, e, mid) >= target) h = mid;
+            else l = mid;
+        }
+        ctrl->scratch[which] = 0.5 * (l + h);
+    }
+}
+
 struct PLayout {
     Ctrl* ctrl;
     double* hist;
     double* part;
-    void *x, *r, *p, *q;
+    double* coef;
+    void *x, *r, *p, *q, *u, *tmp;
     double *bdev, *xdev;
     size_t bytes;
 };
 
-PLayout pplan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t cap) {
+PLayout pplan(const sscg_mat* mat, int maxit, unsigned flags, void* base, size_t cap) {
     PLayout L{};
     size_t ldn = align_up((size_t)mat->n, 64);
     Carve c(base, cap);
     L.ctrl = c.take<Ctrl>(1);
-    L.hist = c.take<double>((size_t)o->maxit + 2);
-    L.part = c.take<double>((size_t)G * 4);
+    L.hist = c.take<double>((size_t)maxit + 2);
+    L.part = c.take<double>((size_t)8 * 160 * 4);
+    L.coef = c.take<double>(2 * ((size_t)maxit + 2));
     L.x = c.take<double>(ldn);
     L.r = c.take<double>(ldn);
     L.p = c.take<double>(ldn);
     L.q = c.take<double>(ldn);
-    if (o->flags & SSCG_HOST_VECTORS) {
+    if (mat->prec == SSCG_PREC_CHEB) {
+        L.u = c.take<double>(ldn);
+        L.tmp = c.take<double>(3 * ldn);
+    }
+    if (flags & SSCG_HOST_VECTORS) {
         L.bdev = c.take<double>(ldn);
         L.xdev = c.take<double>(ldn);
     }
@@ -260,44 +381,57 @@ PLayout pplan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t
     return L;
 }
 
-int cap_of(const sscg_mat* m) {
-    int cap = m->max_tile_nnz;
-    if (cap > 8192) cap = 8192;
-    if (cap < 32) cap = 32;
-    return (cap + 31) / 32 * 32;
-}
-
-template <class A, int VM>
-int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o, const PLayout& L,
-            int G, const typename A::S* dinv, Ctrl* h, Prof& P) {
-    using S = typename A::S;
-    cudaStream_t st = ctx->stream;
-    const int n = (int)mat->n;
-    const int cap = cap_of(mat);
+MatView view(const sscg_mat* mat) {
     MatView M;
-    M.n = n;
-    M.cap = cap;
+    int cap = std::min(8192, std::max(32, mat->max_tile_nnz));
+    M.n = (int)mat->n;
+    M.cap = (cap + 31) / 32 * 32;
     M.rowptr = mat->rowptr;
     M.col = mat->col;
     M.val = mat->val;
     M.vhi = mat->vhi;
     M.vlo = mat->vlo;
-    const size_t smem = stage_bytes<A, VM>(cap), smem64 = stage_bytes<ArithF64, VAL_F64>(cap);
+    return M;
+}
+
+// One PCG run.  x may be null (zero start and no export; the Lanczos
+// estimate); coef receives alpha_j, beta_j when not null.
+template <class A, int VM>
+int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int maxit, const PLayout& L,
+            const typename A::S* dinv, Ctrl* h, Prof& P, double* coef) {
+    using S = typename A::S;
+    cudaStream_t st = ctx->stream;
+    const int n = (int)mat->n;
+    const MatView M = view(mat);
+    const size_t smem = stage_bytes<A, VM>(M.cap), smem64 = stage_bytes<ArithF64, VAL_F64>(M.cap);
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_spmv<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_cheb_step<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_true_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
-    S* xw = A::kind == 0 ? (S*)x : (S*)L.x;
-    S* r = (S*)L.r;
-    S* p = (S*)L.p;
-    S* q = (S*)L.q;
-    P.begin();
     const int Gi = occupancy_grid(ctx, k_pcg_init<A, VM>, smem, n);
     const int Gs = occupancy_grid(ctx, k_pcg_spmv<A, VM>, smem, n);
     const int Gu = occupancy_grid(ctx, k_pcg_update<A>, 0, n);
     const int Gd = occupancy_grid(ctx, k_pcg_dir<A>, 0, n);
+    const int Gr = occupancy_grid(ctx, k_pcg_rho<A>, 0, n);
     const int Gt = occupancy_grid(ctx, k_pcg_true_res, smem64, n);
-    k_pcg_init<A, VM><<<Gi, kThreads, smem, st>>>(M, dinv, b, x, A::kind == 0 ? nullptr : xw, r, p, L.part, L.ctrl,
-                                                 L.hist);
+    const bool diag = mat->prec != SSCG_PREC_CHEB;
+    ChebPrec<A, VM> cheb(diag ? 1 : mat->degree, diag ? 1.0 : mat->plmin, diag ? 2.0 : mat->plmax);
+    const size_t ld = align_up((size_t)mat->n, 64);
+    S* xw = (A::kind == 0) ? (S*)x : (S*)L.x;
+    S* r = (S*)L.r;
+    S* p = (S*)L.p;
+    S* q = (S*)L.q;
+    S* u = (S*)L.u;
+    S* tmp = (S*)L.tmp;
+    if (!x) xw = (S*)L.x;  // zero start: the iterate lives in the workspace
+    P.begin();
+    k_pcg_init<A, VM><<<Gi, kThreads, smem, st>>>(M, dinv, diag ? 1 : 0, b, x, (A::kind == 0 && x) ? nullptr : xw,
+                                                  r, p, L.part, L.ctrl, L.hist);
+    if (!diag) {
+        P.launches += cheb.apply(M, dinv, r, p, tmp, ld, Gd, Gs, smem, st, L.ctrl);
+        k_pcg_rho<A><<<Gr, kThreads, 0, st>>>(n, r, p, 1, L.part, L.ctrl, coef);
+        P.launches++;
+    }
     P.end(FAM_INIT, 0);
     SSCG_CUDA(ctx, cudaGetLastError());
     const int per_chunk = 16;
@@ -305,21 +439,30 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, cons
     SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
     SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
     int launched = 0, chunk = 0, pending = -1, err = 0;
-    while (launched < o->maxit) {
-        int c = std::min(per_chunk, o->maxit - launched);
+    while (launched < maxit) {
+        int c = std::min(per_chunk, maxit - launched);
         for (int k = 0; k < c; k++) {
             const int it = launched + k;
             P.begin();
             k_pcg_spmv<A, VM><<<Gs, kThreads, smem, st>>>(M, p, q, L.part, L.ctrl);
             P.end(FAM_MPK, it);
             P.begin();
-            k_pcg_update<A><<<Gu, kThreads, 0, st>>>(n, xw, r, p, q, dinv, L.part, L.ctrl, L.hist);
+            k_pcg_update<A><<<Gu, kThreads, 0, st>>>(n, diag ? 1 : 0, xw, r, p, q, dinv, L.part, L.ctrl, L.hist,
+                                                     coef);
             P.end(FAM_UPDATE, it);
             P.begin();
-            k_pcg_dir<A><<<Gd, kThreads, 0, st>>>(n, p, r, dinv, L.ctrl);
+            if (!diag) {
+                P.launches += cheb.apply(M, dinv, r, u, tmp, ld, Gd, Gs, smem, st, L.ctrl);
+                k_pcg_rho<A><<<Gr, kThreads, 0, st>>>(n, r, u, 0, L.part, L.ctrl, coef);
+                P.launches++;
+            }
+            k_pcg_dir<A><<<Gd, kThreads, 0, st>>>(n, diag ? 1 : 0, p, r, u, dinv, L.ctrl);
             P.end(FAM_DIR, it);
         }
-        if (cudaGetLastError() != cudaSuccess) { err = 1; break; }
+        if (cudaGetLastError() != cudaSuccess) {
+            err = 1;
+            break;
+        }
         launched += c;
         const int slot = chunk & 1;
         SSCG_CUDA(ctx, cudaMemcpyAsync((void*)(ctx->pinned + slot), &L.ctrl->done, sizeof(int),
@@ -334,21 +477,52 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, cons
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     if (err) return set_err(ctx, SSCG_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-    P.begin();
-    k_pcg_export<A><<<G, kThreads, 0, st>>>(n, xw, x, L.ctrl);
-    k_pcg_true_res<<<Gt, kThreads, smem64, st>>>(M, b, x, L.part, L.ctrl);
-    P.end(FAM_FINAL, 0);
-    P.launches++;
+    if (x) {
+        P.begin();
+        k_pcg_export<A><<<Gd, kThreads, 0, st>>>(n, xw, x, L.ctrl);
+        k_pcg_true_res<<<Gt, kThreads, smem64, st>>>(M, b, x, L.part, L.ctrl);
+        P.end(FAM_FINAL, 0);
+        P.launches++;
+    }
     SSCG_CUDA(ctx, cudaGetLastError());
     SSCG_CUDA(ctx, cudaMemcpyAsync(h, L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     SSCG_CUDA(ctx, cudaStreamSynchronize(st));
     return 0;
 }
 
+int dispatch_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int maxit, int arith,
+                 const PLayout& L, Ctrl* h, Prof& P, double* coef) {
+    const bool scale = mat->prec != SSCG_PREC_NONE;  // Jacobi and Chebyshev scale by D^-1
+    if (arith == SSCG_ARITH_F64)
+        return run_pcg<ArithF64, VAL_F64>(ctx, mat, b, x, maxit, L, scale ? mat->dinv : nullptr, h, P, coef);
+    if (mat->exact_fp32)
+        return run_pcg<ArithDF64, VAL_F32>(ctx, mat, b, x, maxit, L, scale ? mat->dinv_df : nullptr, h, P, coef);
+    return run_pcg<ArithDF64, VAL_DF>(ctx, mat, b, x, maxit, L, scale ? mat->dinv_df : nullptr, h, P, coef);
+}
+
+Ctrl fresh_ctrl(int maxit, double tol) {
+    Ctrl h;
+    memset(&h, 0, sizeof(h));
+    h.status = 1;
+    h.maxit = maxit;
+    h.s = 1;
+    h.tol = tol;
+    return h;
+}
+
 }  // namespace
 
 int pcg_workspace(const sscg_mat* mat, const sscg_opts* o, size_t* bytes) {
-    *bytes = pplan(mat, o, 8 * 160, nullptr, 0).bytes;
+    *bytes = pplan(mat, o->maxit, o->flags, nullptr, 0).bytes;
+    return 0;
+}
+
+int bounds_workspace(const sscg_mat* mat, int steps, size_t* bytes) {
+    Carve c(nullptr, 0);
+    c.used = pplan(mat, steps, 0, nullptr, 0).bytes;
+    c.take<double>(align_up((size_t)mat->n, 64));  // r0
+    c.take<double>(2 * (size_t)steps + 2);        // Ritz work
+    *bytes = c.used;
     return 0;
 }
 
@@ -358,14 +532,11 @@ int solve_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     if (o->maxit < 0 || !(o->tol >= 0.0)) return set_err(ctx, SSCG_ERR_INVALID, "bad maxit or tol");
     if (o->arith != SSCG_ARITH_F64 && o->arith != SSCG_ARITH_DF64)
         return set_err(ctx, SSCG_ERR_INVALID, "arith %d not supported by PCG", o->arith);
-    if (mat->prec != SSCG_PREC_NONE && mat->prec != SSCG_PREC_JACOBI)
-        return set_err(ctx, SSCG_ERR_INVALID, "preconditioner %d not supported by this solver", mat->prec);
     size_t need = 0;
     pcg_workspace(mat, o, &need);
     if (!ws || ws_bytes < need || ((uintptr_t)ws & 255))
         return set_err(ctx, SSCG_ERR_SPACE, "workspace needs %zu bytes, 256-byte aligned (got %zu)", need, ws_bytes);
-    const int G = grid_for(ctx, mat->n, 8);
-    PLayout L = pplan(mat, o, G, ws, ws_bytes);
+    PLayout L = pplan(mat, o->maxit, o->flags, ws, ws_bytes);
     cudaStream_t st = ctx->stream;
     const int64_t n = mat->n;
     const double* bd = b;
@@ -376,26 +547,14 @@ int solve_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
         bd = L.bdev;
         xd = L.xdev;
     }
-    Ctrl h;
-    memset(&h, 0, sizeof(h));
-    h.status = 1;
-    h.maxit = o->maxit;
-    h.s = 1;
-    h.tol = o->tol;
+    Ctrl h = fresh_ctrl(o->maxit, o->tol);
     SSCG_CUDA(ctx, cudaMemcpyAsync(L.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
-    const bool jac = mat->prec == SSCG_PREC_JACOBI;
-    int rc;
     Prof* prof = new Prof(ctx, (o->flags & SSCG_PROFILE) != 0);
     if (!prof->reserve((int)std::min<int64_t>(65536, (int64_t)o->maxit * 3 + 64))) {
         delete prof;
         return set_err(ctx, SSCG_ERR_CUDA, "could not create profiling events");
     }
-    if (o->arith == SSCG_ARITH_F64)
-        rc = run_pcg<ArithF64, VAL_F64>(ctx, mat, bd, xd, o, L, G, jac ? mat->dinv : nullptr, &h, *prof);
-    else if (mat->exact_fp32)
-        rc = run_pcg<ArithDF64, VAL_F32>(ctx, mat, bd, xd, o, L, G, jac ? mat->dinv_df : nullptr, &h, *prof);
-    else
-        rc = run_pcg<ArithDF64, VAL_DF>(ctx, mat, bd, xd, o, L, G, jac ? mat->dinv_df : nullptr, &h, *prof);
+    int rc = dispatch_pcg(ctx, mat, bd, xd, o->maxit, o->arith, L, &h, *prof, nullptr);
     if (rc) {
         delete prof;
         return rc;
@@ -422,6 +581,49 @@ int solve_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
         info->hist_len = info->hist ? len : 0;
     }
     return h.status;
+}
+
+int estimate_bounds(sscg_ctx* ctx, const sscg_mat* mat, int steps, const double* r0, void* ws, size_t ws_bytes,
+                    double* lmin, double* lmax) {
+    if (!mat || !lmin || !lmax || steps < 1 || steps > 100000)
+        return set_err(ctx, SSCG_ERR_INVALID, "bad bounds-estimate arguments");
+    size_t need = 0;
+    bounds_workspace(mat, steps, &need);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255))
+        return set_err(ctx, SSCG_ERR_SPACE, "workspace needs %zu bytes, 256-byte aligned (got %zu)", need, ws_bytes);
+    PLayout L = pplan(mat, steps, 0, ws, ws_bytes);
+    Carve c(ws, ws_bytes);
+    c.used = L.bytes;
+    double* bvec = c.take<double>(align_up((size_t)mat->n, 64));
+    double* dwork = c.take<double>(2 * (size_t)steps + 2);
+    cudaStream_t st = ctx->stream;
+    const int n = (int)mat->n;
+    if (r0) {
+        SSCG_CUDA(ctx, cudaMemcpyAsync(bvec, r0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+        k_splitmix_uniform<<<grid_for(ctx, n, 4), kThreads, 0, st>>>(n, 0x5EED5EEDull, bvec);
+        SSCG_CUDA(ctx, cudaGetLastError());
+    }
+    Ctrl h = fresh_ctrl(steps, 0.0);
+    SSCG_CUDA(ctx, cudaMemcpyAsync(L.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    Prof prof(ctx, false);
+    int rc = dispatch_pcg(ctx, mat, bvec, nullptr, steps, SSCG_ARITH_DF64, L, &h, prof, L.coef);
+    if (rc) return rc;
+    if (h.step < 1) return set_err(ctx, SSCG_BREAKDOWN, "Lanczos took no step");
+    k_ritz<<<1, 32, 0, st>>>(L.coef, h.step, dwork, L.ctrl);
+    SSCG_CUDA(ctx, cudaGetLastError());
+    SSCG_CUDA(ctx, cudaMemcpyAsync(&h, L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    SSCG_CUDA(ctx, cudaStreamSynchronize(st));
+    *lmin = h.scratch[0];
+    *lmax = h.scratch[1];
+    return SSCG_OK;
+}
+
+int splitmix_uniform(sscg_ctx* ctx, int64_t n, uint64_t seed, double* out) {
+    if (!out || n <= 0 || n >= INT32_MAX) return set_err(ctx, SSCG_ERR_INVALID, "bad length");
+    k_splitmix_uniform<<<grid_for(ctx, n, 4), kThreads, 0, ctx->stream>>>((int)n, (unsigned long long)seed, out);
+    SSCG_CUDA(ctx, cudaGetLastError());
+    return SSCG_OK;
 }
 
 }  // namespace sscg

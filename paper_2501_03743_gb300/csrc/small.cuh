@@ -73,7 +73,7 @@ struct SmallScratch {
 //            W_prev beta = b1;  W = H - b1 beta;  W alpha = m
 // (0-based indices; b1 filled over all (a, b), the consistent reading of
 // Algorithm 6, whose b1 equals -c_i of Section II-A.)
-__device__ int warp_sw_monomial(Ctrl* ctrl, int s, int step, SmallScratch* sc) {
+__device__ inline int warp_sw_monomial(Ctrl* ctrl, int s, int step, SmallScratch* sc) {
     const int lane = threadIdx.x & 31;
     const double* mu = ctrl->mu;
     if (step == 0) {
@@ -134,7 +134,7 @@ __device__ int warp_sw_monomial(Ctrl* ctrl, int s, int step, SmallScratch* sc) {
 // The same step with Gram blocks formed directly (any basis):
 //   step 0:  W = G, beta = 0;  step > 0: W_prev beta = -C, W = G + C^T beta
 //   W alpha = m.   G, C (column-major, C(l,j) = (A p_l^old) . u_j) and m in ctrl.
-__device__ int warp_sw_gram(Ctrl* ctrl, int s, int step, SmallScratch* sc) {
+__device__ inline int warp_sw_gram(Ctrl* ctrl, int s, int step, SmallScratch* sc) {
     const int lane = threadIdx.x & 31;
     if (step == 0) {
         for (int e = lane; e < s * s; e += 32) {

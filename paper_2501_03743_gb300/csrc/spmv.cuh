@@ -39,7 +39,7 @@ template <>
 struct Val<ArithDF64, VAL_F32> {
     using T = float;
     __device__ static __forceinline__ T load(const MatView& M, int k) { return __ldg(M.vhi + k); }
-    __device__ static __forceinline__ df64 mac(df64 acc, T v, df64 x) { return df_add(acc, df_mul_f(x, v)); }
+    __device__ static __forceinline__ df64 mac(df64 acc, T v, df64 x) { return df_fma_f(x, v, acc); }
 };
 
 template <>
@@ -48,9 +48,7 @@ struct Val<ArithDF64, VAL_DF> {
     __device__ static __forceinline__ T load(const MatView& M, int k) {
         return make_float2(__ldg(M.vhi + k), __ldg(M.vlo + k));
     }
-    __device__ static __forceinline__ df64 mac(df64 acc, T v, df64 x) {
-        return df_add(acc, df_mul(x, df_make(v.x, v.y)));
-    }
+    __device__ static __forceinline__ df64 mac(df64 acc, T v, df64 x) { return df_fma(x, df_make(v.x, v.y), acc); }
 };
 
 // Bytes of dynamic shared memory for a staging capacity of `cap` entries.

@@ -19,87 +19,13 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "kernels.cuh"
 #include "small.cuh"
 #include "spmv.cuh"
 
 namespace sscg {
 
 namespace {
-
-__device__ __forceinline__ int ctrl_done(const Ctrl* c) { return __ldcg(&c->done); }
-
-// r = b - A x0 (x0 and b FP64), x_w = x0, z = B^-1 r -> u0; ||b||^2, ||r||^2,
-// mu_0 = r . z; the last CTA initialises the control block.
-template <class A, int VM>
-__global__ void __launch_bounds__(kThreads) k_init(MatView M, const typename A::S* __restrict__ dinv,
-                                                   const double* __restrict__ b, const double* __restrict__ x0,
-                                                   typename A::S* __restrict__ xw, typename A::S* __restrict__ r,
-                                                   typename A::S* __restrict__ u0, double* __restrict__ part,
-                                                   Ctrl* ctrl, double* __restrict__ hist) {
-    using R = typename A::R;
-    extern __shared__ __align__(16) char smem[];
-    __shared__ int s_rp[kTileRows + 1];
-    __shared__ double red[3 * (kThreads / 32)];
-    const int ntiles = (M.n + kTileRows - 1) / kTileRows;
-    R bb = A::zero(), rr = A::zero(), rz = A::zero();
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        R y;
-        int row;
-        bool live = tile_spmv<A, VM>(M, tile, [&](int c) { return A::from_d(__ldg(x0 + c)); }, y, row, smem, s_rp);
-        if (live) {
-            R bi = A::from_d(b[row]);
-            R ri = A::sub(bi, y);
-            R zi = dinv ? A::mul(A::ld(dinv + row), ri) : ri;
-            if (xw) A::st(xw + row, A::zero());  // DF64 iterate holds x - x0
-            A::st(r + row, ri);
-            A::st(u0 + row, zi);
-            bb = A::fma(bi, bi, bb);
-            rr = A::fma(ri, ri, rr);
-            rz = A::fma(ri, zi, rz);
-        }
-    }
-    R v[3] = {bb, rr, rz};
-    double out[3];
-    block_sum<A, 3>(v, red, out);
-    const int G = gridDim.x;
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = out[0];
-        part[G + blockIdx.x] = out[1];
-        part[2 * G + blockIdx.x] = out[2];
-    }
-    if (!last_cta(&ctrl->ticket[0])) return;
-    __shared__ double sh[32];
-    double sbb = cta_sum_partials(part, G, sh);
-    double srr = cta_sum_partials(part + G, G, sh);
-    double srz = cta_sum_partials(part + 2 * G, G, sh);
-    if (threadIdx.x == 0) {
-        ctrl->bnorm = sqrt(sbb);
-        ctrl->mu[0] = srz;
-        if (sbb == 0.0) {
-            ctrl->zero_rhs = 1;
-            ctrl->relres = 0.0;
-            hist[0] = 0.0;
-            ctrl->nhist = 1;
-            ctrl->status = 0;
-            ctrl->done = 1;
-        } else {
-            double rel = sqrt(srr) / ctrl->bnorm;
-            ctrl->relres = rel;
-            hist[0] = rel;
-            ctrl->nhist = 1;
-            if (!isfinite(rel)) {
-                ctrl->status = SSCG_ERR_NONFINITE;
-                ctrl->done = 1;
-            } else if (rel < ctrl->tol) {
-                ctrl->status = 0;
-                ctrl->done = 1;
-            } else if (ctrl->maxit == 0) {
-                ctrl->status = 1;
-                ctrl->done = 1;
-            }
-        }
-    }
-}
 
 // One level of the matrix-powers kernel (Algorithm 4): y = A u_j, written to
 // AU_j; u_{j+1} = B^-1 y (when u_next != null); moment partials
@@ -143,12 +69,7 @@ __global__ void __launch_bounds__(kThreads) k_level(MatView M, const typename A:
     }
     if (!last) return;
     if (!last_cta(&ctrl->ticket[1])) return;
-    __shared__ double sh[32];
-    for (int q = 1; q <= 2 * s - 1; q++) {
-        double t = cta_sum_partials(part + (q - 1) * G, G, sh);
-        if (threadIdx.x == 0) ctrl->mu[q] = t;
-    }
-    __syncthreads();
+    cta_sum_rows(part, 2 * s - 1, G, [&](int e, double v) { ctrl->mu[e + 1] = v; });
     SmallScratch* sc = reinterpret_cast<SmallScratch*>(smem);  // staging buffer is free now
     if (threadIdx.x < 32) {
         int st = warp_sw_monomial(ctrl, s, step, sc);
@@ -157,140 +78,6 @@ __global__ void __launch_bounds__(kThreads) k_level(MatView M, const typename A:
             ctrl->done = 1;
         }
     }
-}
-
-// Block updates of Algorithm 3 for one outer step (see file comment).
-// blk_new holds U | AU on entry and P | AP on exit; blk_old holds
-// P_old | AP_old and receives z = B^-1 r_new in its first column.
-template <class A, int SB>
-__global__ void __launch_bounds__(kThreads, SB <= 4 ? 3 : 2) k_update(int n, int ldn, int s, typename A::S* __restrict__ blk_new,
-                                                     typename A::S* __restrict__ blk_old,
-                                                     typename A::S* __restrict__ x, typename A::S* __restrict__ r,
-                                                     const typename A::S* __restrict__ dinv,
-                                                     double* __restrict__ part, int first, Ctrl* ctrl,
-                                                     double* __restrict__ hist) {
-    using R = typename A::R;
-    if (ctrl_done(ctrl)) return;
-    __shared__ R sb[SB * SB];
-    __shared__ R sa[SB];
-    __shared__ double red[2 * (kThreads / 32)];
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) sb[(e % s) + (e / s) * SB] = A::from_d(ctrl->beta[e]);
-    for (int e = threadIdx.x; e < s; e += blockDim.x) sa[e] = A::from_d(ctrl->alpha[e]);
-    __syncthreads();
-    R rr = A::zero(), rz = A::zero();
-    const size_t ld = (size_t)ldn;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        R po[SB], apo[SB];
-        if (!first) {
-#pragma unroll
-            for (int l = 0; l < SB; l++)
-                if (l < s) {
-                    po[l] = A::ld(blk_old + l * ld + i);
-                    apo[l] = A::ld(blk_old + (s + l) * ld + i);
-                }
-        }
-        R xa = A::zero(), ra = A::zero();
-#pragma unroll
-        for (int jj = 0; jj < SB; jj++) {
-            if (jj < s) {
-                R p = A::ld(blk_new + jj * ld + i);
-                R ap = A::ld(blk_new + (s + jj) * ld + i);
-                if (!first) {
-#pragma unroll
-                    for (int l = 0; l < SB; l++)
-                        if (l < s) {
-                            p = A::fma(po[l], sb[l + jj * SB], p);
-                            ap = A::fma(apo[l], sb[l + jj * SB], ap);
-                        }
-                }
-                A::st(blk_new + jj * ld + i, p);
-                A::st(blk_new + (s + jj) * ld + i, ap);
-                xa = A::fma(p, sa[jj], xa);
-                ra = A::fma(ap, sa[jj], ra);
-            }
-        }
-        R xn = A::add(A::ld(x + i), xa);
-        R rn = A::sub(A::ld(r + i), ra);
-        A::st(x + i, xn);
-        A::st(r + i, rn);
-        R z = dinv ? A::mul(A::ld(dinv + i), rn) : rn;
-        A::st(blk_old + i, z);
-        rr = A::fma(rn, rn, rr);
-        rz = A::fma(rn, z, rz);
-    }
-    R v[2] = {rr, rz};
-    double out[2];
-    block_sum<A, 2>(v, red, out);
-    const int G = gridDim.x;
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = out[0];
-        part[G + blockIdx.x] = out[1];
-    }
-    if (!last_cta(&ctrl->ticket[2])) return;
-    __shared__ double sh[32];
-    double srr = cta_sum_partials(part, G, sh);
-    double srz = cta_sum_partials(part + G, G, sh);
-    if (threadIdx.x == 0) {
-        int step = ctrl->step + 1;
-        double rel = sqrt(srr) / ctrl->bnorm;
-        ctrl->step = step;
-        ctrl->relres = rel;
-        ctrl->mu[0] = srz;
-        hist[step] = rel;
-        ctrl->nhist = step + 1;
-        if (!isfinite(rel)) {
-            ctrl->status = 2;
-            ctrl->done = 1;
-        } else if (rel < ctrl->tol) {
-            ctrl->status = 0;
-            ctrl->done = 1;
-        } else if (step >= ctrl->maxit) {
-            ctrl->status = 1;
-            ctrl->done = 1;
-        }
-    }
-}
-
-// x = x0 + (x - x0): the DF64 iterate carries the correction to x0, so x0
-// keeps every bit when no step is taken; 0 when b = 0.
-template <class A>
-__global__ void k_export_x(int n, const typename A::S* __restrict__ xw, double* __restrict__ x, const Ctrl* ctrl) {
-    const int zero = ctrl->zero_rhs;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        x[i] = zero ? 0.0 : x[i] + A::to_d(A::ld(xw + i));
-}
-
-// F64 iterates in place: only b = 0 needs x cleared.
-__global__ void k_zero_if_zero_rhs(int n, double* __restrict__ x, const Ctrl* ctrl) {
-    if (!ctrl->zero_rhs) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = 0.0;
-}
-
-// ||b - A x||^2 in FP64 (the true residual reported at exit).
-__global__ void __launch_bounds__(kThreads) k_true_res(MatView M, const double* __restrict__ b,
-                                                       const double* __restrict__ x, double* __restrict__ part,
-                                                       Ctrl* ctrl) {
-    extern __shared__ __align__(16) char smem[];
-    __shared__ int s_rp[kTileRows + 1];
-    __shared__ double red[kThreads / 32];
-    const int ntiles = (M.n + kTileRows - 1) / kTileRows;
-    double acc = 0.0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        double y;
-        int row;
-        bool live = tile_spmv<ArithF64, VAL_F64>(M, tile, [&](int c) { return __ldg(x + c); }, y, row, smem, s_rp);
-        if (live) {
-            double t = b[row] - y;
-            acc = fma(t, t, acc);
-        }
-    }
-    double v[1] = {acc}, out[1];
-    block_sum<ArithF64, 1>(v, red, out);
-    if (threadIdx.x == 0) part[blockIdx.x] = out[0];
-    if (!last_cta(&ctrl->ticket[3])) return;
-    __shared__ double sh[32];
-    double t = cta_sum_partials(part, gridDim.x, sh);
-    if (threadIdx.x == 0) ctrl->true_res2 = t;
 }
 
 // ------------------------------------------------------------ host side
@@ -399,8 +186,8 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
                 P.end(FAM_MPK, k);
             }
             P.begin();
-            k_update<A, SB><<<Gu, kThreads, 0, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dinv, L.part, k == 0, L.ctrl,
-                                                     L.hist);
+            k_update<A, SB><<<Gu, kThreads, 0, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dinv, L.part, k == 0, 1,
+                                                     L.ctrl, L.hist);
             P.end(FAM_UPDATE, k);
         }
         if (cudaGetLastError() != cudaSuccess) { err = 1; break; }
@@ -446,7 +233,8 @@ static int check_opts(sscg_ctx* ctx, const sscg_mat* mat, const sscg_opts* o) {
     if (!(o->tol >= 0.0)) return set_err(ctx, SSCG_ERR_INVALID, "tol must be >= 0");
     if (o->arith != SSCG_ARITH_F64 && o->arith != SSCG_ARITH_DF64)
         return set_err(ctx, SSCG_ERR_INVALID, "arith %d not supported by this solver", o->arith);
-    if (o->basis != SSCG_BASIS_MONOMIAL) return set_err(ctx, SSCG_ERR_INVALID, "basis %d not supported", o->basis);
+    if (o->basis != SSCG_BASIS_MONOMIAL)
+        return set_err(ctx, SSCG_ERR_INVALID, "the moment recurrence needs the monomial basis");
     if (mat->prec != SSCG_PREC_NONE && mat->prec != SSCG_PREC_JACOBI)
         return set_err(ctx, SSCG_ERR_INVALID, "preconditioner %d not supported by this solver", mat->prec);
     return 0;

@@ -1,0 +1,465 @@
+// The s-step method with Gram blocks formed directly (Section II-A:
+// W_i = P_i^T A P_i, W_{i-1} beta_{i-1} + c_i = 0, W_i alpha_i = m_i), for
+// any polynomial basis of the Krylov block and any preconditioner.  It is
+// the path for the Chebyshev basis (Section IV names it as the stable
+// alternative to the monomial basis) and for the Chebyshev polynomial
+// preconditioner; the monomial basis with a diagonal preconditioner also
+// runs here on request (SSCG_DIRECT_GRAM), as a cross-check of the moment
+// recurrence.
+//
+// Per outer step:
+//   s x k_level_gen : AU_j = A u_j; u_{j+1} from B^-1 AU_j by the basis
+//                     recurrence (fused when B is diagonal, otherwise after
+//                     the preconditioner kernels)
+//   1 x k_gram      : G = U^T AU (lower triangle), m = U^T r,
+//                     C = (A P_old)^T U, from a shared-memory tile of the
+//                     block; the last CTA reduces them and solves
+//                     W_old beta = -C, W = G + C^T beta, W alpha = m
+//   1 x k_update    : the block updates of Algorithm 3
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+#include "kernels.cuh"
+#include "prec.cuh"
+#include "small.cuh"
+#include "spmv.cuh"
+
+namespace sscg {
+
+namespace {
+
+// Basis recurrence coefficients: monomial u_{j+1} = w; Chebyshev
+// u_2 = (w - c u_1)/delta, u_{j+1} = 2 (w - c u_j)/delta - u_{j-1}.
+struct Basis {
+    int cheb;
+    double c, delta;
+};
+
+template <class A>
+__device__ __forceinline__ typename A::R basis_next(const Basis& B, int j, typename A::R w,
+                                                    const typename A::S* uj, const typename A::S* ujm1, int row) {
+    if (!B.cheb) return w;
+    typename A::R t = A::sub(w, A::mul(A::from_d(B.c), A::ld(uj + row)));
+    if (j == 0) return A::mul(t, A::from_d(1.0 / B.delta));
+    return A::sub(A::mul(t, A::from_d(2.0 / B.delta)), A::ld(ujm1 + row));
+}
+
+// AU_j = A u_j; with a diagonal preconditioner also u_{j+1}.
+template <class A, int VM>
+__global__ void __launch_bounds__(kThreads) k_level_gen(MatView M, const typename A::S* __restrict__ dinv,
+                                                        const typename A::S* __restrict__ u_in,
+                                                        const typename A::S* __restrict__ u_prev,
+                                                        typename A::S* __restrict__ au_out,
+                                                        typename A::S* __restrict__ u_next, int j, Basis B,
+                                                        int diag_prec, const Ctrl* ctrl) {
+    using R = typename A::R;
+    if (ctrl_done(ctrl)) return;
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int s_rp[kTileRows + 1];
+    const int ntiles = (M.n + kTileRows - 1) / kTileRows;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        R y;
+        int row;
+        if (tile_spmv<A, VM>(M, tile, [&](int c) { return A::ldg(u_in + c); }, y, row, smem, s_rp)) {
+            A::st(au_out + row, y);
+            if (u_next && diag_prec) {
+                R w = dinv ? A::mul(A::ld(dinv + row), y) : y;
+                A::st(u_next + row, basis_next<A>(B, j, w, u_in, u_prev, row));
+            }
+        }
+    }
+}
+
+// u_{j+1} from w = B^-1 A u_j (general preconditioner).
+template <class A>
+__global__ void __launch_bounds__(kThreads) k_combine(int n, const typename A::S* __restrict__ w,
+                                                      const typename A::S* __restrict__ u_in,
+                                                      const typename A::S* __restrict__ u_prev,
+                                                      typename A::S* __restrict__ u_next, int j, Basis B,
+                                                      const Ctrl* ctrl) {
+    if (ctrl_done(ctrl)) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        A::st(u_next + i, basis_next<A>(B, j, A::ld(w + i), u_in, u_prev, i));
+}
+
+// Gram entries: e < ng: G(i, j), i >= j (u_i . AU_j); then m(i) (u_i . r);
+// then C(l, j) ((A p_l^old) . u_j) when a previous block exists.
+struct GramShape {
+    int s, ng, nm, nc, E, ncols;
+};
+
+__host__ __device__ inline GramShape gram_shape(int s, int has_old) {
+    GramShape g;
+    g.s = s;
+    g.ng = s * (s + 1) / 2;
+    g.nm = s;
+    g.nc = has_old ? s * s : 0;
+    g.E = g.ng + g.nm + g.nc;
+    g.ncols = 2 * s + 1 + (has_old ? s : 0);
+    return g;
+}
+
+// Columns staged per tile: U_0..U_{s-1}, AU_0..AU_{s-1}, r, AP_old_0..AP_old_{s-1}.
+__device__ __forceinline__ void gram_entry(const GramShape& g, int e, int& a, int& b) {
+    const int s = g.s;
+    if (e < g.ng) {  // lower-triangle index -> (i, j), i >= j
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= e) i++;
+        int j = e - i * (i + 1) / 2;
+        a = i;
+        b = s + j;
+    } else if (e < g.ng + g.nm) {
+        a = e - g.ng;
+        b = 2 * s;
+    } else {
+        int q = e - g.ng - g.nm;
+        int l = q % s, j = q / s;
+        a = 2 * s + 1 + l;
+        b = j;
+    }
+}
+
+constexpr int kGramTile = 128;  // rows staged per tile
+
+template <class A, int SB>
+__global__ void __launch_bounds__(kThreads) k_gram(int n, int ldn, int s, const typename A::S* __restrict__ blk_new,
+                                                   const typename A::S* __restrict__ r,
+                                                   const typename A::S* __restrict__ blk_old, int has_old,
+                                                   double* __restrict__ part, int step, Ctrl* ctrl) {
+    using R = typename A::R;
+    using S = typename A::S;
+    if (ctrl_done(ctrl)) return;
+    extern __shared__ __align__(16) char smem[];
+    S* tile = reinterpret_cast<S*>(smem);  // [ncols][kGramTile + 1]
+    constexpr int LD = kGramTile + 1;
+    const GramShape g = gram_shape(s, has_old);
+    // thread -> (entry, row group); entries beyond the thread count loop
+    const int groups = g.E >= kThreads ? 1 : kThreads / g.E;
+    const int active = g.E >= kThreads ? kThreads : g.E * groups;
+    constexpr int kMaxEPT = (SB * (SB + 1) / 2 + SB + SB * SB + kThreads - 1) / kThreads;
+    int ea[kMaxEPT], eb[kMaxEPT];
+    R acc[kMaxEPT];
+    const int grp = threadIdx.x / (g.E >= kThreads ? kThreads : g.E);
+    const int e0 = threadIdx.x % (g.E >= kThreads ? kThreads : g.E);
+#pragma unroll
+    for (int q = 0; q < kMaxEPT; q++) {
+        acc[q] = A::zero();
+        int e = e0 + q * kThreads;
+        if (e < g.E) gram_entry(g, e, ea[q], eb[q]);
+        else ea[q] = eb[q] = 0;
+    }
+    const size_t ld = (size_t)ldn;
+    const int ntiles = (n + kGramTile - 1) / kGramTile;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int r0 = t * kGramTile;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < g.ncols * kGramTile; idx += blockDim.x) {
+            int c = idx / kGramTile, i = idx % kGramTile, row = r0 + i;
+            const S* src;
+            if (c < 2 * s) src = blk_new + c * ld;
+            else if (c == 2 * s) src = r;
+            else src = blk_old + (s + (c - 2 * s - 1)) * ld;
+            S v;
+            if (row < n) v = src[row];
+            else memset(&v, 0, sizeof(S));
+            tile[c * LD + i] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < active) {
+#pragma unroll
+            for (int q = 0; q < kMaxEPT; q++) {
+                if (e0 + q * kThreads >= g.E) break;
+                const S* ta = tile + ea[q] * LD;
+                const S* tb = tile + eb[q] * LD;
+                R a = acc[q];
+                for (int i = grp; i < kGramTile; i += groups) a = A::fma(A::ld(ta + i), A::ld(tb + i), a);
+                acc[q] = a;
+            }
+        }
+    }
+    // combine the row groups of each entry, then one partial per entry
+    __syncthreads();
+    double* red = reinterpret_cast<double*>(smem);  // kThreads doubles (tile is free now)
+    const int G = gridDim.x;
+#pragma unroll
+    for (int q = 0; q < kMaxEPT; q++) {
+        red[threadIdx.x] = (threadIdx.x < active) ? A::to_d(acc[q]) : 0.0;
+        __syncthreads();
+        int e = e0 + q * kThreads;
+        if (grp == 0 && threadIdx.x < active && e < g.E) {
+            double t = 0.0;
+            for (int gg = 0; gg < groups; gg++) t += red[e0 + gg * (g.E >= kThreads ? kThreads : g.E)];
+            part[(size_t)e * G + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+    if (!last_cta(&ctrl->ticket[1])) return;
+    cta_sum_rows(part, g.E, G, [&](int e, double v) {
+        int a, b;
+        gram_entry(g, e, a, b);
+        if (e < g.ng) {
+            int i = a, j = b - s;
+            ctrl->G[i + j * s] = v;
+            ctrl->G[j + i * s] = v;
+        } else if (e < g.ng + g.nm) {
+            ctrl->m[a] = v;
+        } else {
+            int l = a - 2 * s - 1, j = b;
+            ctrl->C[l + j * s] = v;
+        }
+    });
+    SmallScratch* sc = reinterpret_cast<SmallScratch*>(smem);
+    if (threadIdx.x < 32) {
+        int st = warp_sw_gram(ctrl, s, step, sc);
+        if (threadIdx.x == 0 && st != 0) {
+            ctrl->status = st;
+            ctrl->done = 1;
+        }
+    }
+}
+
+struct GLayout {
+    int64_t ldn;
+    Ctrl* ctrl;
+    double* hist;
+    double* part;
+    void* blk[2];
+    void* r;
+    void* xw;
+    void* w;
+    void* tmp;
+    double* bdev;
+    double* xdev;
+    size_t bytes;
+};
+
+GLayout gplan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t cap) {
+    GLayout L{};
+    L.ldn = (int64_t)align_up((size_t)mat->n, 64);
+    Carve c(base, cap);
+    L.ctrl = c.take<Ctrl>(1);
+    L.hist = c.take<double>((size_t)o->maxit + 2);
+    GramShape gs = gram_shape(o->s, 1);
+    L.part = c.take<double>((size_t)G * std::max(gs.E, 4));
+    size_t blk = (size_t)L.ldn * 2 * o->s;
+    L.blk[0] = c.take<double>(blk);
+    L.blk[1] = c.take<double>(blk);
+    L.r = c.take<double>((size_t)L.ldn);
+    L.xw = (o->arith == SSCG_ARITH_F64) ? nullptr : c.take<double>((size_t)L.ldn);
+    L.w = c.take<double>((size_t)L.ldn);
+    L.tmp = c.take<double>((size_t)L.ldn * 3);
+    if (o->flags & SSCG_HOST_VECTORS) {
+        L.bdev = c.take<double>((size_t)L.ldn);
+        L.xdev = c.take<double>((size_t)L.ldn);
+    }
+    L.bytes = c.used;
+    return L;
+}
+
+template <class A, int VM, int SB>
+int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o, const GLayout& L,
+             const typename A::S* dinv, Basis basis, Ctrl* hctrl, Prof& P) {
+    using S = typename A::S;
+    cudaStream_t st = ctx->stream;
+    const int n = (int)mat->n, s = o->s;
+    int cap = std::min(8192, std::max(32, mat->max_tile_nnz));
+    cap = (cap + 31) / 32 * 32;
+    MatView M;
+    M.n = n;
+    M.cap = cap;
+    M.rowptr = mat->rowptr;
+    M.col = mat->col;
+    M.val = mat->val;
+    M.vhi = mat->vhi;
+    M.vlo = mat->vlo;
+    const size_t smem = std::max(stage_bytes<A, VM>(cap), sizeof(SmallScratch));
+    const size_t smem64 = stage_bytes<ArithF64, VAL_F64>(cap);
+    const GramShape gs_full = gram_shape(s, 1);
+    const size_t smem_gram = std::max({(size_t)gs_full.ncols * (kGramTile + 1) * sizeof(S), sizeof(SmallScratch),
+                                       (size_t)kThreads * sizeof(double)});
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_level_gen<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_cheb_step<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_gram<A, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gram));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_true_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
+    const int Gi = occupancy_grid(ctx, k_init<A, VM>, smem, n);
+    const int Gl = occupancy_grid(ctx, k_level_gen<A, VM>, smem, n);
+    const int Gg = occupancy_grid(ctx, k_gram<A, SB>, smem_gram, n);
+    const int Gu = occupancy_grid(ctx, k_update<A, SB>, 0, n);
+    const int Ge = occupancy_grid(ctx, k_combine<A>, 0, n);
+    const int Gt = occupancy_grid(ctx, k_true_res, smem64, n);
+    const bool diag = mat->prec != SSCG_PREC_CHEB;
+    ChebPrec<A, VM> cheb(diag ? 1 : mat->degree, diag ? 1.0 : mat->plmin, diag ? 2.0 : mat->plmax);
+    const size_t ld = (size_t)L.ldn;
+    S* blk[2] = {(S*)L.blk[0], (S*)L.blk[1]};
+    S* r = (S*)L.r;
+    S* xw = A::kind == 0 ? (S*)x : (S*)L.xw;
+    S* w = (S*)L.w;
+    S* tmp = (S*)L.tmp;
+    const S* dvec = dinv;  // Jacobi scaling (null: B = I); the Chebyshev preconditioner scales by D^-1 too
+
+    P.begin();
+    k_init<A, VM><<<Gi, kThreads, smem, st>>>(M, dvec, b, x, A::kind == 0 ? nullptr : xw, r, diag ? blk[0] : nullptr,
+                                              L.part, L.ctrl, L.hist);
+    if (!diag) P.launches += cheb.apply(M, dvec, r, blk[0], tmp, ld, Ge, Gl, smem, st, L.ctrl);
+    P.end(FAM_INIT, 0);
+    SSCG_CUDA(ctx, cudaGetLastError());
+
+    const int per_chunk = std::max(1, 32 / (s + 2));
+    cudaEvent_t ev[2];
+    SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    int launched = 0, chunk = 0, pending = -1, err = 0;
+    while (launched < o->maxit) {
+        int c = std::min(per_chunk, o->maxit - launched);
+        for (int q = 0; q < c; q++) {
+            const int k = launched + q;
+            S* bn = blk[k & 1];
+            S* bo = blk[(k + 1) & 1];
+            P.begin();
+            for (int j = 0; j < s; j++) {
+                S* unext = j + 1 < s ? bn + (j + 1) * ld : nullptr;
+                const S* uprev = j > 0 ? bn + (j - 1) * ld : nullptr;
+                k_level_gen<A, VM><<<Gl, kThreads, smem, st>>>(M, dvec, bn + j * ld, uprev, bn + (s + j) * ld, unext,
+                                                               j, basis, diag ? 1 : 0, L.ctrl);
+                if (!diag && unext) {
+                    P.launches += cheb.apply(M, dvec, bn + (s + j) * ld, w, tmp, ld, Ge, Gl, smem, st, L.ctrl);
+                    k_combine<A><<<Ge, kThreads, 0, st>>>(n, w, bn + j * ld, uprev, unext, j, basis, L.ctrl);
+                    P.launches++;
+                }
+                if (j + 1 < s) P.launches++;
+            }
+            P.end(FAM_MPK, k);
+            P.begin();
+            k_gram<A, SB><<<Gg, kThreads, smem_gram, st>>>(n, (int)L.ldn, s, bn, r, bo, k > 0 ? 1 : 0, L.part, k,
+                                                             L.ctrl);
+            P.end(FAM_DIR, k);
+            P.begin();
+            k_update<A, SB><<<Gu, kThreads, 0, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dvec, L.part, k == 0,
+                                                     diag ? 1 : 0, L.ctrl, L.hist);
+            if (!diag) P.launches += cheb.apply(M, dvec, r, bo, tmp, ld, Ge, Gl, smem, st, L.ctrl);
+            P.end(FAM_UPDATE, k);
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+            err = 1;
+            break;
+        }
+        launched += c;
+        const int slot = chunk & 1;
+        SSCG_CUDA(ctx, cudaMemcpyAsync((void*)(ctx->pinned + slot), &L.ctrl->done, sizeof(int),
+                                       cudaMemcpyDeviceToHost, st));
+        SSCG_CUDA(ctx, cudaEventRecord(ev[slot], st));
+        if (pending >= 0) {
+            SSCG_CUDA(ctx, cudaEventSynchronize(ev[pending & 1]));
+            if (ctx->pinned[pending & 1]) break;
+        }
+        pending = chunk++;
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (err) return set_err(ctx, SSCG_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    P.begin();
+    if (A::kind != 0) k_export_x<A><<<Ge, kThreads, 0, st>>>(n, xw, x, L.ctrl);
+    else k_zero_if_zero_rhs<<<Ge, kThreads, 0, st>>>(n, x, L.ctrl);
+    k_true_res<<<Gt, kThreads, smem64, st>>>(M, b, x, L.part, L.ctrl);
+    P.end(FAM_FINAL, 0);
+    P.launches++;
+    SSCG_CUDA(ctx, cudaGetLastError());
+    SSCG_CUDA(ctx, cudaMemcpyAsync(hctrl, L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    SSCG_CUDA(ctx, cudaStreamSynchronize(st));
+    return 0;
+}
+
+}  // namespace
+
+int gram_workspace(const sscg_mat* mat, const sscg_opts* o, size_t* bytes) {
+    *bytes = gplan(mat, o, 8 * 160, nullptr, 0).bytes;
+    return 0;
+}
+
+int solve_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o,
+               sscg_info* info, void* ws, size_t ws_bytes, double blo, double bhi) {
+    size_t need = 0;
+    gram_workspace(mat, o, &need);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255))
+        return set_err(ctx, SSCG_ERR_SPACE, "workspace needs %zu bytes, 256-byte aligned (got %zu)", need, ws_bytes);
+    GLayout L = gplan(mat, o, 8 * 160, ws, ws_bytes);
+    cudaStream_t st = ctx->stream;
+    const int64_t n = mat->n;
+    const double* bd = b;
+    double* xd = x;
+    if (o->flags & SSCG_HOST_VECTORS) {
+        SSCG_CUDA(ctx, cudaMemcpyAsync(L.bdev, b, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        SSCG_CUDA(ctx, cudaMemcpyAsync(L.xdev, x, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        bd = L.bdev;
+        xd = L.xdev;
+    }
+    Ctrl h;
+    memset(&h, 0, sizeof(h));
+    h.status = 1;
+    h.maxit = o->maxit;
+    h.s = o->s;
+    h.tol = o->tol;
+    SSCG_CUDA(ctx, cudaMemcpyAsync(L.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    Basis basis;
+    basis.cheb = o->basis == SSCG_BASIS_CHEBYSHEV;
+    basis.c = 0.5 * (bhi + blo);
+    basis.delta = 0.5 * (bhi - blo);
+    if (basis.cheb && !(basis.delta > 0.0)) return set_err(ctx, SSCG_ERR_INVALID, "empty Chebyshev basis interval");
+    const int s = o->s;
+    Prof* prof = new Prof(ctx, (o->flags & SSCG_PROFILE) != 0);
+    if (!prof->reserve((int)std::min<int64_t>(65536, (int64_t)o->maxit * 3 + 64))) {
+        delete prof;
+        return set_err(ctx, SSCG_ERR_CUDA, "could not create profiling events");
+    }
+    const bool scale = mat->prec != SSCG_PREC_NONE;  // Jacobi and Chebyshev scale by D^-1
+    int rc;
+    if (o->arith == SSCG_ARITH_F64) {
+        const double* d = scale ? mat->dinv : nullptr;
+        if (s <= 4) rc = run_gram<ArithF64, VAL_F64, 4>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+        else if (s <= 8) rc = run_gram<ArithF64, VAL_F64, 8>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+        else rc = run_gram<ArithF64, VAL_F64, 16>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+    } else {
+        const float2* d = scale ? mat->dinv_df : nullptr;
+        if (mat->exact_fp32) {
+            if (s <= 4) rc = run_gram<ArithDF64, VAL_F32, 4>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+            else if (s <= 8) rc = run_gram<ArithDF64, VAL_F32, 8>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+            else rc = run_gram<ArithDF64, VAL_F32, 16>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+        } else {
+            if (s <= 4) rc = run_gram<ArithDF64, VAL_DF, 4>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+            else if (s <= 8) rc = run_gram<ArithDF64, VAL_DF, 8>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+            else rc = run_gram<ArithDF64, VAL_DF, 16>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+        }
+    }
+    if (rc) {
+        delete prof;
+        return rc;
+    }
+    if (o->flags & SSCG_HOST_VECTORS) {
+        SSCG_CUDA(ctx, cudaMemcpyAsync(x, L.xdev, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        SSCG_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    if (h.status == SSCG_ERR_NONFINITE) {
+        delete prof;
+        return set_err(ctx, SSCG_ERR_NONFINITE, "non-finite right-hand side or x0");
+    }
+    if (info) fill_profile(info, *prof, h.step);
+    delete prof;
+    if (info) {
+        info->status = h.status;
+        info->outer_iters = h.step;
+        info->equiv_iters = (int64_t)h.step * s;
+        info->rel_res_recursive = h.relres;
+        info->rel_res_true = h.zero_rhs ? 0.0 : sqrt(h.true_res2) / h.bnorm;
+        int len = std::min(h.nhist, info->hist_cap);
+        if (info->hist && len > 0)
+            SSCG_CUDA(ctx, cudaMemcpy(info->hist, L.hist, len * sizeof(double), cudaMemcpyDeviceToHost));
+        info->hist_len = info->hist ? len : 0;
+    }
+    return h.status;
+}
+
+}  // namespace sscg

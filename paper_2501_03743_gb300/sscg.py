@@ -29,7 +29,7 @@ EXPORTS = (
     "sscg_create", "sscg_destroy", "sscg_last_error", "sscg_status_str", "sscg_version",
     "sscg_mat_storage_bytes", "sscg_mat_create_csr", "sscg_mat_destroy", "sscg_mat_props_get",
     "sscg_set_preconditioner", "sscg_solve_workspace_bytes", "sscg_solve", "sscg_pcg_workspace_bytes",
-    "sscg_pcg_solve", "sscg_spmv",
+    "sscg_pcg_solve", "sscg_spmv", "sscg_bounds_workspace_bytes", "sscg_estimate_bounds", "sscg_uniform",
 )
 
 
@@ -93,6 +93,9 @@ def load(path: str | None = None):
     L.sscg_pcg_workspace_bytes.argtypes = [vp, P(Opts), P(sz)]
     L.sscg_pcg_solve.argtypes = [vp, vp, vp, vp, P(Opts), P(Info), vp, sz]
     L.sscg_spmv.argtypes = [vp, vp, vp, vp]
+    L.sscg_bounds_workspace_bytes.argtypes = [vp, i32, P(sz)]
+    L.sscg_estimate_bounds.argtypes = [vp, vp, i32, vp, vp, sz, P(dbl), P(dbl)]
+    L.sscg_uniform.argtypes = [vp, i64, C.c_uint64, vp]
     _lib = L
     return L
 
@@ -132,6 +135,13 @@ class Context:
         if rc != OK:
             raise SscgError(rc, "sscg_create failed (no sm_103a device?)")
         self.h = h
+
+    def uniform(self, n, seed):
+        """Device U[-1, 1) vector: splitmix64 draws 0..n-1 from `seed`."""
+        torch = _torch()
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.check(self.lib.sscg_uniform(self.h, n, seed, C.c_void_p(out.data_ptr())))
+        return out
 
     def check(self, rc, allow_positive=False):
         if rc < 0 or (rc > 0 and not allow_positive):
@@ -187,6 +197,18 @@ class Matrix:
         self.ctx.check(self.ctx.lib.sscg_set_preconditioner(self.h, PREC[kind], int(degree), float(lmin), float(lmax)))
         self.prec = kind
 
+    def estimate_bounds(self, steps=20, r0=None):
+        """Extreme Ritz values of B^-1 A from `steps` Lanczos (CG) steps."""
+        torch = _torch()
+        nbytes = C.c_size_t()
+        self.ctx.check(self.ctx.lib.sscg_bounds_workspace_bytes(self.h, steps, C.byref(nbytes)))
+        ws = torch.empty(nbytes.value, dtype=torch.uint8, device=self.storage.device)
+        lo, hi = C.c_double(), C.c_double()
+        rp = C.c_void_p(r0.contiguous().data_ptr()) if r0 is not None else None
+        self.ctx.check(self.ctx.lib.sscg_estimate_bounds(self.ctx.h, self.h, steps, rp, C.c_void_p(ws.data_ptr()),
+                                                         nbytes.value, C.byref(lo), C.byref(hi)))
+        return lo.value, hi.value
+
     def spmv(self, x):
         torch = _torch()
         x = x.contiguous()
@@ -206,9 +228,12 @@ class Matrix:
             pass
 
 
+DIRECT_GRAM = 0x4
+
+
 def make_opts(s=4, basis="monomial", tol=1e-8, maxit=1000, arith="df64", basis_bounds=(0.0, 0.0),
-              replace_every=0, host_vectors=False, profile=False) -> Opts:
-    flags = (HOST_VECTORS if host_vectors else 0) | (PROFILE if profile else 0)
+              replace_every=0, host_vectors=False, profile=False, direct_gram=False) -> Opts:
+    flags = (HOST_VECTORS if host_vectors else 0) | (PROFILE if profile else 0) | (DIRECT_GRAM if direct_gram else 0)
     return Opts(int(s), BASIS[basis], float(basis_bounds[0]), float(basis_bounds[1]), float(tol), int(maxit),
                 ARITH[arith], int(replace_every), flags)
 
