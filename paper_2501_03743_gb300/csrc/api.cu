@@ -404,8 +404,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv_f64(MatView M, const double* 
 }
 
 int spmv_f64(sscg_ctx* ctx, const sscg_mat* m, const double* x, double* y) {
-    int cap = std::min(8192, std::max(32, m->max_tile_nnz));
-    cap = (cap + 31) / 32 * 32;
+    const int cap = stage_cap(m);
     MatView M;
     M.n = (int)m->n;
     M.cap = cap;

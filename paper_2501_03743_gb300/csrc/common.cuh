@@ -203,11 +203,12 @@ __device__ __forceinline__ typename A::R warp_sum(typename A::R v) {
     return v;
 }
 
-// Sum NV values over the CTA (blockDim.x == kThreads); the result is
-// returned as doubles in thread 0.  `sh` holds NV * (kThreads/32) doubles.
+// Sum NV values over the CTA (blockDim.x a multiple of 32, at most
+// kThreads); the result is returned as doubles in thread 0.  `sh` holds
+// NV * (kThreads/32) doubles.
 template <class A, int NV>
 __device__ __forceinline__ void block_sum(typename A::R (&v)[NV], double* sh, double (&out)[NV]) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NV; q++) {
         typename A::R w = warp_sum<A>(v[q]);
@@ -218,7 +219,7 @@ __device__ __forceinline__ void block_sum(typename A::R (&v)[NV], double* sh, do
 #pragma unroll
         for (int q = 0; q < NV; q++) {
             double t = 0.0;
-            for (int w = 0; w < kThreads / 32; w++) t += sh[q * (kThreads / 32) + w];
+            for (int w = 0; w < nw; w++) t += sh[q * (kThreads / 32) + w];
             out[q] = t;
         }
     }

@@ -103,6 +103,15 @@ inline int occupancy_grid(const sscg_ctx* ctx, K kernel, size_t smem, int64_t ro
     return grid_for(ctx, rows, per_sm);
 }
 
+// Entries of a matrix row tile staged in shared memory: the largest tile's
+// count plus 8 for the 16-byte widening of bulk copies, capped at 8192.
+inline int stage_cap(const sscg_mat* m) {
+    int cap = m->max_tile_nnz + 8;
+    if (cap > 8192) cap = 8192;
+    if (cap < 32) cap = 32;
+    return (cap + 31) / 32 * 32;
+}
+
 // Kernel-family timing for SSCG_PROFILE: events on the context's stream
 // around each launch, summed after the call for the steps actually taken.
 enum { FAM_INIT = 0, FAM_MPK = 1, FAM_UPDATE = 2, FAM_DIR = 3, FAM_FINAL = 4, FAM_COUNT = 5 };

@@ -105,20 +105,18 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv(MatView M, const typename
                                                        Ctrl* ctrl) {
     using R = typename A::R;
     if (done_of(ctrl)) return;
-    extern __shared__ __align__(16) char smem[];
-    __shared__ int s_rp[kTileRows + 1];
+    extern __shared__ __align__(16) char smem_raw[];
+    char* smem = align128(smem_raw);
     __shared__ double red[kThreads / 32];
-    const int ntiles = (M.n + kTileRows - 1) / kTileRows;
     R pq = A::zero();
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        R y;
-        int row;
-        bool live = tile_spmv<A, VM>(M, tile, [&](int c) { return A::ldg(p + c); }, y, row, smem, s_rp);
-        if (live) {
+    const bool ok = spmv_pipe<A, VM, kStages>(
+        M, smem, [&](int c) { return A::ldg(p + c); },
+        [&](int row, R y) {
             A::st(q + row, y);
             pq = A::fma(A::ldg(p + row), y, pq);
-        }
-    }
+        },
+        ctrl);
+    if (!ok) return;
     R v[1] = {pq};
     double out[1];
     block_sum<A, 1>(v, red, out);
@@ -383,9 +381,8 @@ PLayout pplan(const sscg_mat* mat, int maxit, unsigned flags, void* base, size_t
 
 MatView view(const sscg_mat* mat) {
     MatView M;
-    int cap = std::min(8192, std::max(32, mat->max_tile_nnz));
     M.n = (int)mat->n;
-    M.cap = (cap + 31) / 32 * 32;
+    M.cap = stage_cap(mat);
     M.rowptr = mat->rowptr;
     M.col = mat->col;
     M.val = mat->val;
@@ -404,12 +401,13 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int 
     const int n = (int)mat->n;
     const MatView M = view(mat);
     const size_t smem = stage_bytes<A, VM>(M.cap), smem64 = stage_bytes<ArithF64, VAL_F64>(M.cap);
+    const size_t smem_pipe = pipe_bytes<VM, kStages>(M.cap) + 128;
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_spmv<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_cheb_step<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_spmv<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pipe));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_cheb_step<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pipe));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_true_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
     const int Gi = occupancy_grid(ctx, k_pcg_init<A, VM>, smem, n);
-    const int Gs = occupancy_grid(ctx, k_pcg_spmv<A, VM>, smem, n);
+    const int Gs = occupancy_grid(ctx, k_pcg_spmv<A, VM>, smem_pipe, n);
     const int Gu = occupancy_grid(ctx, k_pcg_update<A>, 0, n);
     const int Gd = occupancy_grid(ctx, k_pcg_dir<A>, 0, n);
     const int Gr = occupancy_grid(ctx, k_pcg_rho<A>, 0, n);
@@ -428,7 +426,7 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int 
     k_pcg_init<A, VM><<<Gi, kThreads, smem, st>>>(M, dinv, diag ? 1 : 0, b, x, (A::kind == 0 && x) ? nullptr : xw,
                                                   r, p, L.part, L.ctrl, L.hist);
     if (!diag) {
-        P.launches += cheb.apply(M, dinv, r, p, tmp, ld, Gd, Gs, smem, st, L.ctrl);
+        P.launches += cheb.apply(M, dinv, r, p, tmp, ld, Gd, Gs, smem_pipe, st, L.ctrl);
         k_pcg_rho<A><<<Gr, kThreads, 0, st>>>(n, r, p, 1, L.part, L.ctrl, coef);
         P.launches++;
     }
@@ -444,7 +442,7 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int 
         for (int k = 0; k < c; k++) {
             const int it = launched + k;
             P.begin();
-            k_pcg_spmv<A, VM><<<Gs, kThreads, smem, st>>>(M, p, q, L.part, L.ctrl);
+            k_pcg_spmv<A, VM><<<Gs, kThreads, smem_pipe, st>>>(M, p, q, L.part, L.ctrl);
             P.end(FAM_MPK, it);
             P.begin();
             k_pcg_update<A><<<Gu, kThreads, 0, st>>>(n, diag ? 1 : 0, xw, r, p, q, dinv, L.part, L.ctrl, L.hist,
@@ -452,7 +450,7 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int 
             P.end(FAM_UPDATE, it);
             P.begin();
             if (!diag) {
-                P.launches += cheb.apply(M, dinv, r, u, tmp, ld, Gd, Gs, smem, st, L.ctrl);
+                P.launches += cheb.apply(M, dinv, r, u, tmp, ld, Gd, Gs, smem_pipe, st, L.ctrl);
                 k_pcg_rho<A><<<Gr, kThreads, 0, st>>>(n, r, u, 0, L.part, L.ctrl, coef);
                 P.launches++;
             }

@@ -47,21 +47,19 @@ __global__ void __launch_bounds__(kThreads) k_cheb_step(MatView M, const typenam
                                                         double c1, double c2, const Ctrl* ctrl) {
     using R = typename A::R;
     if (ctrl && __ldcg(&ctrl->done)) return;
-    extern __shared__ __align__(16) char smem[];
-    __shared__ int s_rp[kTileRows + 1];
-    const int ntiles = (M.n + kTileRows - 1) / kTileRows;
+    extern __shared__ __align__(16) char smem_raw[];
+    char* smem = align128(smem_raw);
     const R C1 = A::from_d(c1), C2 = A::from_d(c2);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        R q;
-        int row;
-        if (tile_spmv<A, VM>(M, tile, [&](int c) { return A::ldg(d_in + c); }, q, row, smem, s_rp)) {
+    spmv_pipe<A, VM, kStages>(
+        M, smem, [&](int c) { return A::ldg(d_in + c); },
+        [&](int row, R q) {
             R rs = A::sub(A::ld(res + row), A::mul(A::ld(dinv + row), q));
             R dn = A::fma(C1, A::ldg(d_in + row), A::mul(C2, rs));
             A::st(res + row, rs);
             A::st(d_out + row, dn);
             A::st(z + row, A::add(A::ld(z + row), dn));
-        }
-    }
+        },
+        const_cast<Ctrl*>(ctrl));
 }
 
 // Host side: launch the kernels of one apply z = B^-1 v on `st`.

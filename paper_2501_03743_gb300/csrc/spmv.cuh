@@ -90,4 +90,190 @@ __device__ __forceinline__ bool tile_spmv(const MatView& M, int tile, XF xf, typ
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// TMA-pipelined row tiles.
+//
+// Each CTA walks its tiles (blockIdx.x, +gridDim.x, ...) through NS shared
+// memory stages.  Thread 0 fills a stage with three (four for double-float
+// values) 1-D bulk copies, cp.async.bulk global -> shared, completing on the
+// stage's mbarrier: the tile's row pointers, and the column indices and
+// values of its contiguous entry range, widened to 16-byte boundaries (the
+// matrix storage carries 16 entries of slack after every array, so the
+// widened range never leaves it).  While the CTA computes tile k the copies
+// of tiles k+1 .. k+NS-1 are in flight.  Every wait is bounded by
+// %globaltimer; on expiry the kernel records SSCG_TIMEOUT, waits (bounded)
+// for its own outstanding copies and returns.
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded waits give up after 2 s
+constexpr int kStages = 2;                        // pipeline depth of the SpMV kernels
+
+// Dynamic shared memory rounded up to a 128-byte boundary (callers size the
+// allocation with 128 bytes of slack).
+__device__ __forceinline__ char* align128(char* p) {
+    return p + ((128u - (smem_u32(p) & 127u)) & 127u);
+}
+
+// Wait for the phase of `bar` with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (unsigned it = 1; it < (1u << 30); it++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0 && globaltimer() - t0 > kWaitLimitNs) return false;
+    }
+    return false;
+}
+
+// Bytes per element of the value arrays a stage holds (second array: the
+// low part of double-float values).
+template <int VM>
+__host__ __device__ constexpr int val0_bytes() { return VM == VAL_F64 ? 8 : 4; }
+template <int VM>
+__host__ __device__ constexpr int val1_bytes() { return VM == VAL_DF ? 4 : 0; }
+
+constexpr int kPipeRp = kTileRows + 4;  // row-pointer slots per stage (multiple of 4)
+
+template <int VM>
+__host__ __device__ constexpr size_t pipe_stage_bytes(int cap) {
+    return (size_t)kPipeRp * 4 + (size_t)cap * (4 + val0_bytes<VM>() + val1_bytes<VM>());
+}
+
+template <int VM, int NS>
+__host__ __device__ constexpr size_t pipe_bytes(int cap) {
+    return 16 * ((NS * 8 + 15) / 16) + NS * pipe_stage_bytes<VM>(cap);
+}
+
+template <class A, int VM>
+__device__ __forceinline__ typename Val<A, VM>::T stage_val(const char* v0, const char* v1, int k);
+
+template <>
+__device__ __forceinline__ double stage_val<ArithF64, VAL_F64>(const char* v0, const char*, int k) {
+    return reinterpret_cast<const double*>(v0)[k];
+}
+template <>
+__device__ __forceinline__ float stage_val<ArithDF64, VAL_F32>(const char* v0, const char*, int k) {
+    return reinterpret_cast<const float*>(v0)[k];
+}
+template <>
+__device__ __forceinline__ float2 stage_val<ArithDF64, VAL_DF>(const char* v0, const char* v1, int k) {
+    return make_float2(reinterpret_cast<const float*>(v0)[k], reinterpret_cast<const float*>(v1)[k]);
+}
+
+// Runs epi(row, y) with y = (A x)[row] for every row of this CTA's tiles.
+// M.cap (a multiple of 4) is the entries a stage holds.  Every thread of the
+// CTA must call it; `smem` holds pipe_bytes<VM, NS>(M.cap).  Returns false
+// after a timeout (recorded in ctrl).
+template <class A, int VM, int NS, class XF, class EPI>
+__device__ __forceinline__ bool spmv_pipe(const MatView& M, char* smem, XF xf, EPI epi, Ctrl* ctrl) {
+    using V = Val<A, VM>;
+    const int cap = M.cap;
+    const int ntiles = (M.n + kTileRows - 1) / kTileRows;
+    const int G = gridDim.x;
+    const int my = (int)blockIdx.x < ntiles ? (ntiles - (int)blockIdx.x + G - 1) / G : 0;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    char* stage0 = smem + 16 * ((NS * 8 + 15) / 16);
+    const size_t sb = pipe_stage_bytes<VM>(cap);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NS; q++) mbar_init(&bar[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int k) {  // thread 0: tile k of this CTA into stage k % NS
+        const int t = (int)blockIdx.x + k * G, r0 = t * kTileRows, nrows = min(kTileRows, M.n - r0);
+        const int lo = __ldg(M.rowptr + r0), hi = __ldg(M.rowptr + r0 + nrows);
+        const int base = lo & ~3, end = min((hi + 3) & ~3, base + cap), cnt = end - base;
+        char* st = stage0 + (size_t)(k % NS) * sb;
+        const unsigned rpb = (unsigned)(((nrows + 1 + 3) & ~3) * 4);
+        const unsigned tx = rpb + (unsigned)cnt * (4 + val0_bytes<VM>() + val1_bytes<VM>());
+        uint64_t* b = &bar[k % NS];
+        fence_proxy_async();
+        mbar_arrive_expect_tx(b, tx);
+        bulk_g2s(st, M.rowptr + r0, rpb, b);
+        if (cnt > 0) {
+            char* cdst = st + kPipeRp * 4;
+            char* v0 = cdst + (size_t)cap * 4;
+            bulk_g2s(cdst, M.col + base, (unsigned)cnt * 4, b);
+            if (VM == VAL_F64) bulk_g2s(v0, M.val + base, (unsigned)cnt * 8, b);
+            else bulk_g2s(v0, M.vhi + base, (unsigned)cnt * 4, b);
+            if (VM == VAL_DF) bulk_g2s(v0 + (size_t)cap * 4, M.vlo + base, (unsigned)cnt * 4, b);
+        }
+    };
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NS - 1 && k < my; k++) issue(k);
+    for (int k = 0; k < my; k++) {
+        if (threadIdx.x == 0 && k + NS - 1 < my) issue(k + NS - 1);
+        const bool ok = __syncthreads_and(mbar_wait(&bar[k % NS], (unsigned)(k / NS) & 1u));
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                ctrl->status = 3;  // SSCG_TIMEOUT
+                __threadfence();
+                atomicExch(&ctrl->done, 1);
+                for (int q = k + 1; q < my && q < k + NS; q++) mbar_wait(&bar[q % NS], (unsigned)(q / NS) & 1u);
+            }
+            __syncthreads();
+            return false;
+        }
+        const char* st = stage0 + (size_t)(k % NS) * sb;
+        const int* s_rp = reinterpret_cast<const int*>(st);
+        const int32_t* s_col = reinterpret_cast<const int32_t*>(st + kPipeRp * 4);
+        const char* v0 = st + kPipeRp * 4 + (size_t)cap * 4;
+        const char* v1 = v0 + (size_t)cap * val0_bytes<VM>();
+        const int t = (int)blockIdx.x + k * G, r0 = t * kTileRows, nrows = min(kTileRows, M.n - r0);
+        const int base = s_rp[0] & ~3;
+        const int staged = min((s_rp[nrows] + 3) & ~3, base + cap) - base;
+        if ((int)threadIdx.x < nrows) {
+            const int ks = s_rp[threadIdx.x] - base, ke = s_rp[threadIdx.x + 1] - base;
+            const int km = min(ke, staged);
+            typename A::R y = A::zero();
+            for (int q = ks; q < km; q++) y = V::mac(y, stage_val<A, VM>(v0, v1, q), xf(s_col[q]));
+            for (int q = max(ks, staged); q < ke; q++) y = V::mac(y, V::load(M, base + q), xf(__ldg(M.col + base + q)));
+            epi(r0 + (int)threadIdx.x, y);
+        }
+        __syncthreads();  // stage k % NS may be refilled
+    }
+    return true;
+}
+
 }  // namespace sscg

@@ -39,17 +39,14 @@ __global__ void __launch_bounds__(kThreads) k_level(MatView M, const typename A:
                                                     int j, int s, int step, int last, Ctrl* ctrl) {
     using R = typename A::R;
     if (ctrl_done(ctrl)) return;
-    extern __shared__ __align__(16) char smem[];
-    __shared__ int s_rp[kTileRows + 1];
+    extern __shared__ __align__(16) char smem_raw[];
+    char* smem = align128(smem_raw);
     __shared__ double red[2 * (kThreads / 32)];
-    const int ntiles = (M.n + kTileRows - 1) / kTileRows;
     R m1 = A::zero(), m2 = A::zero();
     const bool want_m2 = (2 * j + 2) <= (2 * s - 1);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        R y;
-        int row;
-        bool live = tile_spmv<A, VM>(M, tile, [&](int c) { return A::ldg(u_in + c); }, y, row, smem, s_rp);
-        if (live) {
+    const bool ok = spmv_pipe<A, VM, kStages>(
+        M, smem, [&](int c) { return A::ldg(u_in + c); },
+        [&](int row, R y) {
             A::st(au_out + row, y);
             m1 = A::fma(A::ldg(u_in + row), y, m1);
             if (u_next || want_m2) {
@@ -57,8 +54,9 @@ __global__ void __launch_bounds__(kThreads) k_level(MatView M, const typename A:
                 if (u_next) A::st(u_next + row, z);
                 m2 = A::fma(y, z, m2);
             }
-        }
-    }
+        },
+        ctrl);
+    if (!ok) return;
     R v[2] = {m1, m2};
     double out[2];
     block_sum<A, 2>(v, red, out);
@@ -131,12 +129,6 @@ MatView view_of(const sscg_mat* m, int cap) {
     return v;
 }
 
-int staging_cap(const sscg_mat* m) {
-    int cap = m->max_tile_nnz;
-    if (cap > 8192) cap = 8192;
-    if (cap < 32) cap = 32;
-    return (cap + 31) / 32 * 32;
-}
 
 template <class A, int VM, int SB>
 int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o,
@@ -144,12 +136,13 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     using S = typename A::S;
     cudaStream_t st = ctx->stream;
     const int n = (int)mat->n, s = o->s, G = L.G;
-    const int cap = staging_cap(mat);
+    const int cap = stage_cap(mat);
     MatView M = view_of(mat, cap);
     const size_t smem = std::max(stage_bytes<A, VM>(cap), sizeof(SmallScratch));
+    const size_t smem_pipe = std::max(pipe_bytes<VM, kStages>(cap), sizeof(SmallScratch)) + 128;
     const size_t smem64 = stage_bytes<ArithF64, VAL_F64>(cap);
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_level<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_level<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pipe));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_true_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
     S* blk[2] = {(S*)L.blk[0], (S*)L.blk[1]};
     S* r = (S*)L.r;
@@ -158,8 +151,10 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
 
     P.begin();
     const int Gi = occupancy_grid(ctx, k_init<A, VM>, smem, n);
-    const int Gl = occupancy_grid(ctx, k_level<A, VM>, smem, n);
-    const int Gu = occupancy_grid(ctx, k_update<A, SB>, 0, n);
+    const int Gl = occupancy_grid(ctx, k_level<A, VM>, smem_pipe, n);
+    size_t smem_upd = 0;
+    int Gu = 0;
+    if (int e = update_tma_setup<A, SB>(ctx, n, s, &smem_upd, &Gu)) return e;
     const int Gt = occupancy_grid(ctx, k_true_res, smem64, n);
     k_init<A, VM><<<Gi, kThreads, smem, st>>>(M, dinv, b, x, A::kind == 0 ? nullptr : xw, r, blk[0], L.part,
                                               L.ctrl, L.hist);
@@ -180,14 +175,14 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
             S* bo = blk[(k + 1) & 1];
             for (int j = 0; j < s; j++) {
                 P.begin();
-                k_level<A, VM><<<Gl, kThreads, smem, st>>>(M, dinv, bn + j * ld, bn + (s + j) * ld,
+                k_level<A, VM><<<Gl, kThreads, smem_pipe, st>>>(M, dinv, bn + j * ld, bn + (s + j) * ld,
                                                           j + 1 < s ? bn + (j + 1) * ld : nullptr, L.part, j, s, k,
                                                           j == s - 1, L.ctrl);
                 P.end(FAM_MPK, k);
             }
             P.begin();
-            k_update<A, SB><<<Gu, kThreads, 0, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dinv, L.part, k == 0, 1,
-                                                     L.ctrl, L.hist);
+            k_update_tma<A, SB><<<Gu, kUpdRows, smem_upd, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dinv, L.part,
+                                                                k == 0, 1, L.ctrl, L.hist);
             P.end(FAM_UPDATE, k);
         }
         if (cudaGetLastError() != cudaSuccess) { err = 1; break; }

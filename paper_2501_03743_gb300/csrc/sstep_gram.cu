@@ -57,20 +57,18 @@ __global__ void __launch_bounds__(kThreads) k_level_gen(MatView M, const typenam
                                                         int diag_prec, const Ctrl* ctrl) {
     using R = typename A::R;
     if (ctrl_done(ctrl)) return;
-    extern __shared__ __align__(16) char smem[];
-    __shared__ int s_rp[kTileRows + 1];
-    const int ntiles = (M.n + kTileRows - 1) / kTileRows;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        R y;
-        int row;
-        if (tile_spmv<A, VM>(M, tile, [&](int c) { return A::ldg(u_in + c); }, y, row, smem, s_rp)) {
+    extern __shared__ __align__(16) char smem_raw[];
+    char* smem = align128(smem_raw);
+    spmv_pipe<A, VM, kStages>(
+        M, smem, [&](int c) { return A::ldg(u_in + c); },
+        [&](int row, R y) {
             A::st(au_out + row, y);
             if (u_next && diag_prec) {
                 R w = dinv ? A::mul(A::ld(dinv + row), y) : y;
                 A::st(u_next + row, basis_next<A>(B, j, w, u_in, u_prev, row));
             }
-        }
-    }
+        },
+        const_cast<Ctrl*>(ctrl));
 }
 
 // u_{j+1} from w = B^-1 A u_j (general preconditioner).
@@ -265,8 +263,7 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
     using S = typename A::S;
     cudaStream_t st = ctx->stream;
     const int n = (int)mat->n, s = o->s;
-    int cap = std::min(8192, std::max(32, mat->max_tile_nnz));
-    cap = (cap + 31) / 32 * 32;
+    const int cap = stage_cap(mat);
     MatView M;
     M.n = n;
     M.cap = cap;
@@ -277,18 +274,21 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
     M.vlo = mat->vlo;
     const size_t smem = std::max(stage_bytes<A, VM>(cap), sizeof(SmallScratch));
     const size_t smem64 = stage_bytes<ArithF64, VAL_F64>(cap);
+    const size_t smem_pipe = pipe_bytes<VM, kStages>(cap) + 128;
     const GramShape gs_full = gram_shape(s, 1);
     const size_t smem_gram = std::max({(size_t)gs_full.ncols * (kGramTile + 1) * sizeof(S), sizeof(SmallScratch),
                                        (size_t)kThreads * sizeof(double)});
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_level_gen<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_cheb_step<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_level_gen<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pipe));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_cheb_step<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pipe));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_gram<A, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gram));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_true_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
     const int Gi = occupancy_grid(ctx, k_init<A, VM>, smem, n);
-    const int Gl = occupancy_grid(ctx, k_level_gen<A, VM>, smem, n);
+    const int Gl = occupancy_grid(ctx, k_level_gen<A, VM>, smem_pipe, n);
     const int Gg = occupancy_grid(ctx, k_gram<A, SB>, smem_gram, n);
-    const int Gu = occupancy_grid(ctx, k_update<A, SB>, 0, n);
+    size_t smem_upd = 0;
+    int Gu = 0;
+    if (int e = update_tma_setup<A, SB>(ctx, n, s, &smem_upd, &Gu)) return e;
     const int Ge = occupancy_grid(ctx, k_combine<A>, 0, n);
     const int Gt = occupancy_grid(ctx, k_true_res, smem64, n);
     const bool diag = mat->prec != SSCG_PREC_CHEB;
@@ -304,7 +304,7 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
     P.begin();
     k_init<A, VM><<<Gi, kThreads, smem, st>>>(M, dvec, b, x, A::kind == 0 ? nullptr : xw, r, diag ? blk[0] : nullptr,
                                               L.part, L.ctrl, L.hist);
-    if (!diag) P.launches += cheb.apply(M, dvec, r, blk[0], tmp, ld, Ge, Gl, smem, st, L.ctrl);
+    if (!diag) P.launches += cheb.apply(M, dvec, r, blk[0], tmp, ld, Ge, Gl, smem_pipe, st, L.ctrl);
     P.end(FAM_INIT, 0);
     SSCG_CUDA(ctx, cudaGetLastError());
 
@@ -323,10 +323,10 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
             for (int j = 0; j < s; j++) {
                 S* unext = j + 1 < s ? bn + (j + 1) * ld : nullptr;
                 const S* uprev = j > 0 ? bn + (j - 1) * ld : nullptr;
-                k_level_gen<A, VM><<<Gl, kThreads, smem, st>>>(M, dvec, bn + j * ld, uprev, bn + (s + j) * ld, unext,
+                k_level_gen<A, VM><<<Gl, kThreads, smem_pipe, st>>>(M, dvec, bn + j * ld, uprev, bn + (s + j) * ld, unext,
                                                                j, basis, diag ? 1 : 0, L.ctrl);
                 if (!diag && unext) {
-                    P.launches += cheb.apply(M, dvec, bn + (s + j) * ld, w, tmp, ld, Ge, Gl, smem, st, L.ctrl);
+                    P.launches += cheb.apply(M, dvec, bn + (s + j) * ld, w, tmp, ld, Ge, Gl, smem_pipe, st, L.ctrl);
                     k_combine<A><<<Ge, kThreads, 0, st>>>(n, w, bn + j * ld, uprev, unext, j, basis, L.ctrl);
                     P.launches++;
                 }
@@ -338,9 +338,9 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
                                                              L.ctrl);
             P.end(FAM_DIR, k);
             P.begin();
-            k_update<A, SB><<<Gu, kThreads, 0, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dvec, L.part, k == 0,
-                                                     diag ? 1 : 0, L.ctrl, L.hist);
-            if (!diag) P.launches += cheb.apply(M, dvec, r, bo, tmp, ld, Ge, Gl, smem, st, L.ctrl);
+            k_update_tma<A, SB><<<Gu, kUpdRows, smem_upd, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dvec, L.part,
+                                                                k == 0, diag ? 1 : 0, L.ctrl, L.hist);
+            if (!diag) P.launches += cheb.apply(M, dvec, r, bo, tmp, ld, Ge, Gl, smem_pipe, st, L.ctrl);
             P.end(FAM_UPDATE, k);
         }
         if (cudaGetLastError() != cudaSuccess) {
