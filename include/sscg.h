@@ -183,6 +183,35 @@ int sscg_pcg_solve(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* 
 /* y = A x (device FP64 vectors of length n), the library's CSR SpMV. */
 int sscg_spmv(sscg_ctx* ctx, const sscg_mat* mat, const double* x, double* y);
 
+/* ---------------------------------------- solve with no allocation at all
+ *
+ * Some callers cannot allocate device memory: code that runs inside another
+ * runtime's memory arena, plugins and embedded hosts that forbid cudaMalloc,
+ * and services that must not allocate on the request path (an allocation can
+ * synchronise the device or fail under memory pressure).  For them,
+ * sscg_solve_static runs the same s-step solve as sscg_solve but takes its
+ * workspace from a fixed array of SSCG_STATIC_SCRATCH_BYTES (16 MiB) that the
+ * library itself places in device memory; every GPU that loads the library
+ * holds that array until the process exits.  The caller still passes the
+ * matrix, b and x.  The paper has no counterpart: this is a deployment
+ * convenience, not part of the method.
+ *
+ * - Solves whose sscg_solve_workspace_bytes exceeds the array are rejected
+ *   with SSCG_ERR_SPACE (about n <= 100,000 at s = 4).
+ * - The call makes no cudaMalloc, cudaFree or other device allocation.
+ * - The first call on each device looks the array's device address up
+ *   (cudaGetSymbolAddress) with that device current, and caches it: make that
+ *   first call before any stream capture.  The context's device must be the
+ *   current device (SSCG_ERR_INVALID otherwise).
+ * - All calls on a device share the one array, which keeps the last call's
+ *   contents; the solve initialises everything it reads.  Calls whose work
+ *   overlaps on the GPU (other streams or host threads) race on the array:
+ *   serialise them.
+ */
+#define SSCG_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+int sscg_solve_static(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x,
+                      const sscg_opts* opts, sscg_info* info);
+
 /* -------------------------------------------------- spectral bounds */
 
 /* Workspace bytes for sscg_estimate_bounds with `steps` Lanczos steps. */

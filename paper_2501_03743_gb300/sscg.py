@@ -30,7 +30,9 @@ EXPORTS = (
     "sscg_mat_storage_bytes", "sscg_mat_create_csr", "sscg_mat_destroy", "sscg_mat_props_get",
     "sscg_set_preconditioner", "sscg_solve_workspace_bytes", "sscg_solve", "sscg_pcg_workspace_bytes",
     "sscg_pcg_solve", "sscg_spmv", "sscg_bounds_workspace_bytes", "sscg_estimate_bounds", "sscg_uniform",
+    "sscg_solve_static",
 )
+STATIC_SCRATCH_BYTES = 16 << 20
 
 
 class SscgError(RuntimeError):
@@ -96,6 +98,7 @@ def load(path: str | None = None):
     L.sscg_bounds_workspace_bytes.argtypes = [vp, i32, P(sz)]
     L.sscg_estimate_bounds.argtypes = [vp, vp, i32, vp, vp, sz, P(dbl), P(dbl)]
     L.sscg_uniform.argtypes = [vp, i64, C.c_uint64, vp]
+    L.sscg_solve_static.argtypes = [vp, vp, vp, vp, P(Opts), P(Info)]
     _lib = L
     return L
 
