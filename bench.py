@@ -63,6 +63,7 @@ def parse():
     p.add_argument("--no-pcg", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--fused-mpk", action="store_true", help="several matrix-powers levels per launch (L2-resident)")
     return p.parse_args()
 
 
@@ -221,7 +222,8 @@ def main():
     bm = byte_model(n, nnz, vbytes, a.s, a.arith)
     b = torch.from_numpy(sysm["b"]).cuda()
     x = torch.zeros_like(b)
-    solver = sscg.Solver(A, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, profile=True)
+    solver = sscg.Solver(A, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, profile=True,
+                         fused_mpk=a.fused_mpk)
     stream = ctx.stream
 
     def timed(fn, count):
@@ -299,7 +301,8 @@ def main():
     # end to end through the public API with host buffers
     bh = torch.from_numpy(sysm["b"]).pin_memory()
     xh = torch.zeros(n, dtype=torch.float64).pin_memory()
-    hsolver = sscg.Solver(A, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, host_vectors=True)
+    hsolver = sscg.Solver(A, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, host_vectors=True,
+                          fused_mpk=a.fused_mpk)
     xh.zero_()
     hsolver.solve(bh, xh)
     e2e_t = []

@@ -71,6 +71,7 @@ typedef enum { SSCG_ARITH_F64 = 0, SSCG_ARITH_DF64 = 1, SSCG_ARITH_MIXED = 2 } s
 #define SSCG_HOST_VECTORS 0x1u /* b and x are host pointers; copies happen inside the call */
 #define SSCG_PROFILE 0x2u      /* bracket every kernel with CUDA events; fills the t_* fields of sscg_info */
 #define SSCG_DIRECT_GRAM 0x4u  /* form the Gram blocks directly even for the monomial basis */
+#define SSCG_FUSED_MPK 0x8u    /* several matrix-powers levels per launch, intermediate levels kept in L2 */
 #define SSCG_HOST_ARRAYS 0x1u  /* CSR arrays are host pointers (sscg_mat_create_csr) */
 
 typedef struct sscg_ctx sscg_ctx;

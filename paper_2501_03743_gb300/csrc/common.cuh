@@ -127,6 +127,7 @@ struct ArithF64 {
     __device__ static __forceinline__ R zero() { return 0.0; }
     __device__ static __forceinline__ R ld(const S* p) { return *p; }
     __device__ static __forceinline__ R ldg(const S* p) { return __ldg(p); }
+    __device__ static __forceinline__ R ldcg(const S* p) { return __ldcg(p); }
     __device__ static __forceinline__ void st(S* p, R v) { *p = v; }
     __device__ static __forceinline__ R add(R a, R b) { return a + b; }
     __device__ static __forceinline__ R sub(R a, R b) { return a - b; }
@@ -148,6 +149,10 @@ struct ArithDF64 {
     }
     __device__ static __forceinline__ R ldg(const S* p) {
         float2 v = __ldg(p);
+        return df_make(v.x, v.y);
+    }
+    __device__ static __forceinline__ R ldcg(const S* p) {
+        float2 v = __ldcg(p);
         return df_make(v.x, v.y);
     }
     __device__ static __forceinline__ void st(S* p, R v) { *p = make_float2(v.hi, v.lo); }
@@ -192,6 +197,8 @@ struct Ctrl {
     double basis_c, basis_delta;  // Chebyshev basis centre and half-width
     double rho, pcg_alpha, pcg_beta;  // PCG scalars
     double scratch[8];
+    unsigned claim;  // work-item counter of the fused matrix-powers kernel
+    unsigned pad1[3];
 };
 
 // ------------------------------------------------------------- reductions
@@ -203,23 +210,22 @@ __device__ __forceinline__ typename A::R warp_sum(typename A::R v) {
     return v;
 }
 
-// Sum NV values over the CTA (blockDim.x a multiple of 32, at most
-// kThreads); the result is returned as doubles in thread 0.  `sh` holds
-// NV * (kThreads/32) doubles.
+// Sum NV values over the CTA (blockDim.x a multiple of 32); the result is
+// returned as doubles in thread 0.  `sh` holds NV * (blockDim.x/32) doubles.
 template <class A, int NV>
 __device__ __forceinline__ void block_sum(typename A::R (&v)[NV], double* sh, double (&out)[NV]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NV; q++) {
         typename A::R w = warp_sum<A>(v[q]);
-        if (lane == 0) sh[q * (kThreads / 32) + warp] = A::to_d(w);
+        if (lane == 0) sh[q * nw + warp] = A::to_d(w);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NV; q++) {
             double t = 0.0;
-            for (int w = 0; w < nw; w++) t += sh[q * (kThreads / 32) + w];
+            for (int w = 0; w < nw; w++) t += sh[q * nw + w];
             out[q] = t;
         }
     }

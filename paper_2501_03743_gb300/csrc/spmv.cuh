@@ -201,13 +201,58 @@ __device__ __forceinline__ float2 stage_val<ArithDF64, VAL_DF>(const char* v0, c
     return make_float2(reinterpret_cast<const float*>(v0)[k], reinterpret_cast<const float*>(v1)[k]);
 }
 
+// Thread 0: bulk-copy tile t's row pointers, column indices and values into
+// the stage at `st`, completing on `bar`.
+template <int VM>
+__device__ __forceinline__ void issue_tile(const MatView& M, char* st, uint64_t* bar, int t) {
+    const int cap = M.cap;
+    const int r0 = t * kTileRows, nrows = min(kTileRows, M.n - r0);
+    const int lo = __ldg(M.rowptr + r0), hi = __ldg(M.rowptr + r0 + nrows);
+    const int base = lo & ~3, end = min((hi + 3) & ~3, base + cap), cnt = end - base;
+    const unsigned rpb = (unsigned)(((nrows + 1 + 3) & ~3) * 4);
+    const unsigned tx = rpb + (unsigned)cnt * (4 + val0_bytes<VM>() + val1_bytes<VM>());
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, tx);
+    bulk_g2s(st, M.rowptr + r0, rpb, bar);
+    if (cnt > 0) {
+        char* cdst = st + kPipeRp * 4;
+        char* v0 = cdst + (size_t)cap * 4;
+        bulk_g2s(cdst, M.col + base, (unsigned)cnt * 4, bar);
+        if (VM == VAL_F64) bulk_g2s(v0, M.val + base, (unsigned)cnt * 8, bar);
+        else bulk_g2s(v0, M.vhi + base, (unsigned)cnt * 4, bar);
+        if (VM == VAL_DF) bulk_g2s(v0 + (size_t)cap * 4, M.vlo + base, (unsigned)cnt * 4, bar);
+    }
+}
+
+// Every thread: row r0 + threadIdx.x of tile t from the staged data (entries
+// past the stage's capacity from global memory); epi(row, y).
+template <class A, int VM, class XF, class EPI>
+__device__ __forceinline__ void compute_tile(const MatView& M, const char* st, int t, XF xf, EPI epi) {
+    using V = Val<A, VM>;
+    const int cap = M.cap;
+    const int* s_rp = reinterpret_cast<const int*>(st);
+    const int32_t* s_col = reinterpret_cast<const int32_t*>(st + kPipeRp * 4);
+    const char* v0 = st + kPipeRp * 4 + (size_t)cap * 4;
+    const char* v1 = v0 + (size_t)cap * val0_bytes<VM>();
+    const int r0 = t * kTileRows, nrows = min(kTileRows, M.n - r0);
+    const int base = s_rp[0] & ~3;
+    const int staged = min((s_rp[nrows] + 3) & ~3, base + cap) - base;
+    if ((int)threadIdx.x < nrows) {
+        const int ks = s_rp[threadIdx.x] - base, ke = s_rp[threadIdx.x + 1] - base;
+        const int km = min(ke, staged);
+        typename A::R y = A::zero();
+        for (int q = ks; q < km; q++) y = V::mac(y, stage_val<A, VM>(v0, v1, q), xf(s_col[q]));
+        for (int q = max(ks, staged); q < ke; q++) y = V::mac(y, V::load(M, base + q), xf(__ldg(M.col + base + q)));
+        epi(r0 + (int)threadIdx.x, y);
+    }
+}
+
 // Runs epi(row, y) with y = (A x)[row] for every row of this CTA's tiles.
 // M.cap (a multiple of 4) is the entries a stage holds.  Every thread of the
 // CTA must call it; `smem` holds pipe_bytes<VM, NS>(M.cap).  Returns false
 // after a timeout (recorded in ctrl).
 template <class A, int VM, int NS, class XF, class EPI>
 __device__ __forceinline__ bool spmv_pipe(const MatView& M, char* smem, XF xf, EPI epi, Ctrl* ctrl) {
-    using V = Val<A, VM>;
     const int cap = M.cap;
     const int ntiles = (M.n + kTileRows - 1) / kTileRows;
     const int G = gridDim.x;
@@ -221,24 +266,7 @@ __device__ __forceinline__ bool spmv_pipe(const MatView& M, char* smem, XF xf, E
     }
     __syncthreads();
     auto issue = [&](int k) {  // thread 0: tile k of this CTA into stage k % NS
-        const int t = (int)blockIdx.x + k * G, r0 = t * kTileRows, nrows = min(kTileRows, M.n - r0);
-        const int lo = __ldg(M.rowptr + r0), hi = __ldg(M.rowptr + r0 + nrows);
-        const int base = lo & ~3, end = min((hi + 3) & ~3, base + cap), cnt = end - base;
-        char* st = stage0 + (size_t)(k % NS) * sb;
-        const unsigned rpb = (unsigned)(((nrows + 1 + 3) & ~3) * 4);
-        const unsigned tx = rpb + (unsigned)cnt * (4 + val0_bytes<VM>() + val1_bytes<VM>());
-        uint64_t* b = &bar[k % NS];
-        fence_proxy_async();
-        mbar_arrive_expect_tx(b, tx);
-        bulk_g2s(st, M.rowptr + r0, rpb, b);
-        if (cnt > 0) {
-            char* cdst = st + kPipeRp * 4;
-            char* v0 = cdst + (size_t)cap * 4;
-            bulk_g2s(cdst, M.col + base, (unsigned)cnt * 4, b);
-            if (VM == VAL_F64) bulk_g2s(v0, M.val + base, (unsigned)cnt * 8, b);
-            else bulk_g2s(v0, M.vhi + base, (unsigned)cnt * 4, b);
-            if (VM == VAL_DF) bulk_g2s(v0 + (size_t)cap * 4, M.vlo + base, (unsigned)cnt * 4, b);
-        }
+        issue_tile<VM>(M, stage0 + (size_t)(k % NS) * sb, &bar[k % NS], (int)blockIdx.x + k * G);
     };
     if (threadIdx.x == 0)
         for (int k = 0; k < NS - 1 && k < my; k++) issue(k);
@@ -255,22 +283,7 @@ __device__ __forceinline__ bool spmv_pipe(const MatView& M, char* smem, XF xf, E
             __syncthreads();
             return false;
         }
-        const char* st = stage0 + (size_t)(k % NS) * sb;
-        const int* s_rp = reinterpret_cast<const int*>(st);
-        const int32_t* s_col = reinterpret_cast<const int32_t*>(st + kPipeRp * 4);
-        const char* v0 = st + kPipeRp * 4 + (size_t)cap * 4;
-        const char* v1 = v0 + (size_t)cap * val0_bytes<VM>();
-        const int t = (int)blockIdx.x + k * G, r0 = t * kTileRows, nrows = min(kTileRows, M.n - r0);
-        const int base = s_rp[0] & ~3;
-        const int staged = min((s_rp[nrows] + 3) & ~3, base + cap) - base;
-        if ((int)threadIdx.x < nrows) {
-            const int ks = s_rp[threadIdx.x] - base, ke = s_rp[threadIdx.x + 1] - base;
-            const int km = min(ke, staged);
-            typename A::R y = A::zero();
-            for (int q = ks; q < km; q++) y = V::mac(y, stage_val<A, VM>(v0, v1, q), xf(s_col[q]));
-            for (int q = max(ks, staged); q < ke; q++) y = V::mac(y, V::load(M, base + q), xf(__ldg(M.col + base + q)));
-            epi(r0 + (int)threadIdx.x, y);
-        }
+        compute_tile<A, VM>(M, stage0 + (size_t)(k % NS) * sb, (int)blockIdx.x + k * G, xf, epi);
         __syncthreads();  // stage k % NS may be refilled
     }
     return true;

@@ -78,6 +78,257 @@ __global__ void __launch_bounds__(kThreads) k_level(MatView M, const typename A:
     }
 }
 
+// Fused matrix-powers kernel: levels j0 .. j0+F-1 of one outer step in one
+// launch, so the matrix is read from HBM about once per F levels.
+//
+// Work items are (level jl, tile t) pairs.  Item q has key q / F and level
+// q % F, tile = key - jl * D.  Level jl of tile t needs level jl-1 of tiles
+// t-h .. t+h (h: the matrix bandwidth in tiles), whose keys are at most
+// key - (D - h); CTAs claim items from a global counter in increasing q, so
+// every dependency is claimed before the item that needs it and the
+// smallest unfinished item can always proceed.  D = h + 1 + (items in flight
+// per level) keeps dependencies already finished when an item starts, and
+// the rows a level re-reads (matrix rows, the previous level's vector) were
+// touched D keys earlier: they are still in L2.  Each CTA prefetches its
+// next item's matrix tile by bulk copy while computing the current one.
+// A finished tile publishes flag[jl][t] = epoch (release store after a
+// fence); consumers poll the flags with relaxed gpu-scope loads, fence, and
+// read vectors produced in this launch through L2 (ld.global.cg).  Every wait is bounded by %globaltimer.
+constexpr int kMaxFuse = 4;
+
+// Flags are polled with relaxed gpu-scope loads (coherent at L2); one fence
+// after the last flag orders the reads that follow.
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Barrier 1 among the 256 consumer threads only (the producer warp is busy).
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+constexpr int kFuseStages = 2;
+constexpr int kFuseThreads = kThreads + 32;  // 8 consumer warps + 1 producer warp
+constexpr int kFuseWarps = kThreads / 32;    // arrivals per finished tile
+constexpr unsigned kNoItem = 0xffffffffu;
+
+template <int VM>
+__host__ __device__ constexpr size_t fused_smem(int cap) {
+    return 64 + (size_t)kFuseStages * pipe_stage_bytes<VM>(cap);
+}
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Counters: cnt[jl][t] gains one arrival from each consumer warp that has
+// written its 32 rows of tile t at level slot jl.  want[jl] is the count a
+// tile of slot jl reaches once this launch has finished it (the host adds
+// kFuseWarps per launch that uses the slot; counters are zeroed per solve).
+struct FuseWant {
+    unsigned w[kMaxFuse];
+};
+
+template <class A, int VM>
+__global__ void __launch_bounds__(kFuseThreads) k_mpk_fused(MatView M, const typename A::S* __restrict__ dinv,
+                                                            typename A::S* __restrict__ blk, int ldn, int s, int j0,
+                                                            int F, int T, int h, int D,
+                                                            unsigned* __restrict__ cnt, FuseWant want,
+                                                            double* __restrict__ part, int step, int last,
+                                                            Ctrl* ctrl) {
+    using R = typename A::R;
+    using S = typename A::S;
+    if (ctrl_done(ctrl)) return;
+    extern __shared__ __align__(16) char smem_raw[];
+    char* smem = align128(smem_raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);  // [kFuseStages]
+    uint64_t* empty = full + kFuseStages;                 // [kFuseStages]
+    char* stage0 = smem + 64;
+    const size_t sb = pipe_stage_bytes<VM>(M.cap);
+    __shared__ unsigned s_item[kFuseStages];
+    __shared__ double red[2 * kMaxFuse * 16];
+    const size_t ld = (size_t)ldn;
+    const unsigned Q = (unsigned)(T + (F - 1) * D) * (unsigned)F;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    auto tile_of = [&](unsigned q, int& jl) {
+        jl = (int)(q % (unsigned)F);
+        return (int)(q / (unsigned)F) - jl * D;
+    };
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kFuseStages; q++) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kFuseWarps);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    R m1[kMaxFuse], m2[kMaxFuse];
+#pragma unroll
+    for (int q = 0; q < kMaxFuse; q++) m1[q] = m2[q] = A::zero();
+    bool ok = true;
+    if (warp == kFuseWarps) {
+        // producer: claim items in order and stage each one's matrix tile
+        if (lane == 0) {
+            for (int k = 0;; k++) {
+                const int st = k % kFuseStages;
+                if (k >= kFuseStages && !mbar_wait(&empty[st], (unsigned)((k / kFuseStages) - 1) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                const unsigned q = atomicAdd(&ctrl->claim, 1u);
+                int jl = 0, t = -1;
+                if (q < Q) t = tile_of(q, jl);
+                const bool live = q < Q && t >= 0 && t < T;
+                s_item[st] = q < Q ? (live ? q : kNoItem - 1) : kNoItem;
+                if (live) issue_tile<VM>(M, stage0 + (size_t)st * sb, &full[st], t);
+                else mbar_arrive(&full[st]);  // nothing to copy: the phase completes on arrival
+                if (q >= Q) break;
+            }
+        }
+        __syncwarp();
+    } else {
+        // consumer warps run independently: no CTA barrier per item
+        for (int k = 0;; k++) {
+            const int st = k % kFuseStages;
+            if (!mbar_wait(&full[st], (unsigned)(k / kFuseStages) & 1u)) {
+                ok = false;
+                break;
+            }
+            const unsigned cur = s_item[st];
+            if (cur == kNoItem) break;
+            if (cur != kNoItem - 1) {
+                int jl;
+                const int t = tile_of(cur, jl);
+                if (jl > 0) {  // previous level's tiles t-h .. t+h complete?
+                    const unsigned* c0 = cnt + (size_t)(jl - 1) * T;
+                    const unsigned target = want.w[jl - 1];
+                    const int lo = max(0, t - h), hi = min(T - 1, t + h);
+                    bool dep_ok = true;
+                    uint64_t t0 = 0;
+                    for (int c = lo + lane; c <= hi && dep_ok; c += 32) {
+                        unsigned spins = 0;
+                        while (ld_relaxed_u32(c0 + c) < target) {
+                            if (t0 == 0) t0 = globaltimer();
+                            if ((++spins & 63u) == 0 && globaltimer() - t0 > kWaitLimitNs) {
+                                dep_ok = false;
+                                break;
+                            }
+                        }
+                    }
+                    dep_ok = __all_sync(0xffffffffu, dep_ok);
+                    if (!dep_ok) {
+                        if (lane == 0) {
+                            ctrl->status = 3;  // SSCG_TIMEOUT
+                            __threadfence();
+                            atomicExch(&ctrl->done, 1);
+                        }
+                        ok = false;
+                        break;
+                    }
+                    fence_acq_rel_gpu();  // the gathers below follow the observed counters
+                }
+                const int j = j0 + jl;
+                const S* uj = blk + (size_t)j * ld;
+                S* au = blk + (size_t)(s + j) * ld;
+                S* un = (j + 1 < s) ? blk + (size_t)(j + 1) * ld : nullptr;
+                const bool want_m2 = 2 * j + 2 <= 2 * s - 1;
+                const bool fresh = jl > 0;  // u_j produced in this launch: read through L2
+                compute_tile<A, VM>(
+                    M, stage0 + (size_t)st * sb, t,
+                    [&](int c) { return fresh ? A::ldcg(uj + c) : A::ldg(uj + c); },
+                    [&](int row, R y) {
+                        A::st(au + row, y);
+                        R u = fresh ? A::ldcg(uj + row) : A::ldg(uj + row);
+                        R a1 = A::mul(u, y), a2 = A::zero();
+                        if (un || want_m2) {
+                            R z = dinv ? A::mul(A::ld(dinv + row), y) : y;
+                            if (un) A::st(un + row, z);
+                            a2 = A::mul(y, z);
+                        }
+#pragma unroll
+                        for (int q = 0; q < kMaxFuse; q++)
+                            if (q == jl) {
+                                m1[q] = A::add(m1[q], a1);
+                                m2[q] = A::add(m2[q], a2);
+                            }
+                    });
+                __syncwarp();  // the warp's rows are written
+                if (lane == 0) red_release_add(cnt + (size_t)jl * T + t, 1u);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+        }
+    }
+    if (!__syncthreads_and(ok)) return;
+    const int G = gridDim.x;
+#pragma unroll
+    for (int q = 0; q < kMaxFuse; q++) {
+        if (q >= F) break;
+        R v[2] = {m1[q], m2[q]};
+        double out[2];
+        block_sum<A, 2>(v, red, out);
+        if (threadIdx.x == 0) {
+            part[(2 * (j0 + q)) * G + blockIdx.x] = out[0];
+            part[(2 * (j0 + q) + 1) * G + blockIdx.x] = out[1];
+        }
+    }
+    if (!last_cta(&ctrl->ticket[1])) return;
+    if (threadIdx.x == 0) ctrl->claim = 0u;  // every CTA has left the claim loop
+    if (!last) return;
+    cta_sum_rows(part, 2 * s - 1, G, [&](int e, double v) { ctrl->mu[e + 1] = v; });
+    SmallScratch* sc = reinterpret_cast<SmallScratch*>(smem);
+    if (threadIdx.x < 32) {
+        int st = warp_sw_monomial(ctrl, s, step, sc);
+        if (threadIdx.x == 0 && st != 0) {
+            ctrl->status = st;
+            ctrl->done = 1;
+        }
+    }
+}
+
+// Fusion plan: levels per launch F, key lag D; F = 0 (one launch per level)
+// unless SSCG_FUSED_MPK is set and the levels a launch would keep in L2 fit
+// the budget.  Measured on GB300 the fused kernel cuts DRAM traffic 2.5x
+// but is limited by item latency and dependency waits, so it is opt-in.
+struct FusePlan {
+    int F, T, h, D;
+};
+
+inline FusePlan plan_fusion(const sscg_mat* mat, int s, int G, unsigned flags) {
+    FusePlan p{0, 0, 0, 0};
+    if (!(flags & SSCG_FUSED_MPK)) return p;
+    p.T = (int)((mat->n + kTileRows - 1) / kTileRows);
+    p.h = (int)((mat->bandwidth + kTileRows - 1) / kTileRows);
+    const double row_bytes = (4.0 + (double)mat->nnz / (double)mat->n * 8.0) + 48.0;
+    for (int F = std::min(s, kMaxFuse); F >= 2; F--) {
+        // items in flight: kFuseStages + 1 per CTA; lag them by 1.25x that many keys
+        const int D = p.h + 1 + (5 * G * (kFuseStages + 1) / 4 + F - 1) / F + 8;
+        const double l2 = (double)(F - 1) * D * kTileRows * row_bytes;
+        if (l2 <= 72.0e6 && D < p.T) {
+            p.F = F;
+            p.D = D;
+            return p;
+        }
+    }
+    return p;
+}
+
 // ------------------------------------------------------------ host side
 
 struct Layout {
@@ -88,6 +339,7 @@ struct Layout {
     double* part;
     void* blk[2];
     void* r;
+    unsigned* flags;
     void* xw;
     double* bdev;
     double* xdev;
@@ -108,6 +360,7 @@ Layout plan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t c
     L.blk[0] = c.take<double>(blk);
     L.blk[1] = c.take<double>(blk);
     L.r = c.take<double>((size_t)L.ldn);
+    L.flags = c.take<unsigned>((size_t)kMaxFuse * ((mat->n + kTileRows - 1) / kTileRows));
     L.xw = (o->arith == SSCG_ARITH_F64) ? nullptr : c.take<double>((size_t)L.ldn);
     if (o->flags & SSCG_HOST_VECTORS) {
         L.bdev = c.take<double>((size_t)L.ldn);
@@ -143,6 +396,9 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     const size_t smem64 = stage_bytes<ArithF64, VAL_F64>(cap);
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_level<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pipe));
+    const size_t smem_fused = std::max(fused_smem<VM>(cap), sizeof(SmallScratch)) + 128;
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_mpk_fused<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_fused));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_true_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
     S* blk[2] = {(S*)L.blk[0], (S*)L.blk[1]};
     S* r = (S*)L.r;
@@ -152,6 +408,13 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     P.begin();
     const int Gi = occupancy_grid(ctx, k_init<A, VM>, smem, n);
     const int Gl = occupancy_grid(ctx, k_level<A, VM>, smem_pipe, n);
+    int per_sm = 0;
+    SSCG_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mpk_fused<A, VM>, kFuseThreads,
+                                                                 smem_fused));
+    const int Gf = std::max(1, std::min(kMaxGrid, ctx->sm_count * std::max(per_sm, 1)));
+    const FusePlan fp = plan_fusion(mat, s, Gf, o->flags);
+    if (fp.F > 0) SSCG_CUDA(ctx, cudaMemsetAsync(L.flags, 0, sizeof(unsigned) * kMaxFuse * fp.T, st));
+    FuseWant want{};  // arrivals each level slot's counters reach after the current launch
     size_t smem_upd = 0;
     int Gu = 0;
     if (int e = update_tma_setup<A, SB>(ctx, n, s, &smem_upd, &Gu)) return e;
@@ -173,12 +436,24 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
             const int k = launched + q;
             S* bn = blk[k & 1];
             S* bo = blk[(k + 1) & 1];
-            for (int j = 0; j < s; j++) {
-                P.begin();
-                k_level<A, VM><<<Gl, kThreads, smem_pipe, st>>>(M, dinv, bn + j * ld, bn + (s + j) * ld,
-                                                          j + 1 < s ? bn + (j + 1) * ld : nullptr, L.part, j, s, k,
-                                                          j == s - 1, L.ctrl);
-                P.end(FAM_MPK, k);
+            if (fp.F > 0) {
+                for (int j0 = 0; j0 < s; j0 += fp.F) {
+                    const int F = std::min(fp.F, s - j0);
+                    for (int q = 0; q < F; q++) want.w[q] += kFuseWarps;
+                    P.begin();
+                    k_mpk_fused<A, VM><<<Gf, kFuseThreads, smem_fused, st>>>(M, dinv, bn, (int)L.ldn, s, j0, F, fp.T,
+                                                                            fp.h, fp.D, L.flags, want, L.part, k,
+                                                                            j0 + F == s, L.ctrl);
+                    P.end(FAM_MPK, k);
+                }
+            } else {
+                for (int j = 0; j < s; j++) {
+                    P.begin();
+                    k_level<A, VM><<<Gl, kThreads, smem_pipe, st>>>(M, dinv, bn + j * ld, bn + (s + j) * ld,
+                                                              j + 1 < s ? bn + (j + 1) * ld : nullptr, L.part, j, s,
+                                                              k, j == s - 1, L.ctrl);
+                    P.end(FAM_MPK, k);
+                }
             }
             P.begin();
             k_update_tma<A, SB><<<Gu, kUpdRows, smem_upd, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dinv, L.part,

@@ -232,11 +232,13 @@ class Matrix:
 
 
 DIRECT_GRAM = 0x4
+FUSED_MPK = 0x8
 
 
 def make_opts(s=4, basis="monomial", tol=1e-8, maxit=1000, arith="df64", basis_bounds=(0.0, 0.0),
-              replace_every=0, host_vectors=False, profile=False, direct_gram=False) -> Opts:
+              replace_every=0, host_vectors=False, profile=False, direct_gram=False, fused_mpk=False) -> Opts:
     flags = (HOST_VECTORS if host_vectors else 0) | (PROFILE if profile else 0) | (DIRECT_GRAM if direct_gram else 0)
+    flags |= FUSED_MPK if fused_mpk else 0
     return Opts(int(s), BASIS[basis], float(basis_bounds[0]), float(basis_bounds[1]), float(tol), int(maxit),
                 ARITH[arith], int(replace_every), flags)
 

@@ -308,6 +308,26 @@ def test_identity_preconditioner(ctx, arith):
     assert rj.outer_iters == res.outer_iters and rel(xj, x) < 1e-10
 
 
+@pytest.mark.parametrize("s", [3, 4, 8])
+def test_fused_mpk_matches_sequential_and_oracle(ctx, s):
+    """128^3: large enough that the fused matrix-powers kernel runs (several
+    levels per launch, levels kept in L2); it must give the sequential
+    kernel's iterates and the oracle's."""
+    S = system("poisson7", 128, 7)
+    A = gpu_matrix(ctx, S)
+    x, res = gpu_solve(A, S["b"], s=s, tol=1e-8, maxit=400, fused_mpk=True)
+    xs, rs = gpu_solve(A, S["b"], s=s, tol=1e-8, maxit=400)
+    assert res.status == rs.status
+    assert res.outer_iters == rs.outer_iters
+    # the two kernels accumulate the moments in different orders; the monomial
+    # Hankel system amplifies that at s = 8 (Section II-A's instability)
+    assert rel(x, xs) < (1e-9 if s <= 4 else 1e-5)
+    if res.status == sscg.OK and s <= 4:
+        ref = oracle.pcgs(oracle.as_matrix(S), S["b"], s, tol=0.0, maxit=res.outer_iters)
+        assert rel(x, ref.x) < 1e-7
+        assert res.rel_res_true < 1e-7
+
+
 # ------------------------------------------------------------- full size
 
 @pytest.mark.slow
