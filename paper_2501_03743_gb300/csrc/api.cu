@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kThreads) k_analyze(int n, const int32_t* __re
                                                       const double* __restrict__ val, float* __restrict__ vhi,
                                                       float* __restrict__ vlo, double* __restrict__ diag,
                                                       double* __restrict__ dinv, float2* __restrict__ dinv_df,
-                                                      Analysis* out) {
+                                                      float* __restrict__ dinv_f, Analysis* out) {
     __shared__ unsigned long long s_bad, s_nf, s_ne, s_np, s_bw, s_mn, s_mx;
     if (threadIdx.x == 0) {
         s_bad = s_nf = s_ne = s_np = s_bw = 0ull;
@@ -61,11 +61,13 @@ __global__ void __launch_bounds__(kThreads) k_analyze(int n, const int32_t* __re
             np++;
             dinv[i] = 0.0;
             dinv_df[i] = make_float2(0.f, 0.f);
+            dinv_f[i] = 0.f;
         } else {
             double inv = 1.0 / d;
             dinv[i] = inv;
             float hi = __double2float_rn(inv);
             dinv_df[i] = make_float2(hi, __double2float_rn(inv - (double)hi));
+            dinv_f[i] = hi;
             unsigned long long bits = (unsigned long long)__double_as_longlong(d);
             mn = bits < mn ? bits : mn;
             mx = bits > mx ? bits : mx;
@@ -99,6 +101,7 @@ struct MatLayout {
     double* diag;
     double* dinv;
     float2* dinv_df;
+    float* dinv_f;
     Analysis* an;
     size_t bytes;
 };
@@ -116,6 +119,7 @@ MatLayout mat_layout(int64_t n, int64_t nnz, void* base) {
     L.diag = c.take<double>((size_t)n);
     L.dinv = c.take<double>((size_t)n);
     L.dinv_df = c.take<float2>((size_t)n);
+    L.dinv_f = c.take<float>((size_t)n + 16);
     L.an = c.take<Analysis>(1);
     L.bytes = c.used;
     return L;
@@ -230,7 +234,8 @@ int sscg_mat_create_csr(sscg_ctx* ctx, int64_t n, int64_t nnz, const int32_t* ro
     a0.dmin_bits = ~0ull;
     SSCG_CUDA(ctx, cudaMemcpyAsync(L.an, &a0, sizeof(a0), cudaMemcpyHostToDevice, st));
     int G = grid_for(ctx, n, 4);
-    k_analyze<<<G, kThreads, 0, st>>>((int)n, L.rowptr, L.col, L.val, L.vhi, L.vlo, L.diag, L.dinv, L.dinv_df, L.an);
+    k_analyze<<<G, kThreads, 0, st>>>((int)n, L.rowptr, L.col, L.val, L.vhi, L.vlo, L.diag, L.dinv, L.dinv_df,
+                                      L.dinv_f, L.an);
     SSCG_CUDA(ctx, cudaGetLastError());
     Analysis a;
     SSCG_CUDA(ctx, cudaMemcpyAsync(&a, L.an, sizeof(a), cudaMemcpyDeviceToHost, st));
@@ -251,6 +256,7 @@ int sscg_mat_create_csr(sscg_ctx* ctx, int64_t n, int64_t nnz, const int32_t* ro
     m->diag = L.diag;
     m->dinv = L.dinv;
     m->dinv_df = L.dinv_df;
+    m->dinv_f = L.dinv_f;
     m->bandwidth = (int64_t)a.bandwidth;
     m->exact_fp32 = a.not_exact == 0;
     m->max_row_nnz = max_row;
@@ -319,8 +325,9 @@ static bool auto_bounds(const sscg_opts* o) {
 
 int sscg_solve_workspace_bytes(const sscg_mat* m, const sscg_opts* o, size_t* bytes) {
     if (!m || !o || !bytes || o->s < 1 || o->s > kMaxS || o->maxit < 0) return SSCG_ERR_INVALID;
-    if (!use_gram(m, o)) return sstep_workspace(m, o, bytes);
-    gram_workspace(m, o, bytes);
+    if (o->arith != SSCG_ARITH_MIXED && !use_gram(m, o)) return sstep_workspace(m, o, bytes);
+    if (o->arith == SSCG_ARITH_MIXED) mixed_workspace(m, o, bytes);
+    else gram_workspace(m, o, bytes);
     if (auto_bounds(o)) {
         size_t bb = 0;
         bounds_workspace(m, kAutoBoundSteps, &bb);
@@ -337,9 +344,11 @@ int sscg_solve(sscg_ctx* ctx, const sscg_mat* m, const double* b, double* x, con
     if (o->maxit < 0 || !(o->tol >= 0.0)) return set_err(ctx, SSCG_ERR_INVALID, "bad maxit or tol");
     if (o->basis != SSCG_BASIS_MONOMIAL && o->basis != SSCG_BASIS_CHEBYSHEV)
         return set_err(ctx, SSCG_ERR_INVALID, "unknown basis %d", o->basis);
-    if (o->arith != SSCG_ARITH_F64 && o->arith != SSCG_ARITH_DF64)
+    if (o->arith != SSCG_ARITH_F64 && o->arith != SSCG_ARITH_DF64 && o->arith != SSCG_ARITH_MIXED)
         return set_err(ctx, SSCG_ERR_INVALID, "arith %d not supported", o->arith);
-    if (!use_gram(m, o)) return solve_sstep(ctx, m, b, x, o, info, ws, ws_bytes);
+    if (o->arith == SSCG_ARITH_MIXED && m->prec == SSCG_PREC_CHEB)
+        return set_err(ctx, SSCG_ERR_INVALID, "the mixed-precision mode takes a diagonal preconditioner");
+    if (o->arith != SSCG_ARITH_MIXED && !use_gram(m, o)) return solve_sstep(ctx, m, b, x, o, info, ws, ws_bytes);
     double lo = o->basis_lmin, hi = o->basis_lmax;
     if (auto_bounds(o)) {
         size_t need = 0;
@@ -353,6 +362,7 @@ int sscg_solve(sscg_ctx* ctx, const sscg_mat* m, const double* b, double* x, con
     }
     if (o->basis == SSCG_BASIS_CHEBYSHEV && !(hi > lo && lo >= 0.0))
         return set_err(ctx, SSCG_ERR_INVALID, "Chebyshev basis needs 0 <= basis_lmin < basis_lmax");
+    if (o->arith == SSCG_ARITH_MIXED) return solve_mixed(ctx, m, b, x, o, info, ws, ws_bytes, lo, hi);
     return solve_gram(ctx, m, b, x, o, info, ws, ws_bytes, lo, hi);
 }
 

@@ -167,6 +167,43 @@ struct ArithDF64 {
     }
 };
 
+// FP32 arithmetic and storage (basis blocks of the mixed-precision mode).
+struct ArithF32 {
+    using R = float;
+    using S = float;
+    static constexpr int kind = 2;
+    __device__ static __forceinline__ R zero() { return 0.f; }
+    __device__ static __forceinline__ R ld(const S* p) { return *p; }
+    __device__ static __forceinline__ R ldg(const S* p) { return __ldg(p); }
+    __device__ static __forceinline__ R ldcg(const S* p) { return __ldcg(p); }
+    __device__ static __forceinline__ void st(S* p, R v) { *p = v; }
+    __device__ static __forceinline__ R add(R a, R b) { return a + b; }
+    __device__ static __forceinline__ R sub(R a, R b) { return a - b; }
+    __device__ static __forceinline__ R mul(R a, R b) { return a * b; }
+    __device__ static __forceinline__ R fma(R a, R b, R c) { return fmaf(a, b, c); }
+    __device__ static __forceinline__ R from_d(double x) { return (float)x; }
+    __device__ static __forceinline__ double to_d(R a) { return (double)a; }
+    __device__ static __forceinline__ R shfl_xor(R a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+};
+
+// FP32 storage with double-float accumulation: Gram sums of FP32 blocks,
+// where every product of two FP32 numbers is formed exactly.
+struct ArithF32Acc {
+    using R = df64;
+    using S = float;
+    static constexpr int kind = 3;
+    __device__ static __forceinline__ R zero() { return df_make(0.f, 0.f); }
+    __device__ static __forceinline__ R ld(const S* p) { return df_make(*p, 0.f); }
+    __device__ static __forceinline__ void st(S* p, R v) { *p = v.hi; }
+    __device__ static __forceinline__ R add(R a, R b) { return df_add(a, b); }
+    __device__ static __forceinline__ R fma(R a, R b, R c) { return df_fma(a, b, c); }
+    __device__ static __forceinline__ R from_d(double x) { return df_from_double(x); }
+    __device__ static __forceinline__ double to_d(R a) { return df_to_double(a); }
+    __device__ static __forceinline__ R shfl_xor(R a, int m) {
+        return df_make(__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m));
+    }
+};
+
 // --------------------------------------------------------- control block
 //
 // One per solve, in the caller's workspace.  Kernels read `done` at entry
@@ -194,6 +231,9 @@ struct Ctrl {
     double G[kMaxS * kMaxS];      // direct Gram blocks (Chebyshev basis)
     double C[kMaxS * kMaxS];
     double m[kMaxS];
+    double q[kMaxS];              // P_old^T r (residual-replacement correction of m)
+    int with_q;                   // q was formed this step
+    int pad2;
     double basis_c, basis_delta;  // Chebyshev basis centre and half-width
     double rho, pcg_alpha, pcg_beta;  // PCG scalars
     double scratch[8];

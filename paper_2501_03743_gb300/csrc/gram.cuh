@@ -1,0 +1,232 @@
+// Basis and Gram kernels of the direct-Gram s-step path, shared by the
+// DF64/F64 driver (sstep_gram.cu) and the mixed-precision driver (mixed.cu).
+#pragma once
+
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "small.cuh"
+#include "spmv.cuh"
+
+namespace sscg {
+
+namespace {
+
+// Basis recurrence coefficients: monomial u_{j+1} = w; Chebyshev
+// u_2 = (w - c u_1)/delta, u_{j+1} = 2 (w - c u_j)/delta - u_{j-1}.
+struct Basis {
+    int cheb;
+    double c, delta;
+};
+
+template <class A>
+__device__ __forceinline__ typename A::R basis_next(const Basis& B, int j, typename A::R w,
+                                                    const typename A::S* uj, const typename A::S* ujm1, int row) {
+    if (!B.cheb) return w;
+    typename A::R t = A::sub(w, A::mul(A::from_d(B.c), A::ld(uj + row)));
+    if (j == 0) return A::mul(t, A::from_d(1.0 / B.delta));
+    return A::sub(A::mul(t, A::from_d(2.0 / B.delta)), A::ld(ujm1 + row));
+}
+
+// AU_j = A u_j; with a diagonal preconditioner also u_{j+1}.
+template <class A, int VM>
+__global__ void __launch_bounds__(kThreads) k_level_gen(MatView M, const typename A::S* __restrict__ dinv,
+                                                        const typename A::S* __restrict__ u_in,
+                                                        const typename A::S* __restrict__ u_prev,
+                                                        typename A::S* __restrict__ au_out,
+                                                        typename A::S* __restrict__ u_next, int j, Basis B,
+                                                        int diag_prec, const Ctrl* ctrl) {
+    using R = typename A::R;
+    if (ctrl_done(ctrl)) return;
+    extern __shared__ __align__(16) char smem_raw[];
+    char* smem = align128(smem_raw);
+    spmv_pipe<A, VM, kStages>(
+        M, smem, [&](int c) { return A::ldg(u_in + c); },
+        [&](int row, R y) {
+            A::st(au_out + row, y);
+            if (u_next && diag_prec) {
+                R w = dinv ? A::mul(A::ld(dinv + row), y) : y;
+                A::st(u_next + row, basis_next<A>(B, j, w, u_in, u_prev, row));
+            }
+        },
+        const_cast<Ctrl*>(ctrl));
+}
+
+// u_{j+1} from w = B^-1 A u_j (general preconditioner).
+template <class A>
+__global__ void __launch_bounds__(kThreads) k_combine(int n, const typename A::S* __restrict__ w,
+                                                      const typename A::S* __restrict__ u_in,
+                                                      const typename A::S* __restrict__ u_prev,
+                                                      typename A::S* __restrict__ u_next, int j, Basis B,
+                                                      const Ctrl* ctrl) {
+    if (ctrl_done(ctrl)) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        A::st(u_next + i, basis_next<A>(B, j, A::ld(w + i), u_in, u_prev, i));
+}
+
+// Gram entries: e < ng: G(i, j), i >= j (u_i . AU_j); then m(i) (u_i . r);
+// then C(l, j) ((A p_l^old) . u_j) when a previous block exists.
+// then, with a true (replaced) residual, q(l) = p_l^old . r.
+struct GramShape {
+    int s, ng, nm, nc, nq, E, ncols;
+};
+
+__host__ __device__ inline GramShape gram_shape(int s, int has_old, int with_q = 0) {
+    GramShape g;
+    g.s = s;
+    g.ng = s * (s + 1) / 2;
+    g.nm = s;
+    g.nc = has_old ? s * s : 0;
+    g.nq = (has_old && with_q) ? s : 0;
+    g.E = g.ng + g.nm + g.nc + g.nq;
+    g.ncols = 2 * s + 1 + (has_old ? s : 0) + g.nq;
+    return g;
+}
+
+// Columns staged per tile: U_0..U_{s-1}, AU_0..AU_{s-1}, r,
+// AP_old_0..AP_old_{s-1}, P_old_0..P_old_{s-1}.
+__device__ __forceinline__ void gram_entry(const GramShape& g, int e, int& a, int& b) {
+    const int s = g.s;
+    if (e < g.ng) {  // lower-triangle index -> (i, j), i >= j
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= e) i++;
+        int j = e - i * (i + 1) / 2;
+        a = i;
+        b = s + j;
+    } else if (e < g.ng + g.nm) {
+        a = e - g.ng;
+        b = 2 * s;
+    } else if (e < g.ng + g.nm + g.nc) {
+        int q = e - g.ng - g.nm;
+        int l = q % s, j = q / s;
+        a = 2 * s + 1 + l;
+        b = j;
+    } else {
+        int l = e - g.ng - g.nm - g.nc;
+        a = 3 * s + 1 + l;
+        b = 2 * s;
+    }
+}
+
+constexpr int kGramTile = 128;  // rows staged per tile
+
+// Widening of a staged element to the arithmetic's storage type.
+template <class S, class TB>
+__device__ __forceinline__ S widen(TB v) {
+    return v;
+}
+template <>
+__device__ __forceinline__ float2 widen<float2, float>(float v) {
+    return make_float2(v, 0.f);
+}
+
+// TB: element type of the basis columns U (the new block's first s
+// columns, or `ublk` when given); AU (`au`, s columns), r and the old block
+// use A::S.  The
+// mixed-precision mode passes FP32 U with double-float AU, r and P_old.
+template <class A, int SB, class TB = typename A::S>
+__global__ void __launch_bounds__(kThreads) k_gram(int n, int ldn, int s, const typename A::S* __restrict__ blk_new,
+                                                   const TB* __restrict__ ublk, const typename A::S* __restrict__ au,
+                                                   const typename A::S* __restrict__ r,
+                                                   const typename A::S* __restrict__ blk_old, int has_old,
+                                                   int with_q, double* __restrict__ part, int step, Ctrl* ctrl) {
+    using R = typename A::R;
+    using S = typename A::S;
+    if (ctrl_done(ctrl)) return;
+    extern __shared__ __align__(16) char smem[];
+    S* tile = reinterpret_cast<S*>(smem);  // [ncols][kGramTile + 1]
+    constexpr int LD = kGramTile + 1;
+    const GramShape g = gram_shape(s, has_old, with_q);
+    // thread -> (entry, row group); entries beyond the thread count loop
+    const int groups = g.E >= kThreads ? 1 : kThreads / g.E;
+    const int active = g.E >= kThreads ? kThreads : g.E * groups;
+    constexpr int kMaxEPT = (SB * (SB + 1) / 2 + 2 * SB + SB * SB + kThreads - 1) / kThreads;
+    int ea[kMaxEPT], eb[kMaxEPT];
+    R acc[kMaxEPT];
+    const int grp = threadIdx.x / (g.E >= kThreads ? kThreads : g.E);
+    const int e0 = threadIdx.x % (g.E >= kThreads ? kThreads : g.E);
+#pragma unroll
+    for (int q = 0; q < kMaxEPT; q++) {
+        acc[q] = A::zero();
+        int e = e0 + q * kThreads;
+        if (e < g.E) gram_entry(g, e, ea[q], eb[q]);
+        else ea[q] = eb[q] = 0;
+    }
+    const size_t ld = (size_t)ldn;
+    const int ntiles = (n + kGramTile - 1) / kGramTile;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int r0 = t * kGramTile;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < g.ncols * kGramTile; idx += blockDim.x) {
+            int c = idx / kGramTile, i = idx % kGramTile, row = r0 + i;
+            S v;
+            if (row >= n) memset(&v, 0, sizeof(S));
+            else if (c < s) v = ublk ? widen<S, TB>(ublk[c * ld + row]) : blk_new[c * ld + row];
+            else if (c < 2 * s) v = au[(c - s) * ld + row];
+            else if (c == 2 * s) v = r[row];
+            else if (c <= 3 * s) v = blk_old[(s + (c - 2 * s - 1)) * ld + row];
+            else v = blk_old[(c - 3 * s - 1) * ld + row];
+            tile[c * LD + i] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < active) {
+#pragma unroll
+            for (int q = 0; q < kMaxEPT; q++) {
+                if (e0 + q * kThreads >= g.E) break;
+                const S* ta = tile + ea[q] * LD;
+                const S* tb = tile + eb[q] * LD;
+                R a = acc[q];
+                for (int i = grp; i < kGramTile; i += groups) a = A::fma(A::ld(ta + i), A::ld(tb + i), a);
+                acc[q] = a;
+            }
+        }
+    }
+    // combine the row groups of each entry, then one partial per entry
+    __syncthreads();
+    double* red = reinterpret_cast<double*>(smem);  // kThreads doubles (tile is free now)
+    const int G = gridDim.x;
+#pragma unroll
+    for (int q = 0; q < kMaxEPT; q++) {
+        red[threadIdx.x] = (threadIdx.x < active) ? A::to_d(acc[q]) : 0.0;
+        __syncthreads();
+        int e = e0 + q * kThreads;
+        if (grp == 0 && threadIdx.x < active && e < g.E) {
+            double t = 0.0;
+            for (int gg = 0; gg < groups; gg++) t += red[e0 + gg * (g.E >= kThreads ? kThreads : g.E)];
+            part[(size_t)e * G + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+    if (!last_cta(&ctrl->ticket[1])) return;
+    cta_sum_rows(part, g.E, G, [&](int e, double v) {
+        int a, b;
+        gram_entry(g, e, a, b);
+        if (e < g.ng) {
+            int i = a, j = b - s;
+            ctrl->G[i + j * s] = v;
+            ctrl->G[j + i * s] = v;
+        } else if (e < g.ng + g.nm) {
+            ctrl->m[a] = v;
+        } else if (e < g.ng + g.nm + g.nc) {
+            int l = a - 2 * s - 1, j = b;
+            ctrl->C[l + j * s] = v;
+        } else {
+            ctrl->q[a - 3 * s - 1] = v;
+        }
+    });
+    if (threadIdx.x == 0) ctrl->with_q = g.nq > 0;
+    __syncthreads();
+    SmallScratch* sc = reinterpret_cast<SmallScratch*>(smem);
+    if (threadIdx.x < 32) {
+        int st = warp_sw_gram(ctrl, s, step, sc);
+        if (threadIdx.x == 0 && st != 0) {
+            ctrl->status = st;
+            ctrl->done = 1;
+        }
+    }
+}
+
+}  // namespace
+
+}  // namespace sscg

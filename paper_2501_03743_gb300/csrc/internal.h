@@ -31,7 +31,7 @@ struct sscg_mat {
     double* diag;
     double* dinv;    // 1 / diag
     float2* dinv_df; // 1 / diag as a double-float
-    float2* ones_df; // unused slot kept for alignment
+    float* dinv_f;   // 1 / diag rounded to FP32 (mixed-precision basis)
     // properties
     int64_t bandwidth;
     int exact_fp32;
@@ -194,6 +194,9 @@ int bounds_workspace(const sscg_mat* mat, int steps, size_t* bytes);
 int estimate_bounds(sscg_ctx* ctx, const sscg_mat* mat, int steps, const double* r0, void* ws, size_t ws_bytes,
                     double* lmin, double* lmax);
 int splitmix_uniform(sscg_ctx* ctx, int64_t n, uint64_t seed, double* out);
+int mixed_workspace(const sscg_mat* mat, const sscg_opts* opts, size_t* bytes);
+int solve_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* opts,
+                sscg_info* info, void* ws, size_t ws_bytes, double blo, double bhi);
 
 // Steps of the Lanczos estimate a Chebyshev-basis solve runs when the caller
 // gives no basis interval, and the widening applied to its Ritz values.

@@ -1,0 +1,428 @@
+// Mixed-precision s-step solve (Section IV, item (ii): higher precision for
+// the moment-related computations).  The Krylov basis U that the
+// matrix-powers kernel builds each outer step is stored in FP32; A U is formed
+// from it in double-float (every product of two FP32 numbers is exact) and
+// stored in double-float, so the block the method works with satisfies
+// AU = A U to double-float accuracy whatever rounding U carries.  The Gram
+// sums, the direction blocks P, AP (the method's memory across steps), x and
+// r are double-float; the s x s solves are FP64.  Every `replace_every` outer steps the
+// residual is replaced by the true residual (Section IV, item (i)),
+// r = r0 - A (x - x0) with r0 = b - A x0, computed in double-float with the
+// matrix values to full precision, and convergence is tested on it.
+// Blocks are formed by the direct-Gram path (any basis), because the moment
+// recurrence of Algorithm 6 assumes the exact recurrences that FP32 storage
+// and residual replacement perturb.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "gram.cuh"
+#include "internal.h"
+#include "kernels.cuh"
+#include "small.cuh"
+#include "spmv.cuh"
+
+namespace sscg {
+
+namespace {
+
+// r0 = r, u_1 = B^-1 r in FP32.
+__global__ void k_mx_prep(int n, const float2* __restrict__ r, float2* __restrict__ r0,
+                          const float* __restrict__ dinv_f, float* __restrict__ u0, const Ctrl* ctrl) {
+    if (__ldcg(&ctrl->done)) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float2 v = r[i];
+        r0[i] = v;
+        u0[i] = dinv_f ? dinv_f[i] * v.x : v.x;
+    }
+}
+
+// AU_j = A u_j in double-float from the FP32 u_j; u_{j+1} from B^-1 AU_j by
+// the basis recurrence, rounded to FP32.
+template <int VM>
+__global__ void __launch_bounds__(kThreads) k_mx_level(MatView M, const float2* __restrict__ dinv_df,
+                                                       const float* __restrict__ u_in,
+                                                       const float* __restrict__ u_prev, float2* __restrict__ au_out,
+                                                       float* __restrict__ u_next, int j, Basis B, Ctrl* ctrl) {
+    if (__ldcg(&ctrl->done)) return;
+    extern __shared__ __align__(16) char smem_raw[];
+    char* smem = align128(smem_raw);
+    spmv_pipe<ArithDF64, VM, kStages>(
+        M, smem, [&](int c) { return df_make(__ldg(u_in + c), 0.f); },
+        [&](int row, df64 y) {
+            au_out[row] = make_float2(y.hi, y.lo);
+            if (u_next) {
+                df64 w = dinv_df ? df_mul(ArithDF64::ld(dinv_df + row), y) : y;
+                df64 un = w;
+                if (B.cheb) {
+                    df64 t = df_add(w, df_neg(df_mul(df_from_double(B.c), df_make(u_in[row], 0.f))));
+                    un = j == 0 ? df_mul(t, df_from_double(1.0 / B.delta))
+                                : df_add(df_mul(t, df_from_double(2.0 / B.delta)), df_make(-u_prev[row], 0.f));
+                }
+                u_next[row] = un.hi;
+            }
+        },
+        ctrl);
+}
+
+// Closes an outer step in the last CTA: step count, history, stop test.
+__device__ __forceinline__ void close_step(Ctrl* ctrl, double* hist, double rr) {
+    int step = ctrl->step + 1;
+    double rel = sqrt(rr) / ctrl->bnorm;
+    ctrl->step = step;
+    ctrl->relres = rel;
+    hist[step] = rel;
+    ctrl->nhist = step + 1;
+    if (!isfinite(rel)) {
+        ctrl->status = 2;
+        ctrl->done = 1;
+    } else if (rel < ctrl->tol) {
+        ctrl->status = 0;
+        ctrl->done = 1;
+    } else if (step >= ctrl->maxit) {
+        ctrl->status = 1;
+        ctrl->done = 1;
+    }
+}
+
+// P = U + P_old beta, AP = AU + AP_old beta, x += P alpha in double-float
+// (U, AU FP32); with write_r also r -= AP alpha, u_1 = B^-1 r in FP32 and the
+// stop test on the recursive residual (steps without residual replacement).
+template <int SB>
+__global__ void __launch_bounds__(kThreads) k_mx_update(int n, int ldn, int s, float* __restrict__ ublk,
+                                                        const float2* __restrict__ aublk,
+                                                        float2* __restrict__ p_new, const float2* __restrict__ p_old,
+                                                        float2* __restrict__ xw, float2* __restrict__ r,
+                                                        const float* __restrict__ dinv_f, double* __restrict__ part,
+                                                        int first, int write_r, Ctrl* ctrl,
+                                                        double* __restrict__ hist) {
+    if (__ldcg(&ctrl->done)) return;
+    __shared__ df64 sb[SB * SB];
+    __shared__ df64 sa[SB];
+    __shared__ double red[kThreads / 32];
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) sb[(e % s) + (e / s) * SB] = df_from_double(ctrl->beta[e]);
+    for (int e = threadIdx.x; e < s; e += blockDim.x) sa[e] = df_from_double(ctrl->alpha[e]);
+    __syncthreads();
+    const size_t ld = (size_t)ldn;
+    df64 rr = df_make(0.f, 0.f);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        df64 po[SB], apo[SB];
+        if (!first) {
+#pragma unroll
+            for (int l = 0; l < SB; l++)
+                if (l < s) {
+                    float2 a = p_old[l * ld + i], b = p_old[(s + l) * ld + i];
+                    po[l] = df_make(a.x, a.y);
+                    apo[l] = df_make(b.x, b.y);
+                }
+        }
+        df64 xa = df_make(0.f, 0.f), ra = df_make(0.f, 0.f);
+#pragma unroll
+        for (int jj = 0; jj < SB; jj++) {
+            if (jj < s) {
+                float2 a = aublk[jj * ld + i];
+                df64 p = df_make(ublk[jj * ld + i], 0.f), ap = df_make(a.x, a.y);
+                if (!first) {
+#pragma unroll
+                    for (int l = 0; l < SB; l++)
+                        if (l < s) {
+                            p = df_fma(po[l], sb[l + jj * SB], p);
+                            ap = df_fma(apo[l], sb[l + jj * SB], ap);
+                        }
+                }
+                p_new[jj * ld + i] = make_float2(p.hi, p.lo);
+                p_new[(s + jj) * ld + i] = make_float2(ap.hi, ap.lo);
+                xa = df_fma(p, sa[jj], xa);
+                ra = df_fma(ap, sa[jj], ra);
+            }
+        }
+        float2 xv = xw[i];
+        df64 xn = df_add(df_make(xv.x, xv.y), xa);
+        xw[i] = make_float2(xn.hi, xn.lo);
+        if (write_r) {
+            float2 rv = r[i];
+            df64 rn = df_add(df_make(rv.x, rv.y), df_neg(ra));
+            r[i] = make_float2(rn.hi, rn.lo);
+            ublk[i] = dinv_f ? dinv_f[i] * rn.hi : rn.hi;
+            rr = df_fma(rn, rn, rr);
+        }
+    }
+    if (!write_r) return;
+    df64 v[1] = {rr};
+    double out[1];
+    block_sum<ArithDF64, 1>(v, red, out);
+    if (threadIdx.x == 0) part[blockIdx.x] = out[0];
+    if (!last_cta(&ctrl->ticket[2])) return;
+    __shared__ double sh[32];
+    double t = cta_sum_partials(part, gridDim.x, sh);
+    if (threadIdx.x == 0) close_step(ctrl, hist, t);
+}
+
+// Residual replacement: r = r0 - A (x - x0) in double-float, u_1 = B^-1 r
+// in FP32; the stop test on this true residual.
+template <int VM>
+__global__ void __launch_bounds__(kThreads) k_mx_replace(MatView M, const float2* __restrict__ xw,
+                                                         const float2* __restrict__ r0, float2* __restrict__ r,
+                                                         const float* __restrict__ dinv_f, float* __restrict__ u0,
+                                                         double* __restrict__ part, Ctrl* ctrl,
+                                                         double* __restrict__ hist) {
+    if (__ldcg(&ctrl->done)) return;
+    extern __shared__ __align__(16) char smem_raw[];
+    char* smem = align128(smem_raw);
+    __shared__ double red[kThreads / 32];
+    df64 rr = df_make(0.f, 0.f);
+    const bool ok = spmv_pipe<ArithDF64, VM, kStages>(
+        M, smem, [&](int c) { return ArithDF64::ldg(xw + c); },
+        [&](int row, df64 y) {
+            float2 a = r0[row];
+            df64 rn = df_add(df_make(a.x, a.y), df_neg(y));
+            r[row] = make_float2(rn.hi, rn.lo);
+            u0[row] = dinv_f ? dinv_f[row] * rn.hi : rn.hi;
+            rr = df_fma(rn, rn, rr);
+        },
+        ctrl);
+    if (!ok) return;
+    df64 v[1] = {rr};
+    double out[1];
+    block_sum<ArithDF64, 1>(v, red, out);
+    if (threadIdx.x == 0) part[blockIdx.x] = out[0];
+    if (!last_cta(&ctrl->ticket[3])) return;
+    __shared__ double sh[32];
+    double t = cta_sum_partials(part, gridDim.x, sh);
+    if (threadIdx.x == 0) close_step(ctrl, hist, t);
+}
+
+struct MLayout {
+    int64_t ldn;
+    Ctrl* ctrl;
+    double* hist;
+    double* part;
+    float* ublk;       // U, FP32, rebuilt every outer step
+    float2* aublk;     // A U, double-float
+    float2* pblk[2];   // P | AP, double-float, alternating new / old
+    float2* r;
+    float2* r0;
+    float2* xw;
+    double* bdev;
+    double* xdev;
+    size_t bytes;
+};
+
+MLayout mplan(const sscg_mat* mat, const sscg_opts* o, void* base, size_t cap) {
+    MLayout L{};
+    L.ldn = (int64_t)align_up((size_t)mat->n, 64);
+    Carve c(base, cap);
+    L.ctrl = c.take<Ctrl>(1);
+    L.hist = c.take<double>((size_t)o->maxit + 2);
+    L.part = c.take<double>((size_t)kMaxGrid * (o->s * (o->s + 1) / 2 + 2 * o->s + o->s * o->s + 4));
+    L.ublk = c.take<float>((size_t)L.ldn * o->s);
+    L.aublk = c.take<float2>((size_t)L.ldn * o->s);
+    L.pblk[0] = c.take<float2>((size_t)L.ldn * 2 * o->s);
+    L.pblk[1] = c.take<float2>((size_t)L.ldn * 2 * o->s);
+    L.r = c.take<float2>((size_t)L.ldn);
+    L.r0 = c.take<float2>((size_t)L.ldn);
+    L.xw = c.take<float2>((size_t)L.ldn);
+    if (o->flags & SSCG_HOST_VECTORS) {
+        L.bdev = c.take<double>((size_t)L.ldn);
+        L.xdev = c.take<double>((size_t)L.ldn);
+    }
+    L.bytes = c.used;
+    return L;
+}
+
+template <int VM, int SB>
+int run_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o, const MLayout& L,
+              Basis basis, Ctrl* hctrl, Prof& P) {
+    cudaStream_t st = ctx->stream;
+    const int n = (int)mat->n, s = o->s;
+    const int cap = stage_cap(mat);
+    MatView M;
+    M.n = n;
+    M.cap = cap;
+    M.rowptr = mat->rowptr;
+    M.col = mat->col;
+    M.val = mat->val;
+    M.vhi = mat->vhi;
+    M.vlo = mat->vlo;
+    const bool jac = mat->prec == SSCG_PREC_JACOBI;
+    const float* dinv_f = jac ? mat->dinv_f : nullptr;
+    const float2* dinv_df = jac ? mat->dinv_df : nullptr;
+    const size_t smem_init = stage_bytes<ArithDF64, VM>(cap);
+    const size_t smem_lvl = pipe_bytes<VAL_F32, kStages>(cap) + 128;
+    const size_t smem_df = pipe_bytes<VM, kStages>(cap) + 128;
+    const size_t smem64 = stage_bytes<ArithF64, VAL_F64>(cap);
+    const GramShape gs_full = gram_shape(s, 1, 1);
+    const size_t smem_gram = std::max({(size_t)gs_full.ncols * (kGramTile + 1) * sizeof(float2), sizeof(SmallScratch),
+                                       (size_t)kThreads * sizeof(double)});
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<ArithDF64, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_init));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_mx_level<VAL_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_lvl));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_gram<ArithDF64, SB, float>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gram));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_mx_replace<VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_true_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
+    const int Gi = occupancy_grid(ctx, k_init<ArithDF64, VM>, smem_init, n);
+    const int Gl = occupancy_grid(ctx, k_mx_level<VAL_F32>, smem_lvl, n);
+    const int Gg = occupancy_grid(ctx, k_gram<ArithDF64, SB, float>, smem_gram, n);
+    const int Gu = occupancy_grid(ctx, k_mx_update<SB>, 0, n);
+    const int Gr = occupancy_grid(ctx, k_mx_replace<VM>, smem_df, n);
+    const int Ge = occupancy_grid(ctx, k_mx_prep, 0, n);
+    const int Gt = occupancy_grid(ctx, k_true_res, smem64, n);
+    const size_t ld = (size_t)L.ldn;
+    const int every = o->replace_every > 0 ? o->replace_every : 1;
+
+    P.begin();
+    k_init<ArithDF64, VM><<<Gi, kThreads, smem_init, st>>>(M, dinv_df, b, x, L.xw, L.r, nullptr, L.part, L.ctrl,
+                                                           L.hist);
+    k_mx_prep<<<Ge, kThreads, 0, st>>>(n, L.r, L.r0, dinv_f, L.ublk, L.ctrl);
+    P.end(FAM_INIT, 0);
+    P.launches++;
+    SSCG_CUDA(ctx, cudaGetLastError());
+    const int per_chunk = std::max(1, 32 / (s + 3));
+    cudaEvent_t ev[2];
+    SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    int launched = 0, chunk = 0, pending = -1, err = 0;
+    while (launched < o->maxit) {
+        int c = std::min(per_chunk, o->maxit - launched);
+        for (int q = 0; q < c; q++) {
+            const int k = launched + q;
+            float* ub = L.ublk;
+            float2* aub = L.aublk;
+            float2* pn = L.pblk[k & 1];
+            float2* po = L.pblk[(k + 1) & 1];
+            P.begin();
+            for (int j = 0; j < s; j++) {
+                float* unext = j + 1 < s ? ub + (j + 1) * ld : nullptr;
+                const float* uprev = j > 0 ? ub + (j - 1) * ld : nullptr;
+                k_mx_level<VAL_F32><<<Gl, kThreads, smem_lvl, st>>>(M, dinv_df, ub + j * ld, uprev, aub + j * ld,
+                                                                    unext, j, basis, L.ctrl);
+                if (j + 1 < s) P.launches++;
+            }
+            P.end(FAM_MPK, k);
+            P.begin();
+            k_gram<ArithDF64, SB, float><<<Gg, kThreads, smem_gram, st>>>(n, (int)L.ldn, s, nullptr, ub, aub, L.r,
+                                                                          po, k > 0 ? 1 : 0, 1, L.part, k, L.ctrl);
+            P.end(FAM_DIR, k);
+            const bool replace = (k + 1) % every == 0;
+            P.begin();
+            k_mx_update<SB><<<Gu, kThreads, 0, st>>>(n, (int)L.ldn, s, ub, aub, pn, po, L.xw, L.r, dinv_f, L.part,
+                                                     k == 0, replace ? 0 : 1, L.ctrl, L.hist);
+            if (replace) {
+                k_mx_replace<VM><<<Gr, kThreads, smem_df, st>>>(M, L.xw, L.r0, L.r, dinv_f, ub, L.part, L.ctrl,
+                                                                L.hist);
+                P.launches++;
+            }
+            P.end(FAM_UPDATE, k);
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+            err = 1;
+            break;
+        }
+        launched += c;
+        const int slot = chunk & 1;
+        SSCG_CUDA(ctx, cudaMemcpyAsync((void*)(ctx->pinned + slot), &L.ctrl->done, sizeof(int),
+                                       cudaMemcpyDeviceToHost, st));
+        SSCG_CUDA(ctx, cudaEventRecord(ev[slot], st));
+        if (pending >= 0) {
+            SSCG_CUDA(ctx, cudaEventSynchronize(ev[pending & 1]));
+            if (ctx->pinned[pending & 1]) break;
+        }
+        pending = chunk++;
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (err) return set_err(ctx, SSCG_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    P.begin();
+    k_export_x<ArithDF64><<<Ge, kThreads, 0, st>>>(n, L.xw, x, L.ctrl);
+    k_true_res<<<Gt, kThreads, smem64, st>>>(M, b, x, L.part, L.ctrl);
+    P.end(FAM_FINAL, 0);
+    P.launches++;
+    SSCG_CUDA(ctx, cudaGetLastError());
+    SSCG_CUDA(ctx, cudaMemcpyAsync(hctrl, L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    SSCG_CUDA(ctx, cudaStreamSynchronize(st));
+    return 0;
+}
+
+}  // namespace
+
+int mixed_workspace(const sscg_mat* mat, const sscg_opts* o, size_t* bytes) {
+    *bytes = mplan(mat, o, nullptr, 0).bytes;
+    return 0;
+}
+
+int solve_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o,
+                sscg_info* info, void* ws, size_t ws_bytes, double blo, double bhi) {
+    size_t need = 0;
+    mixed_workspace(mat, o, &need);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255))
+        return set_err(ctx, SSCG_ERR_SPACE, "workspace needs %zu bytes, 256-byte aligned (got %zu)", need, ws_bytes);
+    MLayout L = mplan(mat, o, ws, ws_bytes);
+    cudaStream_t st = ctx->stream;
+    const int64_t n = mat->n;
+    const double* bd = b;
+    double* xd = x;
+    if (o->flags & SSCG_HOST_VECTORS) {
+        SSCG_CUDA(ctx, cudaMemcpyAsync(L.bdev, b, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        SSCG_CUDA(ctx, cudaMemcpyAsync(L.xdev, x, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        bd = L.bdev;
+        xd = L.xdev;
+    }
+    Ctrl h;
+    memset(&h, 0, sizeof(h));
+    h.status = 1;
+    h.maxit = o->maxit;
+    h.s = o->s;
+    h.tol = o->tol;
+    SSCG_CUDA(ctx, cudaMemcpyAsync(L.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    Basis basis;
+    basis.cheb = o->basis == SSCG_BASIS_CHEBYSHEV;
+    basis.c = 0.5 * (bhi + blo);
+    basis.delta = 0.5 * (bhi - blo);
+    const int s = o->s;
+    Prof* prof = new Prof(ctx, (o->flags & SSCG_PROFILE) != 0);
+    if (!prof->reserve((int)std::min<int64_t>(65536, (int64_t)o->maxit * 3 + 64))) {
+        delete prof;
+        return set_err(ctx, SSCG_ERR_CUDA, "could not create profiling events");
+    }
+    int rc;
+    if (mat->exact_fp32) {
+        if (s <= 4) rc = run_mixed<VAL_F32, 4>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
+        else if (s <= 8) rc = run_mixed<VAL_F32, 8>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
+        else rc = run_mixed<VAL_F32, 16>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
+    } else {
+        if (s <= 4) rc = run_mixed<VAL_DF, 4>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
+        else if (s <= 8) rc = run_mixed<VAL_DF, 8>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
+        else rc = run_mixed<VAL_DF, 16>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
+    }
+    if (rc) {
+        delete prof;
+        return rc;
+    }
+    if (o->flags & SSCG_HOST_VECTORS) {
+        SSCG_CUDA(ctx, cudaMemcpyAsync(x, L.xdev, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        SSCG_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    if (h.status == SSCG_ERR_NONFINITE) {
+        delete prof;
+        return set_err(ctx, SSCG_ERR_NONFINITE, "non-finite right-hand side or x0");
+    }
+    if (info) fill_profile(info, *prof, h.step);
+    delete prof;
+    if (info) {
+        info->status = h.status;
+        info->outer_iters = h.step;
+        info->equiv_iters = (int64_t)h.step * s;
+        info->rel_res_recursive = h.relres;
+        info->rel_res_true = h.zero_rhs ? 0.0 : sqrt(h.true_res2) / h.bnorm;
+        int len = std::min(h.nhist, info->hist_cap);
+        if (info->hist && len > 0)
+            SSCG_CUDA(ctx, cudaMemcpy(info->hist, L.hist, len * sizeof(double), cudaMemcpyDeviceToHost));
+        info->hist_len = info->hist ? len : 0;
+    }
+    return h.status;
+}
+
+}  // namespace sscg

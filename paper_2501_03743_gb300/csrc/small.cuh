@@ -133,7 +133,10 @@ __device__ inline int warp_sw_monomial(Ctrl* ctrl, int s, int step, SmallScratch
 
 // The same step with Gram blocks formed directly (any basis):
 //   step 0:  W = G, beta = 0;  step > 0: W_prev beta = -C, W = G + C^T beta
-//   W alpha = m.   G, C (column-major, C(l,j) = (A p_l^old) . u_j) and m in ctrl.
+//   W alpha = m (+ beta^T q when q = P_old^T r was formed: the right-hand
+//   side P^T r of Section II-A for a residual that is not exactly orthogonal
+//   to P_old, as after residual replacement).
+//   G, C (column-major, C(l,j) = (A p_l^old) . u_j), m and q in ctrl.
 __device__ inline int warp_sw_gram(Ctrl* ctrl, int s, int step, SmallScratch* sc) {
     const int lane = threadIdx.x & 31;
     if (step == 0) {
@@ -158,7 +161,12 @@ __device__ inline int warp_sw_gram(Ctrl* ctrl, int s, int step, SmallScratch* sc
     }
     __syncwarp();
     for (int e = lane; e < s * s; e += 32) sc->L[e] = sc->Wn[e];
-    if (lane < s) sc->a[lane] = ctrl->m[lane];
+    if (lane < s) {
+        double mi = ctrl->m[lane];
+        if (step > 0 && ctrl->with_q)
+            for (int l = 0; l < s; l++) mi += sc->X[l + lane * s] * ctrl->q[l];
+        sc->a[lane] = mi;
+    }
     __syncwarp();
     if (!warp_cholesky(sc->L, s)) return 2;
     if (!warp_chol_solve(sc->L, s, sc->a, 1)) return 2;

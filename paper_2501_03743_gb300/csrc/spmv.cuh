@@ -43,6 +43,13 @@ struct Val<ArithDF64, VAL_F32> {
 };
 
 template <>
+struct Val<ArithF32, VAL_F32> {
+    using T = float;
+    __device__ static __forceinline__ T load(const MatView& M, int k) { return __ldg(M.vhi + k); }
+    __device__ static __forceinline__ float mac(float acc, T v, float x) { return fmaf(v, x, acc); }
+};
+
+template <>
 struct Val<ArithDF64, VAL_DF> {
     using T = float2;
     __device__ static __forceinline__ T load(const MatView& M, int k) {
@@ -194,6 +201,10 @@ __device__ __forceinline__ double stage_val<ArithF64, VAL_F64>(const char* v0, c
 }
 template <>
 __device__ __forceinline__ float stage_val<ArithDF64, VAL_F32>(const char* v0, const char*, int k) {
+    return reinterpret_cast<const float*>(v0)[k];
+}
+template <>
+__device__ __forceinline__ float stage_val<ArithF32, VAL_F32>(const char* v0, const char*, int k) {
     return reinterpret_cast<const float*>(v0)[k];
 }
 template <>

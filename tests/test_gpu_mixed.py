@@ -1,0 +1,85 @@
+"""The mixed-precision mode (FP32 basis blocks and SpMV values, double-float
+Gram sums, x and r, FP64 s x s solves, true-residual replacement) against
+the FP64 oracle: it must reach the requested true residual, and its error
+against the oracle's FP64 solution is reported (bounded here by the
+conditioning at tol 1e-10)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_03743_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2501_03743_gb300 import sscg  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2501_03743_gb300 import build
+
+    build.build()
+    return sscg.Context()
+
+
+def solve(A, b, **kw):
+    bt = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    xt = torch.zeros_like(bt)
+    r = sscg.Solver(A, **kw).solve(bt, xt)
+    return xt.cpu().numpy(), r
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+CASES = [("poisson27", 24, 0.0), ("varcoef7", 20, 1.0)]
+
+
+@pytest.mark.parametrize("kind,N,sigma", CASES)
+@pytest.mark.parametrize("basis,s", [("monomial", 4), ("chebyshev", 8)])
+@pytest.mark.parametrize("every", [1, 2])
+def test_mixed_reaches_tolerance_and_matches_fp64(ctx, kind, N, sigma, basis, s, every):
+    S = inputs.system(kind, N, seed=3, sigma=sigma)
+    A = sscg.Matrix(ctx, S["rowptr"], S["col"], S["val"])
+    tol = 1e-10
+    x, r = solve(A, S["b"], s=s, basis=basis, tol=tol, maxit=2000, arith="mixed", replace_every=every)
+    assert r.status == sscg.OK, r
+    assert r.rel_res_true < 2 * tol
+    M = oracle.as_matrix(S)
+    ref = oracle.pcg(M, S["b"], tol=tol, maxit=5000)
+    assert ref.status == oracle.OK
+    err = rel(x, ref.x)
+    # both solutions satisfy ||b - A x||/||b|| < 1e-10; their distance is
+    # bounded by kappa * 2e-10 and far below that in practice
+    assert err < 1e-7, err
+    # an FP32 basis perturbs the block A-conjugacy the short recurrence relies
+    # on, which costs outer steps; the count is reported, bounded loosely here
+    assert r.equiv_iters <= 4 * ref.iters + s
+
+
+def test_mixed_history_is_the_true_residual(ctx):
+    """With replacement every step, the recorded residual is b - A x itself."""
+    S = inputs.system("poisson27", 16, seed=4)
+    A = sscg.Matrix(ctx, S["rowptr"], S["col"], S["val"])
+    x, r = solve(A, S["b"], s=4, tol=1e-10, maxit=500, arith="mixed", replace_every=1)
+    true = np.linalg.norm(S["b"] - oracle.spmv(oracle.as_matrix(S), x)) / np.linalg.norm(S["b"])
+    assert abs(r.hist[-1] - true) < 1e-12 and abs(r.rel_res_true - true) < 1e-12
+
+
+@pytest.mark.slow
+def test_mixed_27point_192(ctx):
+    """27-point stencil on 192^3, FP32 values and basis, residual replaced
+    every outer step, tol 1e-10; error against the DF64 solve reported."""
+    S = inputs.system("poisson27", 192, seed=0)
+    A = sscg.Matrix(ctx, S["rowptr"], S["col"], S["val"])
+    x, r = solve(A, S["b"], s=4, tol=1e-10, maxit=2000, arith="mixed", replace_every=1)
+    assert r.status == sscg.OK and r.rel_res_true < 2e-10
+    xd, rd = solve(A, S["b"], s=4, tol=1e-10, maxit=2000, arith="df64")
+    assert rd.status == sscg.OK
+    assert rel(x, xd) < 1e-7
+    assert rel(x, S["x_true"]) < 1e-7
