@@ -84,6 +84,8 @@ def lib():
         L.orc_mlp_nparams.argtypes = [i32, i32, i32]; L.orc_mlp_nparams.restype = i64
         L.orc_mlp_forward.argtypes = [i32, i32, i32, vp, i32, vp, vp]
         L.orc_mlp_loss_grad.argtypes = [i32, i32, i32, vp, i32, vp, vp, vp]; L.orc_mlp_loss_grad.restype = dbl
+        L.orc_features.argtypes = [P(_Csr), vp]; L.orc_features.restype = i32
+        L.orc_adam_step.argtypes = [i64, vp, vp, vp, vp, dbl, dbl, dbl, dbl, i32]
         L.orc_num_threads.restype = i32
         _lib = L
     return _lib
@@ -294,3 +296,23 @@ def mlp_loss_grad(d, h, o, theta, X, T):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+NFEAT = 10
+
+
+def features(A):
+    """The ten matrix features of the spectral-bound network (orc_features)."""
+    A = as_matrix(A)
+    f = np.zeros(NFEAT)
+    if lib().orc_features(C.byref(A.c), _ptr(f)) != 0:
+        raise ValueError("non-positive diagonal")
+    return f
+
+
+def adam_step(theta, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step in place on theta, m, v (orc_adam_step)."""
+    for a in (theta, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _f64(g)
+    lib().orc_adam_step(theta.size, _ptr(theta), _ptr(g), _ptr(m), _ptr(v), lr, b1, b2, eps, int(t))

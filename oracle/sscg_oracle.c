@@ -12,6 +12,8 @@
  *                      alpha from W alpha = m), for any polynomial basis
  *   - orc_lanczos_bounds : Ritz values from the CG coefficients
  *   - orc_mlp_*      : the spectral-bound network in FP64
+ *   - orc_features   : matrix features the network reads
+ *   - orc_adam_step  : the optimiser step that trains it
  * Compiled with -ffp-contract=off so that x86 and Arm hosts round the same.
  */
 #include "sscg_oracle.h"
@@ -740,4 +742,73 @@ double orc_mlp_loss_grad(int d, int h, int o, const double* th, int batch, const
     }
     free(h1); free(h2); free(y); free(dy); free(d2); free(d1);
     return loss;
+}
+
+/* ------------------------------------------------- features and optimiser */
+
+int orc_features(const orc_csr* A, double* f) {
+    int64_t n = A->n;
+    double* d = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    orc_diag(A, d);
+    /* first pass: means, extremes, dominance */
+    double s1 = 0.0, dmin = INFINITY, dmax = -INFINITY, dom = 0.0;
+    double cnt = 0.0, c1 = 0.0, cmin = INFINITY;
+    for (int64_t i = 0; i < n; i++) {
+        if (!(d[i] > 0.0)) { free(d); return -1; }
+        double ld = log(d[i]);
+        s1 += ld;
+        if (ld < dmin) dmin = ld;
+        if (ld > dmax) dmax = ld;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        double off = 0.0;
+        for (int64_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {
+            int64_t j = A->col[k];
+            if (j == i) continue;
+            double a = fabs(A->val[k]);
+            off += a;
+            if (a > 0.0) {
+                double lc = log(a / sqrt(d[i] * d[j]));
+                cnt += 1.0; c1 += lc;
+                if (lc < cmin) cmin = lc;
+            }
+        }
+        dom += off / d[i];
+    }
+    double mean = s1 / (double)n, cm = cnt > 0.0 ? c1 / cnt : 0.0;
+    /* second pass: spreads about the means */
+    double s2 = 0.0, c2 = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double e = log(d[i]) - mean;
+        s2 += e * e;
+        for (int64_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {
+            int64_t j = A->col[k];
+            double a = fabs(A->val[k]);
+            if (j == i || !(a > 0.0)) continue;
+            double ec = log(a / sqrt(d[i] * d[j])) - cm;
+            c2 += ec * ec;
+        }
+    }
+    f[0] = log((double)n) / 3.0;
+    f[1] = log((double)A->rowptr[n] / (double)n);
+    f[2] = mean;
+    f[3] = sqrt(s2 / (double)n);
+    f[4] = dmin - mean;
+    f[5] = dmax - mean;
+    f[6] = dom / (double)n;
+    f[7] = cm;
+    f[8] = cnt > 0.0 ? sqrt(c2 / cnt) : 0.0;
+    f[9] = cnt > 0.0 ? cmin : 0.0;
+    free(d);
+    return 0;
+}
+
+void orc_adam_step(int64_t np, double* theta, const double* g, double* m, double* v,
+                   double lr, double b1, double b2, double eps, int t) {
+    double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+    for (int64_t i = 0; i < np; i++) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        theta[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
 }

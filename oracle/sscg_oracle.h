@@ -103,6 +103,25 @@ void orc_mlp_forward(int d, int h, int o, const double* theta, int batch, const 
 double orc_mlp_loss_grad(int d, int h, int o, const double* theta, int batch, const double* X,
                          const double* T, double* grad);
 
+/* Matrix features for the spectral-bound network (the paper gives none; the
+ * definitions are this project's).  With d_i = a_ii and, over the
+ * off-diagonal entries, c_ij = |a_ij| / sqrt(d_i d_j):
+ *   f0 = ln(n)/3            f1 = ln(nnz/n)
+ *   f2 = mean ln d          f3 = std ln d (population)
+ *   f4 = min ln d - f2      f5 = max ln d - f2
+ *   f6 = mean_i (sum_{j!=i} |a_ij|) / d_i
+ *   f7 = mean ln c          f8 = std ln c           f9 = min ln c
+ * Off-diagonal zeros are skipped in f7-f9.  Returns 0, or -1 if a diagonal
+ * entry is not positive. */
+#define ORC_NFEAT 10
+int orc_features(const orc_csr* A, double* f);
+
+/* One Adam step (Kingma and Ba, 2015) with bias correction at step t >= 1:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * theta -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps). */
+void orc_adam_step(int64_t np, double* theta, const double* g, double* m, double* v,
+                   double lr, double b1, double b2, double eps, int t);
+
 int orc_num_threads(void);
 
 #ifdef __cplusplus

@@ -33,6 +33,11 @@ MUTANTS = {
     "lanczos-diag-term": ("d[j] = 1.0 / a[j] + (j > 0 ? bb[j - 1] / a[j - 1] : 0.0);", "d[j] = 1.0 / a[j];"),
     "chol-back-substitution": ("t -= L[k + (size_t)i * n] * x[k];", "t -= L[i + (size_t)k * n] * x[k];"),
     "mlp-tanh-derivative": ("d2[j] = t * (1.0 - h2[j] * h2[j]);", "d2[j] = t * (1.0 - h2[j]);"),
+    "features-coupling-scale": ("double lc = log(a / sqrt(d[i] * d[j]));", "double lc = log(a / sqrt(d[i] * d[i]));"),
+    "features-std-mean": ("double e = log(d[i]) - mean;", "double e = log(d[i]);"),
+    "adam-bias-correction": ("theta[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);",
+                             "theta[i] -= lr * m[i] / (sqrt(v[i] / c2) + eps);"),
+    "adam-moment-weights": ("v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];", "v[i] = b1 * v[i] + (1.0 - b1) * g[i] * g[i];"),
     "pfcg-gamma-sign": ("p[i] = u[i] - c * p[i];", "p[i] = u[i] + c * p[i];"),
     "spmv-dropped-diagonal": ("for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) t += A->val[k] * x[A->col[k]];\n        y[i] = t;",
                               "for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) if (A->col[k] != i) t += A->val[k] * x[A->col[k]];\n        y[i] = t;"),

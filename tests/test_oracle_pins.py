@@ -452,6 +452,88 @@ def test_mlp_forward_special_case():
     assert np.allclose(Y, (W3 @ np.tanh(b2) + b3)[None, :], rtol=1e-15, atol=1e-15)
 
 
+# ------------------------------------------------- features and optimiser
+
+def test_features_closed_form_poisson7():
+    """Constant 7-point stencil on N^3: every diagonal is 6 and every coupling
+    |a_ij|/sqrt(d_i d_j) is 1/6, so the spreads vanish; nnz = 7n - 6N^2."""
+    N = 5
+    A = inputs.system("poisson7", N, seed=0)
+    n = N ** 3
+    nnz = 7 * n - 6 * N * N
+    assert int(A["rowptr"][-1]) == nnz
+    f = oracle.features(A)
+    want = [np.log(N), np.log(nnz / n), np.log(6.0), 0.0, 0.0, 0.0, (nnz - n) / (6.0 * n),
+            np.log(1 / 6), 0.0, np.log(1 / 6)]
+    assert np.allclose(f, want, rtol=1e-13, atol=1e-13)
+
+
+def test_features_closed_form_poisson27():
+    N = 4
+    A = inputs.system("poisson27", N, seed=0)
+    n = N ** 3
+    nnz = int(A["rowptr"][-1])
+    assert nnz == (3 * N - 2) ** 3  # a 1-D factor of N + 2(N-1) entries per direction
+    f = oracle.features(A)
+    assert np.allclose(f[[2, 7, 9]], [np.log(26.0), np.log(1 / 26), np.log(1 / 26)], rtol=1e-13)
+    assert np.allclose(f[[3, 4, 5, 8]], 0.0, atol=1e-13)
+    assert abs(f[6] - (nnz - n) / (26.0 * n)) < 1e-14
+
+
+def test_features_two_valued_diagonal():
+    """Diagonal matrix with entries e^a and e^b, two of each: mean (a+b)/2,
+    standard deviation |a-b|/2; no off-diagonal entries."""
+    a, b = -0.7, 1.9
+    D = np.diag(np.exp([a, b, b, a]))
+    f = oracle.features(oracle.Matrix.from_dense(D))
+    want = [np.log(4) / 3, 0.0, (a + b) / 2, (b - a) / 2, -(b - a) / 2, (b - a) / 2, 0.0, 0.0, 0.0, 0.0]
+    assert np.allclose(f, want, rtol=1e-13, atol=1e-13)
+
+
+def test_features_scaling_invariances():
+    """Scaling A by c shifts the mean log-diagonal by ln c and leaves the rest;
+    a symmetric diagonal scaling S A S leaves the couplings (f7-f9) alone."""
+    _, D = random_spd_csr(30, seed=11)
+    f = oracle.features(oracle.Matrix.from_dense(D))
+    g = oracle.features(oracle.Matrix.from_dense(3.5 * D))
+    assert abs(g[2] - f[2] - np.log(3.5)) < 1e-13
+    assert np.allclose(np.delete(g, 2), np.delete(f, 2), rtol=1e-12, atol=1e-13)
+    s = np.exp(inputs.uniform(12, 30))
+    h = oracle.features(oracle.Matrix.from_dense(D * s[:, None] * s[None, :]))
+    assert np.allclose(h[7:], f[7:], rtol=1e-12, atol=1e-13)
+    assert abs(h[2] - f[2] - 2 * np.mean(np.log(s))) < 1e-12
+    # the coupling of a 2x2 block [[p, q], [q, r]] is |q|/sqrt(pr)
+    t = oracle.features(oracle.Matrix.from_dense(np.array([[4.0, -1.0], [-1.0, 9.0]])))
+    assert np.allclose(t[7:], [np.log(1 / 6), 0.0, np.log(1 / 6)], rtol=1e-14)
+    assert abs(t[6] - (1 / 4 + 1 / 9) / 2) < 1e-15
+
+
+def test_adam_constant_gradient_closed_form():
+    """With a constant gradient the bias-corrected moments equal g and g^2, so
+    every step moves theta by lr g / (|g| + eps)."""
+    g = inputs.uniform(5, 7)
+    theta = inputs.uniform(6, 7)
+    t0 = theta.copy()
+    m, v = np.zeros(7), np.zeros(7)
+    for t in range(1, 6):
+        oracle.adam_step(theta, g, m, v, t, lr=0.01)
+    assert np.allclose(theta, t0 - 5 * 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-13, atol=1e-15)
+
+
+def test_adam_alternating_gradient_closed_form():
+    """Gradients g then -g: after two steps m/(1-b1^2) = -(1-b1)/(1+b1) g and
+    v/(1-b2^2) = g^2, so the second step moves by +lr (1-b1)/(1+b1) g/(|g|+eps)."""
+    b1, b2, lr, eps = 0.8, 0.95, 0.1, 1e-8
+    g = inputs.uniform(7, 5)
+    theta = np.zeros(5)
+    m, v = np.zeros(5), np.zeros(5)
+    oracle.adam_step(theta, g, m, v, 1, lr, b1, b2, eps)
+    after1 = theta.copy()
+    assert np.allclose(after1, -lr * g / (np.abs(g) + eps), rtol=1e-14)
+    oracle.adam_step(theta, -g, m, v, 2, lr, b1, b2, eps)
+    assert np.allclose(theta - after1, lr * (1 - b1) / (1 + b1) * g / (np.abs(g) + eps), rtol=1e-12)
+
+
 # ------------------------------------------------------- the paper's count
 
 @pytest.mark.slow
