@@ -80,7 +80,9 @@ typedef struct sscg_mat sscg_mat;
 typedef struct {
     int s;              /* block size, 1..16 (Alg. 3) */
     int basis;          /* sscg_basis */
-    double basis_lmin;  /* Chebyshev basis: spectral interval of B^-1 A; 0,0 = from the matrix's bounds */
+    double basis_lmin;  /* Chebyshev basis: spectral interval of B^-1 A; 0,0 = estimated by the solve:
+                           the matrix's bounds network (sscg_set_bounds_model) under the Jacobi
+                           preconditioner, else 20 Lanczos steps; widened by 0.95 / 1.05 */
     double basis_lmax;
     double tol;         /* stop when ||r||_2 / ||b||_2 < tol, r the recursive residual */
     int maxit;          /* outer steps (each is s CG steps), >= 0 */
@@ -224,6 +226,8 @@ int sscg_bounds_workspace_bytes(const sscg_mat* mat, int steps, size_t* bytes);
  * T_{j,j+1} = sqrt(beta_j)/alpha_j, whose extreme eigenvalues (bisection on
  * the Sturm count, on the device) approach the spectrum's ends from inside.
  * These are the spectral bounds the Chebyshev basis (Section IV) needs.
+ * CG stops early once ||r|| <= 1e-14 ||r0||, where the Krylov space is
+ * invariant to working precision (more steps would only add rounding noise).
  * r0: device FP64 vector of length n, or NULL for the library's fixed
  * pseudo-random start (splitmix64, seed 0x5EED5EED).  Errors:
  * SSCG_ERR_INVALID, SSCG_ERR_SPACE, SSCG_ERR_CUDA; SSCG_BREAKDOWN if CG
@@ -235,6 +239,81 @@ int sscg_estimate_bounds(sscg_ctx* ctx, const sscg_mat* mat, int steps, const do
  * z = mix(seed + (i+1) 0x9E3779B97F4A7C15), out = 2 (z >> 11) 2^-53 - 1.
  * A seeded device generator for start vectors and synthetic inputs. */
 int sscg_uniform(sscg_ctx* ctx, int64_t n, uint64_t seed, double* out);
+
+
+/* -------------------------------------------- spectral-bound network
+ *
+ * A learned alternative to sscg_estimate_bounds: a multilayer perceptron
+ * maps ten features of the matrix to (ln lambda_min, ln lambda_max) of
+ * D^-1 A (D the diagonal of A).  The paper names the Chebyshev basis
+ * (Section IV) but not where its bounds come from; the features, the network
+ * and its training are this library's own.  All arrays below are device
+ * memory, FP64, row-major; workspaces are 256-byte aligned device memory
+ * the caller owns (SSCG_ERR_SPACE when too small or misaligned).
+ *
+ * Network (d inputs, h hidden units per layer, o outputs):
+ *   h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), y = W3 h2 + b3,
+ *   theta = [W1 (h x d), b1 (h), W2 (h x h), b2 (h), W3 (o x h), b3 (o)];
+ *   loss = mean over batch and outputs of (y - t)^2.
+ */
+
+/* Features, with d_i = a_ii and c_ij = |a_ij| / sqrt(d_i d_j) over the
+ * nonzero off-diagonal entries:
+ *   f0 = ln(n)/3, f1 = ln(nnz/n), f2 = mean ln d, f3 = std ln d,
+ *   f4 = min ln d - f2, f5 = max ln d - f2, f6 = mean_i sum_{j!=i}|a_ij|/d_i,
+ *   f7 = mean ln c, f8 = std ln c, f9 = min ln c  (f7-f9 are 0 without
+ *   off-diagonal entries).
+ * The pass reads the FP32 copies of the values and of 1/d and works in FP32
+ * with FP64 sums, so each feature carries an error of about 1e-6 relative
+ * (absolute near zero). */
+#define SSCG_NFEAT 10
+int sscg_features_workspace_bytes(size_t* bytes);
+int sscg_mat_features(sscg_ctx* ctx, const sscg_mat* mat, double* feat /* SSCG_NFEAT */, void* workspace,
+                      size_t workspace_bytes);
+
+/* Parameter count h d + h + h h + h + o h + o, or -1 for a size below 1. */
+int64_t sscg_mlp_nparams(int d, int h, int o);
+/* Workspace for sscg_mlp_forward / _loss_grad / _train at this batch size. */
+int sscg_mlp_workspace_bytes(int d, int h, int o, int batch, size_t* bytes);
+/* Y (batch x o) = network(X (batch x d)).  Stream-ordered. */
+int sscg_mlp_forward(sscg_ctx* ctx, int d, int h, int o, const double* theta, int batch, const double* X, double* Y,
+                     void* workspace, size_t workspace_bytes);
+/* grad (nparams) = d loss / d theta for targets T (batch x o), by the chain
+ * rule layer by layer (tanh' = 1 - tanh^2).  When `loss` (a host pointer) is
+ * not NULL the call waits and stores the loss there; otherwise it is
+ * stream-ordered. */
+int sscg_mlp_loss_grad(sscg_ctx* ctx, int d, int h, int o, const double* theta, int batch, const double* X,
+                       const double* T, double* grad, double* loss, void* workspace, size_t workspace_bytes);
+/* One Adam step (Kingma and Ba, 2015) at step t >= 1 on theta, with first
+ * and second moments m, v (np each, zero before step 1):
+ *   m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ *   theta -= lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps).  Stream-ordered. */
+int sscg_mlp_adam_step(sscg_ctx* ctx, int64_t np, double* theta, const double* grad, double* m, double* v, double lr,
+                       double beta1, double beta2, double eps, int t);
+/* Full-batch training: `epochs` Adam steps (b1 0.9, b2 0.999, eps 1e-8) on
+ * the mean squared error, theta updated in place.  loss_hist: device array
+ * of `epochs` doubles receiving the loss before each step, or NULL.
+ * Returns after the last step. */
+int sscg_mlp_train(sscg_ctx* ctx, int d, int h, int o, double* theta, int batch, const double* X, const double* T,
+                   int epochs, double lr, double* loss_hist, void* workspace, size_t workspace_bytes);
+/* Spectral bounds from a trained network with d = SSCG_NFEAT, o = 2 and
+ * 1 <= h <= 256.  model: device array [x_mean (d), x_std (d), y_mean (2),
+ * y_std (2), theta]; the network sees (f - x_mean)/x_std and its outputs
+ * y give lambda = exp(y y_std + y_mean).  One features pass (about the
+ * traffic of one SpMV) and one inference launch; returns after the bounds
+ * are on the host.  SSCG_ERR_NONFINITE if the network's interval is empty
+ * or not finite (bounds untouched).  Workspace: sscg_features_workspace_bytes. */
+int sscg_bounds_mlp(sscg_ctx* ctx, const sscg_mat* mat, int h, const double* model, void* workspace,
+                    size_t workspace_bytes, double* lmin, double* lmax);
+
+/* Attach a trained bounds network (the model blob of sscg_bounds_mlp, width
+ * h) to a matrix, or detach it with model = NULL.  The blob is borrowed: it
+ * must stay valid while attached.  A Chebyshev-basis solve given no interval
+ * then takes its interval from the network instead of Lanczos steps, when
+ * the matrix's preconditioner is Jacobi (the network predicts the interval
+ * of D^-1 A); a network interval that is empty or not finite makes the solve
+ * return SSCG_ERR_NONFINITE.  SSCG_ERR_INVALID for h outside 1..256. */
+int sscg_set_bounds_model(sscg_mat* mat, int h, const double* model);
 
 #ifdef __cplusplus
 }

@@ -641,7 +641,9 @@ int orc_lanczos_bounds(const orc_csr* A, const orc_prec* B, const double* r0, in
     double* bb = (double*)calloc((size_t)k, sizeof(double));
     double* y = vec(n);
     orc_result res = {0};
-    orc_pcg(A, B, r0, y, 0.0, k, &res, a, bb);
+    /* stop at an invariant Krylov space (to working precision): beyond it the
+     * coefficients only carry rounding noise */
+    orc_pcg(A, B, r0, y, 1e-14, k, &res, a, bb);
     int kk = res.iters;
     if (kk < 1) { free(a); free(bb); free(y); return ORC_BREAKDOWN; }
     double* d = (double*)calloc((size_t)kk, sizeof(double));

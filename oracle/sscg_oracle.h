@@ -92,6 +92,9 @@ int orc_pfcg(const orc_csr* A, const orc_prec* B, const double* b, double* x,
 int orc_chol_solve(int n, const double* A, int nrhs, const double* B, double* X);
 
 int orc_tridiag_eig_extremes(int k, const double* d, const double* e, double* lo, double* hi);
+/* Extreme Ritz values of B^-1 A from at most k CG-Lanczos steps from r0;
+ * CG stops early once ||r|| <= 1e-14 ||r0|| (the Krylov space is then
+ * invariant to working precision). */
 int orc_lanczos_bounds(const orc_csr* A, const orc_prec* B, const double* r0, int k,
                        double* lo, double* hi);
 

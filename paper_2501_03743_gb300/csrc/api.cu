@@ -323,6 +323,10 @@ static bool auto_bounds(const sscg_opts* o) {
     return o->basis == SSCG_BASIS_CHEBYSHEV && o->basis_lmin == 0.0 && o->basis_lmax == 0.0;
 }
 
+// The network predicts the interval of D^-1 A, which is the operator of the
+// basis only under the Jacobi preconditioner.
+static bool model_bounds(const sscg_mat* m) { return m->bounds_model && m->prec == SSCG_PREC_JACOBI; }
+
 int sscg_solve_workspace_bytes(const sscg_mat* m, const sscg_opts* o, size_t* bytes) {
     if (!m || !o || !bytes || o->s < 1 || o->s > kMaxS || o->maxit < 0) return SSCG_ERR_INVALID;
     if (o->arith != SSCG_ARITH_MIXED && !use_gram(m, o)) return sstep_workspace(m, o, bytes);
@@ -330,7 +334,8 @@ int sscg_solve_workspace_bytes(const sscg_mat* m, const sscg_opts* o, size_t* by
     else gram_workspace(m, o, bytes);
     if (auto_bounds(o)) {
         size_t bb = 0;
-        bounds_workspace(m, kAutoBoundSteps, &bb);
+        if (model_bounds(m)) bb = features_workspace();
+        else bounds_workspace(m, kAutoBoundSteps, &bb);
         *bytes = std::max(*bytes, bb);
     }
     return SSCG_OK;
@@ -355,7 +360,8 @@ int sscg_solve(sscg_ctx* ctx, const sscg_mat* m, const double* b, double* x, con
         sscg_solve_workspace_bytes(m, o, &need);
         if (!ws || ws_bytes < need || ((uintptr_t)ws & 255))
             return set_err(ctx, SSCG_ERR_SPACE, "workspace needs %zu bytes, 256-byte aligned", need);
-        int rc = estimate_bounds(ctx, m, kAutoBoundSteps, nullptr, ws, ws_bytes, &lo, &hi);
+        int rc = model_bounds(m) ? bounds_mlp(ctx, m, m->bounds_h, m->bounds_model, ws, ws_bytes, &lo, &hi)
+                                 : estimate_bounds(ctx, m, kAutoBoundSteps, nullptr, ws, ws_bytes, &lo, &hi);
         if (rc != SSCG_OK) return rc;
         lo *= kAutoBoundLow;
         hi *= kAutoBoundHigh;

@@ -41,6 +41,10 @@ struct sscg_mat {
     // preconditioner
     int prec, degree;
     double plmin, plmax;
+    // spectral-bound network for automatic Chebyshev-basis intervals
+    // (device blob owned by the caller), or null
+    const double* bounds_model;
+    int bounds_h;
 };
 
 namespace sscg {
@@ -202,5 +206,16 @@ int solve_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, 
 // gives no basis interval, and the widening applied to its Ritz values.
 constexpr int kAutoBoundSteps = 20;
 constexpr double kAutoBoundLow = 0.95, kAutoBoundHigh = 1.05;
+
+// The Lanczos estimate stops once ||r|| <= kLanczosTol ||r0||: the Krylov
+// space is then invariant to working precision.  Past that point the
+// double-float CG would square residuals below FP32's exponent range
+// (rho underflows to 0) and put NaN coefficients into the tridiagonal.
+constexpr double kLanczosTol = 1e-14;
+
+// Spectral-bound network (mlp.cu): features pass plus inference.
+size_t features_workspace();
+int bounds_mlp(sscg_ctx* ctx, const sscg_mat* m, int h, const double* model, void* ws, size_t ws_bytes, double* lmin,
+               double* lmax);
 
 }  // namespace sscg

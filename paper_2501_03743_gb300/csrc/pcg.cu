@@ -602,7 +602,7 @@ int estimate_bounds(sscg_ctx* ctx, const sscg_mat* mat, int steps, const double*
         k_splitmix_uniform<<<grid_for(ctx, n, 4), kThreads, 0, st>>>(n, 0x5EED5EEDull, bvec);
         SSCG_CUDA(ctx, cudaGetLastError());
     }
-    Ctrl h = fresh_ctrl(steps, 0.0);
+    Ctrl h = fresh_ctrl(steps, kLanczosTol);
     SSCG_CUDA(ctx, cudaMemcpyAsync(L.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
     Prof prof(ctx, false);
     int rc = dispatch_pcg(ctx, mat, bvec, nullptr, steps, SSCG_ARITH_DF64, L, &h, prof, L.coef);

@@ -30,8 +30,11 @@ EXPORTS = (
     "sscg_mat_storage_bytes", "sscg_mat_create_csr", "sscg_mat_destroy", "sscg_mat_props_get",
     "sscg_set_preconditioner", "sscg_solve_workspace_bytes", "sscg_solve", "sscg_pcg_workspace_bytes",
     "sscg_pcg_solve", "sscg_spmv", "sscg_bounds_workspace_bytes", "sscg_estimate_bounds", "sscg_uniform",
-    "sscg_solve_static",
+    "sscg_solve_static", "sscg_features_workspace_bytes", "sscg_mat_features", "sscg_mlp_nparams",
+    "sscg_mlp_workspace_bytes", "sscg_mlp_forward", "sscg_mlp_loss_grad", "sscg_mlp_adam_step", "sscg_mlp_train",
+    "sscg_bounds_mlp", "sscg_set_bounds_model",
 )
+NFEAT = 10
 STATIC_SCRATCH_BYTES = 16 << 20
 
 
@@ -99,6 +102,16 @@ def load(path: str | None = None):
     L.sscg_estimate_bounds.argtypes = [vp, vp, i32, vp, vp, sz, P(dbl), P(dbl)]
     L.sscg_uniform.argtypes = [vp, i64, C.c_uint64, vp]
     L.sscg_solve_static.argtypes = [vp, vp, vp, vp, P(Opts), P(Info)]
+    L.sscg_features_workspace_bytes.argtypes = [P(sz)]
+    L.sscg_mat_features.argtypes = [vp, vp, vp, vp, sz]
+    L.sscg_mlp_nparams.argtypes = [i32, i32, i32]; L.sscg_mlp_nparams.restype = i64
+    L.sscg_mlp_workspace_bytes.argtypes = [i32, i32, i32, i32, P(sz)]
+    L.sscg_mlp_forward.argtypes = [vp, i32, i32, i32, vp, i32, vp, vp, vp, sz]
+    L.sscg_mlp_loss_grad.argtypes = [vp, i32, i32, i32, vp, i32, vp, vp, vp, P(dbl), vp, sz]
+    L.sscg_mlp_adam_step.argtypes = [vp, i64, vp, vp, vp, vp, dbl, dbl, dbl, dbl, i32]
+    L.sscg_mlp_train.argtypes = [vp, i32, i32, i32, vp, i32, vp, vp, i32, dbl, vp, vp, sz]
+    L.sscg_bounds_mlp.argtypes = [vp, vp, i32, vp, vp, sz, P(dbl), P(dbl)]
+    L.sscg_set_bounds_model.argtypes = [vp, i32, vp]
     _lib = L
     return L
 
@@ -211,6 +224,39 @@ class Matrix:
         self.ctx.check(self.ctx.lib.sscg_estimate_bounds(self.ctx.h, self.h, steps, rp, C.c_void_p(ws.data_ptr()),
                                                          nbytes.value, C.byref(lo), C.byref(hi)))
         return lo.value, hi.value
+
+    def features(self):
+        """The SSCG_NFEAT matrix features of the spectral-bound network (host array)."""
+        torch = _torch()
+        nbytes = C.c_size_t()
+        self.ctx.check(self.ctx.lib.sscg_features_workspace_bytes(C.byref(nbytes)))
+        ws = torch.empty(nbytes.value, dtype=torch.uint8, device=self.storage.device)
+        f = torch.empty(NFEAT, dtype=torch.float64, device=self.storage.device)
+        self.ctx.check(self.ctx.lib.sscg_mat_features(self.ctx.h, self.h, C.c_void_p(f.data_ptr()),
+                                                      C.c_void_p(ws.data_ptr()), nbytes.value))
+        return f.cpu().numpy()
+
+    def bounds_mlp(self, hidden, model):
+        """Spectral bounds of D^-1 A from a trained network; `model` is the
+        device blob [x_mean, x_std, y_mean, y_std, theta] (FP64)."""
+        torch = _torch()
+        nbytes = C.c_size_t()
+        self.ctx.check(self.ctx.lib.sscg_features_workspace_bytes(C.byref(nbytes)))
+        ws = torch.empty(nbytes.value, dtype=torch.uint8, device=self.storage.device)
+        lo, hi = C.c_double(), C.c_double()
+        self.ctx.check(self.ctx.lib.sscg_bounds_mlp(self.ctx.h, self.h, int(hidden), C.c_void_p(model.data_ptr()),
+                                                    C.c_void_p(ws.data_ptr()), nbytes.value, C.byref(lo),
+                                                    C.byref(hi)))
+        return lo.value, hi.value
+
+    def set_bounds_model(self, hidden, model):
+        """Attach a bounds network blob (kept alive here) for automatic
+        Chebyshev-basis intervals; model=None detaches it."""
+        rc = self.ctx.lib.sscg_set_bounds_model(self.h, int(hidden) if model is not None else 0,
+                                                C.c_void_p(model.data_ptr()) if model is not None else None)
+        if rc != OK:
+            raise SscgError(rc, "sscg_set_bounds_model: bad width")
+        self._bounds_model = model
 
     def spmv(self, x):
         torch = _torch()

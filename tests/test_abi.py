@@ -22,7 +22,7 @@ def declared_functions():
     for h in os.listdir(os.path.join(ROOT, "include")):
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names |= set(re.findall(r"^\s*(?:int|const char\*|void)\s+\**\s*(sscg_\w+)\s*\(", src, flags=re.M))
+        names |= set(re.findall(r"^\s*(?:int64_t|int|const char\*|void)\s+\**\s*(sscg_\w+)\s*\(", src, flags=re.M))
     return sorted(names)
 
 

@@ -321,6 +321,17 @@ def test_lanczos_full_run_gives_exact_extremes():
     assert abs(lo - ev[0]) < 1e-8 and abs(hi - ev[-1]) < 1e-8
 
 
+def test_lanczos_more_steps_than_needed_stays_in_spectrum():
+    """Asking for far more steps than CG needs (27-point stencil, kappa ~ 23,
+    400 steps on 1,728 unknowns) still gives Ritz values at the exact ends of
+    the spectrum of D^-1 A: no spurious values from steps past convergence."""
+    N = 12
+    A = inputs.system("poisson27", N, seed=0)
+    lo, hi = oracle.lanczos_bounds(oracle.as_matrix(A), inputs.uniform(3, N ** 3), 400)
+    clo, chi = inputs.closed_form_bounds("poisson27", N)
+    assert abs(lo - clo / 26) < 1e-7 * chi and abs(hi - chi / 26) < 1e-7 * chi
+
+
 def _cheb_T(m, x):
     x = np.asarray(x, dtype=float)
     inside = np.cos(m * np.arccos(np.clip(x, -1, 1)))
