@@ -69,6 +69,17 @@ def parse():
 
 # ------------------------------------------------------------ byte model
 
+# DRAM bytes (read + write) per row and launch that ncu --set full measured
+# for this workload's kernels (7-point stencil, df64, s = 4, sequential
+# matrix-powers levels) at n = 4,096,000 (profiles/
+# k_level_k_update_tma_poisson7_160_df64_s4.txt): the level averaged over the
+# four levels of an outer step, and the block update.  The roofline's
+# "traffic" scales them to the workload's n; it is null for any other
+# configuration, whose kernels were not captured.
+NCU_TRAFFIC_PER_ROW = {"mpk": 345.232e6 / 4.096e6, "update": 931.526e6 / 4.096e6}
+NCU_TRAFFIC_CONFIG = dict(s=4, arith="df64", fused_mpk=False)
+
+
 def byte_model(n, nnz, vbytes, s, arith):
     V = 8 * n
     M = 4 * (n + 1) + nnz * (4 + vbytes)
@@ -77,6 +88,14 @@ def byte_model(n, nnz, vbytes, s, arith):
     return dict(M=M, V=V, level=lv, level_avg=sum(lv) / s, update=(6 * s + 6) * V, update_first=(4 * s + 6) * V,
                 init=M + 5 * V + (V if df else 0), final=M + 2 * V + (3 * V if df else 0),
                 pcg_spmv=M + 2 * V, pcg_update=7 * V, pcg_dir=4 * V)
+
+
+def traffic(a, family, n):
+    """Measured DRAM bytes per launch of `family`, scaled to n rows, or None."""
+    cfg = dict(s=a.s, arith=a.arith, fused_mpk=bool(a.fused_mpk))
+    if cfg != NCU_TRAFFIC_CONFIG or family not in NCU_TRAFFIC_PER_ROW:
+        return None
+    return round(NCU_TRAFFIC_PER_ROW[family] * n)
 
 
 def sstep_bytes(bm, outer):
@@ -279,7 +298,7 @@ def main():
     kernel_names = {"mpk": "k_level (matrix-powers level: CSR SpMV + Jacobi + moments)",
                     "update": "k_update (block update P, AP, x, r + next z)"}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "kernel": kernel_names[dom],
+                "frac": round(achieved / peak, 4), "traffic": traffic(a, dom, n), "kernel": kernel_names[dom],
                 "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "family_ms_per_solve": {k: round(v["ms"] / a.steps, 3) for k, v in fam.items()},
                 "family_gbs": {k: round(v["bytes_per_launch"] / (v["ms"] / max(v["launches"], 1) * 1e-3) / 1e9, 1)
