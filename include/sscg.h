@@ -315,6 +315,59 @@ int sscg_bounds_mlp(sscg_ctx* ctx, const sscg_mat* mat, int h, const double* mod
  * return SSCG_ERR_NONFINITE.  SSCG_ERR_INVALID for h outside 1..256. */
 int sscg_set_bounds_model(sscg_mat* mat, int h, const double* model);
 
+
+/* ------------------------------------------------------ batched solves
+ *
+ * Many independent SPD systems, each with 1..SSCG_BATCH_MAX_RHS right-hand
+ * sides, solved together by one persistent cooperative kernel (captured in
+ * a CUDA graph when the driver allows).  Every (system, right-hand side)
+ * runs Algorithm 3 with the monomial basis and the moment recurrence of
+ * Algorithm 6 under the Jacobi preconditioner, exactly as sscg_solve does
+ * for one system; the kernel interleaves the systems' matrix-powers levels,
+ * s x s solves and block updates, separated by grid-wide barriers, and
+ * gathers A's columns once for all right-hand sides of a system.  The paper
+ * has no batched form; this is the library's serving path.
+ *
+ * The plan binds the matrices (not copied: they must outlive the plan), the
+ * options (s <= SSCG_BATCH_MAX_S, monomial basis, f64 or df64 arithmetic,
+ * tol, maxit) and the caller's workspace.  Rows are processed in items of T
+ * rows per system; T depends on the system's size class (n < 2^16, < 2^19,
+ * < 2^21, larger).  With `tune` set, sscg_batch_create times two outer steps
+ * of each class's systems (synthetic right-hand sides) for T in {256, 512,
+ * 1024, 2048, 4096} and keeps the fastest; otherwise fixed defaults apply.
+ */
+#define SSCG_BATCH_MAX_RHS 8
+#define SSCG_BATCH_MAX_S 8
+#define SSCG_BATCH_MAX_SYSTEMS 4096
+typedef struct sscg_batch sscg_batch;
+
+/* Workspace bytes for a plan (SSCG_ERR_INVALID on bad arguments). */
+int sscg_batch_workspace_bytes(int nsys, const sscg_mat* const* mats, const int* nrhs, const sscg_opts* opts,
+                               size_t* bytes);
+/* Create a plan.  mats[k]: the systems (Jacobi preconditioner set);
+ * nrhs[k] in 1..SSCG_BATCH_MAX_RHS.  Errors: SSCG_ERR_INVALID (sizes,
+ * options, preconditioner), SSCG_ERR_SPACE (workspace), SSCG_ERR_CUDA,
+ * SSCG_TIMEOUT (an autotuning run stopped). */
+int sscg_batch_create(sscg_ctx* ctx, int nsys, const sscg_mat* const* mats, const int* nrhs, const sscg_opts* opts,
+                      int tune, void* workspace, size_t workspace_bytes, sscg_batch** plan);
+int sscg_batch_destroy(sscg_batch* plan);
+/* Solve all systems.  B[k], X[k]: device FP64 arrays of n_k x nrhs[k],
+ * column-major (right-hand side r at offset r n_k); X holds x0 on entry and
+ * the solution on exit.  infos[k] (may be NULL): per system, the worst
+ * status and the largest iteration count and residuals over its right-hand
+ * sides; rhs_infos (may be NULL): one entry per right-hand side, systems in
+ * order; latency_ms[k] (may be NULL): device time from the kernel's start
+ * until system k's result (x and true residual) was final.  hist is not
+ * written.  Returns after the results are on the host: SSCG_OK, or the worst
+ * positive status over all right-hand sides; SSCG_TIMEOUT if a barrier wait
+ * expired (x then undefined). */
+int sscg_batch_solve(sscg_batch* plan, const double* const* B, double* const* X, sscg_info* infos,
+                     sscg_info* rhs_infos, double* latency_ms);
+/* Plan facts: rows per item of every system (nsys entries), the persistent
+ * grid size, whether solves replay a CUDA graph, and the last solve's time
+ * in ms (CUDA events around the graph).  Any pointer may be NULL. */
+int sscg_batch_props(const sscg_batch* plan, int* tile_rows, int* grid, int* graph, float* last_ms);
+
 #ifdef __cplusplus
 }
 #endif

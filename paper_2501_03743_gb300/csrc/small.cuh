@@ -53,15 +53,17 @@ __device__ __forceinline__ bool warp_chol_solve(const double* L, int s, double* 
     return __all_sync(0xffffffffu, ok);
 }
 
-// Scratch for the solves: 5 s x s matrices and 3 vectors (kMaxS bounds).
-struct SmallScratch {
-    double L[kMaxS * kMaxS];
-    double X[kMaxS * kMaxS];
-    double Wn[kMaxS * kMaxS];
-    double b1[kMaxS * kMaxS];
-    double a[kMaxS];
-    double c[kMaxS];
+// Scratch for the solves: 4 s x s matrices and 2 vectors, for s <= MS.
+template <int MS>
+struct SmallScratchT {
+    double L[MS * MS];
+    double X[MS * MS];
+    double Wn[MS * MS];
+    double b1[MS * MS];
+    double a[MS];
+    double c[MS];
 };
+using SmallScratch = SmallScratchT<kMaxS>;
 
 // Algorithm 6 (SW) for the monomial basis, or its first-step form, by one
 // warp.  Inputs in ctrl: mu[0..2s-1] (vm(k) = mu_{k-1}), and for step > 0
@@ -73,7 +75,8 @@ struct SmallScratch {
 //            W_prev beta = b1;  W = H - b1 beta;  W alpha = m
 // (0-based indices; b1 filled over all (a, b), the consistent reading of
 // Algorithm 6, whose b1 equals -c_i of Section II-A.)
-__device__ inline int warp_sw_monomial(Ctrl* ctrl, int s, int step, SmallScratch* sc) {
+template <class SC>
+__device__ inline int warp_sw_monomial(Ctrl* ctrl, int s, int step, SC* sc) {
     const int lane = threadIdx.x & 31;
     const double* mu = ctrl->mu;
     if (step == 0) {

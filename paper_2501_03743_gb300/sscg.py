@@ -32,8 +32,11 @@ EXPORTS = (
     "sscg_pcg_solve", "sscg_spmv", "sscg_bounds_workspace_bytes", "sscg_estimate_bounds", "sscg_uniform",
     "sscg_solve_static", "sscg_features_workspace_bytes", "sscg_mat_features", "sscg_mlp_nparams",
     "sscg_mlp_workspace_bytes", "sscg_mlp_forward", "sscg_mlp_loss_grad", "sscg_mlp_adam_step", "sscg_mlp_train",
-    "sscg_bounds_mlp", "sscg_set_bounds_model",
+    "sscg_bounds_mlp", "sscg_set_bounds_model", "sscg_batch_workspace_bytes", "sscg_batch_create",
+    "sscg_batch_destroy", "sscg_batch_solve", "sscg_batch_props",
 )
+BATCH_MAX_RHS = 8
+BATCH_MAX_S = 8
 NFEAT = 10
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -112,6 +115,11 @@ def load(path: str | None = None):
     L.sscg_mlp_train.argtypes = [vp, i32, i32, i32, vp, i32, vp, vp, i32, dbl, vp, vp, sz]
     L.sscg_bounds_mlp.argtypes = [vp, vp, i32, vp, vp, sz, P(dbl), P(dbl)]
     L.sscg_set_bounds_model.argtypes = [vp, i32, vp]
+    L.sscg_batch_workspace_bytes.argtypes = [i32, vp, vp, P(Opts), P(sz)]
+    L.sscg_batch_create.argtypes = [vp, i32, vp, vp, P(Opts), i32, vp, sz, P(vp)]
+    L.sscg_batch_destroy.argtypes = [vp]
+    L.sscg_batch_solve.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.sscg_batch_props.argtypes = [vp, vp, P(i32), P(i32), P(C.c_float)]
     _lib = L
     return L
 
@@ -329,3 +337,77 @@ def solve(A: Matrix, b, x=None, method="sstep", **kw):
         x = torch.zeros_like(b)
     r = Solver(A, method=method, **kw).solve(b, x)
     return x, r
+
+
+@dataclass
+class BatchResult:
+    status: int
+    systems: list          # SolveResult per system (worst over its right-hand sides)
+    rhs: list              # SolveResult per right-hand side, systems in order
+    latency_ms: np.ndarray  # device time until each system's result was final
+    solve_ms: float         # CUDA-event time of the whole batched solve
+
+
+class BatchSolver:
+    """Plan for solving many systems (each with 1..8 right-hand sides) in one
+    persistent launch; see sscg_batch_create."""
+
+    def __init__(self, mats, nrhs, s=4, tol=1e-8, maxit=1000, arith="df64", tune=False):
+        torch = _torch()
+        self.mats = list(mats)
+        self.nrhs = [int(r) for r in nrhs]
+        assert len(self.mats) == len(self.nrhs)
+        self.ctx = self.mats[0].ctx
+        lib = self.ctx.lib
+        k = len(self.mats)
+        self._mh = (C.c_void_p * k)(*[m.h.value for m in self.mats])
+        self._nr = (C.c_int * k)(*self.nrhs)
+        self.opts = make_opts(s=s, tol=tol, maxit=maxit, arith=arith)
+        nbytes = C.c_size_t()
+        rc = lib.sscg_batch_workspace_bytes(k, self._mh, self._nr, C.byref(self.opts), C.byref(nbytes))
+        if rc != OK:
+            raise SscgError(rc, "sscg_batch_workspace_bytes: invalid batch")
+        self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device="cuda")
+        h = C.c_void_p()
+        self.ctx.check(lib.sscg_batch_create(self.ctx.h, k, self._mh, self._nr, C.byref(self.opts), int(bool(tune)),
+                                             C.c_void_p(self.workspace.data_ptr()), self.workspace.numel(),
+                                             C.byref(h)))
+        self.h = h
+
+    def props(self):
+        k = len(self.mats)
+        tiles = (C.c_int * k)()
+        grid, graph, ms = C.c_int(), C.c_int(), C.c_float()
+        self.ctx.check(self.ctx.lib.sscg_batch_props(self.h, tiles, C.byref(grid), C.byref(graph), C.byref(ms)))
+        return dict(tile_rows=list(tiles), grid=grid.value, graph=bool(graph.value), last_ms=ms.value)
+
+    def solve(self, B, X) -> BatchResult:
+        """B[k], X[k]: FP64 device tensors of shape (nrhs[k], n_k) (each
+        right-hand side contiguous); X holds x0 and receives the solution."""
+        k = len(self.mats)
+        for i in range(k):
+            assert B[i].is_contiguous() and X[i].is_contiguous()
+            assert tuple(B[i].shape) == (self.nrhs[i], self.mats[i].n) == tuple(X[i].shape)
+        bp = (C.c_void_p * k)(*[t.data_ptr() for t in B])
+        xp = (C.c_void_p * k)(*[t.data_ptr() for t in X])
+        infos = (Info * k)()
+        rinf = (Info * sum(self.nrhs))()
+        lat = np.zeros(k)
+        rc = self.ctx.lib.sscg_batch_solve(self.h, bp, xp, infos, rinf, lat.ctypes.data_as(C.c_void_p))
+        self.ctx.check(rc, allow_positive=True)
+
+        def res(i):
+            return SolveResult(i.status, i.outer_iters, i.equiv_iters, i.rel_res_recursive, i.rel_res_true)
+
+        return BatchResult(rc, [res(i) for i in infos], [res(i) for i in rinf], lat, self.props()["last_ms"])
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.sscg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
