@@ -12,6 +12,10 @@ benchmark systems this library is measured on):
   nodes, lexicographic order ``row = i + N*(j + N*k)``, diagonal 6 and
   neighbours -1, boundary values eliminated (no h^2 factor).
 * ``poisson27(N)`` - 27-point stencil, diagonal 26 and all 26 neighbours -1.
+* ``batch_spec(count, seed)`` - a serving mix of independent systems:
+  7- and 27-point stencils and variable-coefficient fields (sigma in
+  {0.5, 1, 2, 3}) on grids drawn log-uniformly from 32^3 .. 160^3, each with
+  1..8 right-hand sides.
 * ``varcoef7(N, sigma, seed)`` - 7-point finite-volume discretisation of
   -div(k grad u) with k = exp(sigma * g), g a seeded Gaussian field smoothed
   with a Gaussian kernel of ``ell`` cells and normalised to mean 0 and
@@ -85,14 +89,17 @@ def _stencil(N: int, offsets, weights):
     return _assemble(n, cols, vals)
 
 
+_OFFS7 = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+_OFFS27 = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+
+
 def poisson7(N: int):
-    offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
     w = [6.0] + [-1.0] * 6
-    return _stencil(N, offs, w)
+    return _stencil(N, _OFFS7, w)
 
 
 def poisson27(N: int):
-    offs = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    offs = _OFFS27
     w = [26.0 if o == (0, 0, 0) else -1.0 for o in offs]
     return _stencil(N, offs, w)
 
@@ -173,3 +180,53 @@ def closed_form_bounds(kind: str, N: int):
     if kind == "poisson27":
         return 27.0 - (1.0 + 2.0 * c) ** 3, 27.0 + (1.0 + 2.0 * c) ** 2 * (2.0 * c - 1.0)
     raise ValueError(kind)
+
+
+def batch_spec(count: int, seed: int = 2025, nmin: int = 32, nmax: int = 160):
+    """Seeded serving mix: ``count`` dicts (kind, N, sigma, field_seed, nrhs).
+
+    Draws 4k..4k+3 of splitmix64(seed) pick, for system k: the kind
+    (poisson7, poisson27, varcoef7 twice as likely as each), the grid edge N
+    = round(nmin (nmax/nmin)^u) (log-uniform), sigma in {0.5, 1, 2, 3} and
+    1..8 right-hand sides."""
+    u = (uniform(seed, 4 * count) + 1.0) / 2.0  # [0, 1)
+    kinds = ("poisson7", "poisson27", "varcoef7", "varcoef7")
+    out = []
+    for k in range(count):
+        a, b, c, d = u[4 * k:4 * k + 4]
+        out.append(dict(kind=kinds[int(a * 4)], N=int(round(nmin * (nmax / nmin) ** b)),
+                        sigma=(0.5, 1.0, 2.0, 3.0)[int(c * 4)], field_seed=1000 + k, nrhs=1 + int(d * 8)))
+    return out
+
+
+def batch_csr(spec: dict):
+    """CSR arrays (rowptr, col, val) of one ``batch_spec`` entry."""
+    if spec["kind"] == "varcoef7":
+        return varcoef7(spec["N"], spec["sigma"], spec["field_seed"])
+    if spec["kind"] == "poisson27":
+        return poisson27(spec["N"])
+    return poisson7(spec["N"])
+
+
+def stencil_torch(kind: str, N: int, device="cuda"):
+    """``poisson7`` / ``poisson27`` built with torch on `device`: the same
+    CSR arrays (row order, column order, values) as the numpy builders,
+    as int32 / int32 / float64 tensors.  For large serving mixes."""
+    import torch
+
+    offs = _OFFS7 if kind == "poisson7" else _OFFS27
+    diag = 6.0 if kind == "poisson7" else 26.0
+    n = N ** 3
+    order = sorted(offs, key=lambda o: o[0] * N * N + o[1] * N + o[2])
+    i = torch.arange(n, dtype=torch.int64, device=device)
+    x, y, z = i % N, (i // N) % N, i // (N * N)
+    cols = torch.empty((n, len(order)), dtype=torch.int32, device=device)
+    vals = torch.empty((n, len(order)), dtype=torch.float64, device=device)
+    for c, (dz, dy, dx) in enumerate(order):
+        ok = (x + dx >= 0) & (x + dx < N) & (y + dy >= 0) & (y + dy < N) & (z + dz >= 0) & (z + dz < N)
+        cols[:, c] = torch.where(ok, i + dx + N * (dy + N * dz), torch.full_like(i, -1)).to(torch.int32)
+        vals[:, c] = diag if (dz, dy, dx) == (0, 0, 0) else -1.0
+    mask = cols >= 0
+    rowptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    torch.cumsum(mask.sum(dim=1), 0, out=rowptr[1:])
+    return rowptr.to(torch.int32), cols[mask], vals[mask]
