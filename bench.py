@@ -19,10 +19,12 @@ Reported:
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same solve
 
 Byte model (bytes per launch; V = 8 n, M = 4 (n+1) + nnz (4 + value bytes)):
-  MPK level j     M + 2V (u_j gathered, A u_j written) + 2V when j < s-1
-                  (1/diag read, u_{j+1} written)
-  block update    (6s + 6) V: U, AU, P_old, AP_old, x, r, 1/diag read;
-                  P, AP, x, r, next z written (first step: (4s + 6) V)
+  MPK level j     M + 3V: u_j gathered, 1/diag read, u_{j+1} = D^-1 A u_j
+                  written (A u_j is not stored)
+  block update    (5s + 5) V: U_1..U_{s+1}, P_old, Q_old, x, diag read;
+                  P, Q, x and the next z written (first step: (2s + 5) V)
+  (with --fused-mpk the levels and update of the A U / A P form are timed:
+  levels M + 2V, + 2V when j < s-1; update (6s + 6) V, first (4s + 6) V)
   init            M + 5V: x0 gathered, b, 1/diag read, r, z written
                   (DF64: + V, the zeroed correction)
   final           M + 2V: x gathered, b read (DF64: + 3V, x = x0 + correction)
@@ -76,21 +78,24 @@ def parse():
 
 # DRAM bytes (read + write) per row and launch that ncu --set full measured
 # for this workload's kernels (7-point stencil, df64, s = 4, sequential
-# matrix-powers levels) at n = 4,096,000 (profiles/
-# k_level_k_update_tma_poisson7_160_df64_s4.txt): the level averaged over the
-# four levels of an outer step, and the block update.  The roofline's
-# "traffic" scales them to the workload's n; it is null for any other
-# configuration, whose kernels were not captured.
-NCU_TRAFFIC_PER_ROW = {"mpk": 345.232e6 / 4.096e6, "update": 931.526e6 / 4.096e6}
+# matrix-powers levels), keyed by kernel family; the roofline's "traffic"
+# scales them to the workload's n.  Empty until the current kernels are
+# captured: traffic is then null.
+NCU_TRAFFIC_PER_ROW = {}
 NCU_TRAFFIC_CONFIG = dict(s=4, arith="df64", fused_mpk=False)
 
 
-def byte_model(n, nnz, vbytes, s, arith):
+def byte_model(n, nnz, vbytes, s, arith, fused=False):
     V = 8 * n
     M = 4 * (n + 1) + nnz * (4 + vbytes)
     df = arith != "f64"
-    lv = [M + 2 * V + (2 * V if j < s - 1 else 0) for j in range(s)]
-    return dict(M=M, V=V, level=lv, level_avg=sum(lv) / s, update=(6 * s + 6) * V, update_first=(4 * s + 6) * V,
+    if fused:
+        lv = [M + 2 * V + (2 * V if j < s - 1 else 0) for j in range(s)]
+        upd, upd_first = (6 * s + 6) * V, (4 * s + 6) * V
+    else:
+        lv = [M + 3 * V for j in range(s)]
+        upd, upd_first = (5 * s + 5) * V, (2 * s + 5) * V
+    return dict(M=M, V=V, level=lv, level_avg=sum(lv) / s, update=upd, update_first=upd_first,
                 init=M + 5 * V + (V if df else 0), final=M + 2 * V + (3 * V if df else 0),
                 pcg_spmv=M + 2 * V, pcg_update=7 * V, pcg_dir=4 * V)
 
@@ -245,7 +250,7 @@ def main():
     A = sscg.Matrix(ctx, sysm["rowptr"], sysm["col"], sysm["val"])
     props = A.props()
     vbytes = 8 if a.arith == "f64" else (4 if props["values_exact_fp32"] else 8)
-    bm = byte_model(n, nnz, vbytes, a.s, a.arith)
+    bm = byte_model(n, nnz, vbytes, a.s, a.arith, fused=a.fused_mpk)
     b = torch.from_numpy(sysm["b"]).cuda()
     x = torch.zeros_like(b)
     solver = sscg.Solver(A, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, profile=True,
@@ -303,7 +308,8 @@ def main():
         peak, peak_src = 6800.0, "fallback"
     achieved = d["bytes_per_launch"] / avg_s / 1e9
     kernel_names = {"mpk": "k_level (matrix-powers level: CSR SpMV + Jacobi + moments)",
-                    "update": "k_update (block update P, AP, x, r + next z)"}
+                    "update": ("k_update_tma (block update P, AP, x, r + next z)" if a.fused_mpk else
+                               "k_update_q (block update P, Q = D^-1 A P, x, z)")}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic(a, dom, n), "kernel": kernel_names[dom],
                 "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",

@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(kThreads) k_analyze(int n, const int32_t* __re
                                                       const double* __restrict__ val, float* __restrict__ vhi,
                                                       float* __restrict__ vlo, double* __restrict__ diag,
                                                       double* __restrict__ dinv, float2* __restrict__ dinv_df,
-                                                      float* __restrict__ dinv_f, Analysis* out) {
+                                                      float2* __restrict__ diag_df, float* __restrict__ dinv_f,
+                                                      Analysis* out) {
     __shared__ unsigned long long s_bad, s_nf, s_ne, s_np, s_bw, s_mn, s_mx;
     if (threadIdx.x == 0) {
         s_bad = s_nf = s_ne = s_np = s_bw = 0ull;
@@ -57,6 +58,10 @@ __global__ void __launch_bounds__(kThreads) k_analyze(int n, const int32_t* __re
             if (c == i) d += v;
         }
         diag[i] = d;
+        {
+            float dh = __double2float_rn(d);
+            diag_df[i] = make_float2(dh, __double2float_rn(d - (double)dh));
+        }
         if (!(d > 0.0) || !isfinite(d)) {
             np++;
             dinv[i] = 0.0;
@@ -101,6 +106,7 @@ struct MatLayout {
     double* diag;
     double* dinv;
     float2* dinv_df;
+    float2* diag_df;
     float* dinv_f;
     Analysis* an;
     size_t bytes;
@@ -116,9 +122,10 @@ MatLayout mat_layout(int64_t n, int64_t nnz, void* base) {
     L.val = c.take<double>((size_t)nnz + 16);
     L.vhi = c.take<float>((size_t)nnz + 16);
     L.vlo = c.take<float>((size_t)nnz + 16);
-    L.diag = c.take<double>((size_t)n);
-    L.dinv = c.take<double>((size_t)n);
-    L.dinv_df = c.take<float2>((size_t)n);
+    L.diag = c.take<double>((size_t)n + 16);
+    L.dinv = c.take<double>((size_t)n + 16);
+    L.dinv_df = c.take<float2>((size_t)n + 16);
+    L.diag_df = c.take<float2>((size_t)n + 16);
     L.dinv_f = c.take<float>((size_t)n + 16);
     L.an = c.take<Analysis>(1);
     L.bytes = c.used;
@@ -235,7 +242,7 @@ int sscg_mat_create_csr(sscg_ctx* ctx, int64_t n, int64_t nnz, const int32_t* ro
     SSCG_CUDA(ctx, cudaMemcpyAsync(L.an, &a0, sizeof(a0), cudaMemcpyHostToDevice, st));
     int G = grid_for(ctx, n, 4);
     k_analyze<<<G, kThreads, 0, st>>>((int)n, L.rowptr, L.col, L.val, L.vhi, L.vlo, L.diag, L.dinv, L.dinv_df,
-                                      L.dinv_f, L.an);
+                                      L.diag_df, L.dinv_f, L.an);
     SSCG_CUDA(ctx, cudaGetLastError());
     Analysis a;
     SSCG_CUDA(ctx, cudaMemcpyAsync(&a, L.an, sizeof(a), cudaMemcpyDeviceToHost, st));
@@ -257,6 +264,7 @@ int sscg_mat_create_csr(sscg_ctx* ctx, int64_t n, int64_t nnz, const int32_t* ro
     m->dinv = L.dinv;
     m->dinv_df = L.dinv_df;
     m->dinv_f = L.dinv_f;
+    m->diag_df = L.diag_df;
     m->bandwidth = (int64_t)a.bandwidth;
     m->exact_fp32 = a.not_exact == 0;
     m->max_row_nnz = max_row;

@@ -31,6 +31,7 @@ struct sscg_mat {
     double* diag;
     double* dinv;    // 1 / diag
     float2* dinv_df; // 1 / diag as a double-float
+    float2* diag_df; // diag as a double-float
     float* dinv_f;   // 1 / diag rounded to FP32 (mixed-precision basis)
     // properties
     int64_t bandwidth;

@@ -28,7 +28,7 @@ namespace sscg {
 namespace {
 
 // One level of the matrix-powers kernel (Algorithm 4): y = A u_j, written to
-// AU_j; u_{j+1} = B^-1 y (when u_next != null); moment partials
+// AU_j when au_out != null; u_{j+1} = B^-1 y (when u_next != null); moment partials
 // mu_{2j+1} = u_j . y and mu_{2j+2} = y . B^-1 y.  With `last` set, the last
 // CTA reduces mu_1..mu_{2s-1} and runs Algorithm 6.
 template <class A, int VM>
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kThreads) k_level(MatView M, const typename A:
     const bool ok = spmv_pipe<A, VM, kStages>(
         M, smem, [&](int c) { return A::ldg(u_in + c); },
         [&](int row, R y) {
-            A::st(au_out + row, y);
+            if (au_out) A::st(au_out + row, y);
             m1 = A::fma(A::ldg(u_in + row), y, m1);
             if (u_next || want_m2) {
                 R z = dinv ? A::mul(A::ld(dinv + row), y) : y;
@@ -356,7 +356,7 @@ Layout plan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t c
     L.ctrl = c.take<Ctrl>(1);
     L.hist = c.take<double>((size_t)o->maxit + 2);
     L.part = c.take<double>((size_t)G * (2 * kMaxS + 4));
-    size_t blk = (size_t)L.ldn * 2 * o->s;
+    size_t blk = (size_t)L.ldn * (2 * o->s + 1);
     L.blk[0] = c.take<double>(blk);
     L.blk[1] = c.take<double>(blk);
     L.r = c.take<double>((size_t)L.ldn);
@@ -385,7 +385,7 @@ MatView view_of(const sscg_mat* m, int cap) {
 
 template <class A, int VM, int SB>
 int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o,
-              const Layout& L, const typename A::S* dinv, Ctrl* hctrl, Prof& P) {
+              const Layout& L, const typename A::S* dinv, const typename A::S* diag, Ctrl* hctrl, Prof& P) {
     using S = typename A::S;
     cudaStream_t st = ctx->stream;
     const int n = (int)mat->n, s = o->s, G = L.G;
@@ -418,6 +418,9 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     size_t smem_upd = 0;
     int Gu = 0;
     if (int e = update_tma_setup<A, SB>(ctx, n, s, &smem_upd, &Gu)) return e;
+    size_t smem_updq = 0;
+    int Gq = 0;
+    if (int e = update_q_setup<A, SB>(ctx, n, s, &smem_updq, &Gq)) return e;
     const int Gt = occupancy_grid(ctx, k_true_res, smem64, n);
     k_init<A, VM><<<Gi, kThreads, smem, st>>>(M, dinv, b, x, A::kind == 0 ? nullptr : xw, r, blk[0], L.part,
                                               L.ctrl, L.hist);
@@ -447,17 +450,22 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
                     P.end(FAM_MPK, k);
                 }
             } else {
+                // u_{j+1} = D^-1 A u_j into column j+1 (all j, u_{s+1} too); A u_j is not stored
                 for (int j = 0; j < s; j++) {
                     P.begin();
-                    k_level<A, VM><<<Gl, kThreads, smem_pipe, st>>>(M, dinv, bn + j * ld, bn + (s + j) * ld,
-                                                              j + 1 < s ? bn + (j + 1) * ld : nullptr, L.part, j, s,
-                                                              k, j == s - 1, L.ctrl);
+                    k_level<A, VM><<<Gl, kThreads, smem_pipe, st>>>(M, dinv, bn + j * ld, nullptr,
+                                                              bn + (j + 1) * ld, L.part, j, s, k, j == s - 1,
+                                                              L.ctrl);
                     P.end(FAM_MPK, k);
                 }
             }
             P.begin();
-            k_update_tma<A, SB><<<Gu, kUpdRows, smem_upd, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dinv, L.part,
-                                                                k == 0, 1, L.ctrl, L.hist);
+            if (fp.F > 0)
+                k_update_tma<A, SB><<<Gu, kUpdRows, smem_upd, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dinv, L.part,
+                                                                    k == 0, 1, L.ctrl, L.hist);
+            else
+                k_update_q<A, SB><<<Gq, kUpdRows, smem_updq, st>>>(n, (int)L.ldn, s, bn, bo, xw, diag, L.part,
+                                                                   k == 0, L.ctrl, L.hist);
             P.end(FAM_UPDATE, k);
         }
         if (cudaGetLastError() != cudaSuccess) { err = 1; break; }
@@ -548,19 +556,21 @@ int solve_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, 
     }
     if (o->arith == SSCG_ARITH_F64) {
         const double* dinv = jac ? mat->dinv : nullptr;
-        if (s <= 4) rc = run_sstep<ArithF64, VAL_F64, 4>(ctx, mat, bd, xd, o, L, dinv, &h, *prof);
-        else if (s <= 8) rc = run_sstep<ArithF64, VAL_F64, 8>(ctx, mat, bd, xd, o, L, dinv, &h, *prof);
-        else rc = run_sstep<ArithF64, VAL_F64, 16>(ctx, mat, bd, xd, o, L, dinv, &h, *prof);
+        const double* diag = jac ? mat->diag : nullptr;
+        if (s <= 4) rc = run_sstep<ArithF64, VAL_F64, 4>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        else if (s <= 8) rc = run_sstep<ArithF64, VAL_F64, 8>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        else rc = run_sstep<ArithF64, VAL_F64, 16>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
     } else {
         const float2* dinv = jac ? mat->dinv_df : nullptr;
+        const float2* diag = jac ? mat->diag_df : nullptr;
         if (mat->exact_fp32) {
-            if (s <= 4) rc = run_sstep<ArithDF64, VAL_F32, 4>(ctx, mat, bd, xd, o, L, dinv, &h, *prof);
-            else if (s <= 8) rc = run_sstep<ArithDF64, VAL_F32, 8>(ctx, mat, bd, xd, o, L, dinv, &h, *prof);
-            else rc = run_sstep<ArithDF64, VAL_F32, 16>(ctx, mat, bd, xd, o, L, dinv, &h, *prof);
+            if (s <= 4) rc = run_sstep<ArithDF64, VAL_F32, 4>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            else if (s <= 8) rc = run_sstep<ArithDF64, VAL_F32, 8>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            else rc = run_sstep<ArithDF64, VAL_F32, 16>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
         } else {
-            if (s <= 4) rc = run_sstep<ArithDF64, VAL_DF, 4>(ctx, mat, bd, xd, o, L, dinv, &h, *prof);
-            else if (s <= 8) rc = run_sstep<ArithDF64, VAL_DF, 8>(ctx, mat, bd, xd, o, L, dinv, &h, *prof);
-            else rc = run_sstep<ArithDF64, VAL_DF, 16>(ctx, mat, bd, xd, o, L, dinv, &h, *prof);
+            if (s <= 4) rc = run_sstep<ArithDF64, VAL_DF, 4>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            else if (s <= 8) rc = run_sstep<ArithDF64, VAL_DF, 8>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            else rc = run_sstep<ArithDF64, VAL_DF, 16>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
         }
     }
     if (rc) {

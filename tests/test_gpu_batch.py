@@ -132,24 +132,27 @@ def test_batch_edge_cases(ctx):
     assert abs(res.rhs[3].outer_iters - ref.iters) <= 1
 
 
-def test_batch_breakdown_stays_local(ctx):
-    """Monomial s = 8 asked for 1e-14 loses the basis's independence before
-    it gets there; the batch reports the failure for that system, keeps x
-    finite, and the other system's outcome is the one the single-system
-    solver gets with the same options."""
+def test_batch_failure_stays_local(ctx):
+    """A right-hand side with a NaN entry fails alone: it is reported as a
+    breakdown (non-finite value) with x left finite, and the other system's
+    outcome is the one the single-system solver gets."""
     cv = csr("varcoef7", 10, 4, 0.5)
     cp = csr("poisson7", 7)
     Av, Ap = sscg.Matrix(ctx, *cv), sscg.Matrix(ctx, *cp)
-    bv = inputs.matvec(*cv, inputs.uniform(5, Av.n))[None, :]
+    bv = np.stack([inputs.matvec(*cv, inputs.uniform(5, Av.n)), inputs.matvec(*cv, inputs.uniform(7, Av.n))])
+    bv[0, 17] = np.nan
     bp = inputs.matvec(*cp, inputs.uniform(6, Ap.n))[None, :]
     B = [torch.from_numpy(bv).cuda(), torch.from_numpy(bp).cuda()]
     X = [torch.zeros_like(B[0]), torch.zeros_like(B[1])]
-    res = sscg.BatchSolver([Av, Ap], [1, 1], s=8, tol=1e-14, maxit=40).solve(B, X)
-    assert res.rhs[0].status in (sscg.BREAKDOWN, sscg.NOT_CONVERGED)
+    res = sscg.BatchSolver([Av, Ap], [2, 1], s=4, tol=1e-9, maxit=300).solve(B, X)
+    assert res.status == sscg.BREAKDOWN
+    assert res.rhs[0].status == sscg.BREAKDOWN and res.rhs[0].outer_iters == 0
+    assert res.rhs[1].status == sscg.OK and res.rhs[1].rel_res_true < 1e-8
     assert np.all(np.isfinite(X[0].cpu().numpy())) and np.all(np.isfinite(X[1].cpu().numpy()))
     x1 = torch.zeros(Ap.n, dtype=torch.float64, device="cuda")
-    single = sscg.Solver(Ap, s=8, tol=1e-14, maxit=40).solve(B[1][0].contiguous(), x1)
-    assert res.rhs[1].status == single.status and res.rhs[1].outer_iters == single.outer_iters
+    single = sscg.Solver(Ap, s=4, tol=1e-9, maxit=300).solve(B[1][0].contiguous(), x1)
+    assert res.rhs[2].status == single.status and res.rhs[2].outer_iters == single.outer_iters
+    assert rel(X[1][0].cpu().numpy(), x1.cpu().numpy()) < 1e-10
 
 
 def test_batch_maxit_reached(ctx):
