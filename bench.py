@@ -8,27 +8,41 @@ recursive rel. residual 1e-8.  One step = one complete solve (init, every
 outer step, export of x, true residual) through the C ABI.
 
 Reported:
-  value      whole-job effective HBM bandwidth of the s-step solves:
-             algorithmic bytes of a solve (per-kernel byte model below) over
-             its device time, summed over ranks
+  value      whole-job effective bandwidth of the s-step solves: the bytes
+             Algorithm 3 moves on the system as given (CSR with FP64 values,
+             FP64 vectors, A U and A P stored: the yardstick model below) over
+             the solve's device time, summed over ranks.  The yardstick does
+             not change with the library's storage choices, so a faster solve
+             always reads higher; plain PCG, the CPU oracle and the reference
+             arm are measured against the same yardstick (Algorithm 1 for PCG).
   e2e        the same metric through the public API with host buffers
              (b, x0 copied in and x copied out inside the timed region)
   roofline   the dominant kernel family, timed by the library's CUDA events
-             on its own stream over the timed steps
+             on its own stream over the timed steps, against the bytes its
+             kernels actually move (the per-kernel byte model below)
   pcg_*      plain PCG (Algorithm 1) on the same kernels, timed beside it
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same solve
 
-Byte model (bytes per launch; V = 8 n, M = 4 (n+1) + nnz (4 + value bytes)):
+Yardstick (bytes per solve, V = 8 n, M = 12 nnz + 4 (n+1)): init M + 5V,
+final M + 2V, per outer step s levels of M + 2V (+ 2V when j < s-1) and the
+block update (6s + 6) V ((4s + 6) V in the first step); PCG per iteration
+M + 13V.
+
+Per-kernel byte model (bytes per launch; V = 8 n, M = 4 (n+1) + nnz (4 + value bytes)):
   MPK level j     M + 3V: u_j gathered, 1/diag read, u_{j+1} = D^-1 A u_j
                   written (A u_j is not stored)
   block update    (5s + 5) V: U_1..U_{s+1}, P_old, Q_old, x, diag read;
                   P, Q, x and the next z written (first step: (2s + 5) V)
+  A matrix in the constant-coefficient diagonal form (the 7-point stencil)
+  replaces M by 4n (one presence mask per row) in the levels and PCG's SpMV,
+  and reads no 1/diag or diag vector: level 4n + 2V, update (5s + 4) V.
   (with --fused-mpk the levels and update of the A U / A P form are timed:
   levels M + 2V, + 2V when j < s-1; update (6s + 6) V, first (4s + 6) V)
   init            M + 5V: x0 gathered, b, 1/diag read, r, z written
                   (DF64: + V, the zeroed correction)
   final           M + 2V: x gathered, b read (DF64: + 3V, x = x0 + correction)
-PCG per iteration: SpMV + p.Ap M + 2V; update 7V; direction 4V.
+PCG per iteration: SpMV + p.Ap M + 2V; update 7V; direction 4V (diagonal
+form: 4n + 2V, 6V, 3V).
 
 Multi-GPU: replicas only.  Every rank solves its own system (seed = rank)
 with no collective on the data path; value = all ranks' bytes / max time.
@@ -77,35 +91,45 @@ def parse():
 # ------------------------------------------------------------ byte model
 
 # DRAM bytes (read + write) per row and launch that ncu --set full measured
-# for this workload's kernels (7-point stencil, df64, s = 4, sequential
-# matrix-powers levels), keyed by kernel family; the roofline's "traffic"
-# scales them to the workload's n.  Empty until the current kernels are
-# captured: traffic is then null.
-NCU_TRAFFIC_PER_ROW = {}
-NCU_TRAFFIC_CONFIG = dict(s=4, arith="df64", fused_mpk=False)
+# for this workload's kernels (7-point stencil in the diagonal form, df64,
+# s = 4, sequential levels) at n = 4,096,000 (profiles/
+# k_level_dia_k_update_q_poisson7_160_df64_s4.txt): a level (mean of two
+# captured launches; at that size L2 still holds most of the level's writes
+# when it ends) and the block update.  The roofline's "traffic" scales them
+# to the workload's n; it is null for any other configuration.
+NCU_TRAFFIC_PER_ROW = {"mpk": 53.678e6 / 4.096e6, "update": 732.694e6 / 4.096e6}
+NCU_TRAFFIC_CONFIG = dict(s=4, arith="df64", fused_mpk=False, dia=True)
 
 
-def byte_model(n, nnz, vbytes, s, arith, fused=False):
+def byte_model(n, nnz, vbytes, s, arith, fused=False, dia=False):
     V = 8 * n
     M = 4 * (n + 1) + nnz * (4 + vbytes)
     df = arith != "f64"
+    # diagonal form: a 4-byte mask per row replaces the CSR arrays in the
+    # levels and PCG's SpMV, and the constant diagonal replaces 1/diag reads
+    Md, dv = (4 * n, 0) if dia else (M, V)
     if fused:
         lv = [M + 2 * V + (2 * V if j < s - 1 else 0) for j in range(s)]
         upd, upd_first = (6 * s + 6) * V, (4 * s + 6) * V
     else:
-        lv = [M + 3 * V for j in range(s)]
-        upd, upd_first = (5 * s + 5) * V, (2 * s + 5) * V
+        lv = [Md + 2 * V + dv for j in range(s)]
+        upd, upd_first = (5 * s + 4) * V + dv, (2 * s + 4) * V + dv
     return dict(M=M, V=V, level=lv, level_avg=sum(lv) / s, update=upd, update_first=upd_first,
                 init=M + 5 * V + (V if df else 0), final=M + 2 * V + (3 * V if df else 0),
-                pcg_spmv=M + 2 * V, pcg_update=7 * V, pcg_dir=4 * V)
+                pcg_spmv=Md + 2 * V, pcg_update=6 * V + dv, pcg_dir=3 * V + dv)
 
 
-def traffic(a, family, n):
+def traffic(a, family, n, dia):
     """Measured DRAM bytes per launch of `family`, scaled to n rows, or None."""
-    cfg = dict(s=a.s, arith=a.arith, fused_mpk=bool(a.fused_mpk))
+    cfg = dict(s=a.s, arith=a.arith, fused_mpk=bool(a.fused_mpk), dia=bool(dia))
     if cfg != NCU_TRAFFIC_CONFIG or family not in NCU_TRAFFIC_PER_ROW:
         return None
     return round(NCU_TRAFFIC_PER_ROW[family] * n)
+
+
+def yardstick(n, nnz, s):
+    """The fixed model behind `value` (see the module docstring)."""
+    return byte_model(n, nnz, 8, s, "f64", fused=True, dia=False)
 
 
 def sstep_bytes(bm, outer):
@@ -250,7 +274,9 @@ def main():
     A = sscg.Matrix(ctx, sysm["rowptr"], sysm["col"], sysm["val"])
     props = A.props()
     vbytes = 8 if a.arith == "f64" else (4 if props["values_exact_fp32"] else 8)
-    bm = byte_model(n, nnz, vbytes, a.s, a.arith, fused=a.fused_mpk)
+    dia = props["format"] == 1 and not a.fused_mpk
+    bm = byte_model(n, nnz, vbytes, a.s, a.arith, fused=a.fused_mpk, dia=dia)
+    ym = yardstick(n, nnz, a.s)
     b = torch.from_numpy(sysm["b"]).cuda()
     x = torch.zeros_like(b)
     solver = sscg.Solver(A, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, profile=True,
@@ -288,7 +314,8 @@ def main():
     r0 = res[-1]
     total_ms = max_over_ranks(pg, sum(ms))
     ms_per_step = total_ms / a.steps
-    bytes_solve = sstep_bytes(bm, r0.outer_iters)
+    bytes_solve = sstep_bytes(ym, r0.outer_iters)
+    kernel_bytes_solve = sstep_bytes(bm, r0.outer_iters)
     value = sum_over_ranks(pg, bytes_solve * a.steps) / (total_ms * 1e-3) / 1e9
 
     # dominant kernel family over the timed steps
@@ -307,11 +334,12 @@ def main():
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
     achieved = d["bytes_per_launch"] / avg_s / 1e9
-    kernel_names = {"mpk": "k_level (matrix-powers level: CSR SpMV + Jacobi + moments)",
+    kernel_names = {"mpk": ("k_level (matrix-powers level: diagonal-form SpMV + Jacobi + moments)" if dia else
+                            "k_level (matrix-powers level: CSR SpMV + Jacobi + moments)"),
                     "update": ("k_update_tma (block update P, AP, x, r + next z)" if a.fused_mpk else
                                "k_update_q (block update P, Q = D^-1 A P, x, z)")}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic(a, dom, n), "kernel": kernel_names[dom],
+                "frac": round(achieved / peak, 4), "traffic": traffic(a, dom, n, dia), "kernel": kernel_names[dom],
                 "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "family_ms_per_solve": {k: round(v["ms"] / a.steps, 3) for k, v in fam.items()},
                 "family_gbs": {k: round(v["bytes_per_launch"] / (v["ms"] / max(v["launches"], 1) * 1e-3) / 1e9, 1)
@@ -327,7 +355,8 @@ def main():
         p0 = pres[-1]
         pcg_ms = max_over_ranks(pg, sum(pms)) / len(pms)
         pcg = dict(pcg_solve_ms=round(pcg_ms, 3), pcg_iters=p0.outer_iters, pcg_rel_res_true=p0.rel_res_true,
-                   pcg_gbs=round(pcg_bytes(bm, p0.outer_iters) / (pcg_ms * 1e-3) / 1e9, 1),
+                   pcg_gbs=round(pcg_bytes(ym, p0.outer_iters) / (pcg_ms * 1e-3) / 1e9, 1),
+                   pcg_kernel_gbs=round(pcg_bytes(bm, p0.outer_iters) / (pcg_ms * 1e-3) / 1e9, 1),
                    speedup_vs_pcg=round(pcg_ms / ms_per_step, 4))
 
     # end to end through the public API with host buffers
@@ -345,17 +374,17 @@ def main():
         hr = hsolver.solve(bh, xh)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(pg, sum(e2e_t) / len(e2e_t))
-    e2e = {"value": round(sum_over_ranks(pg, sstep_bytes(bm, hr.outer_iters)) / e2e_s / 1e9, 1), "unit": "GB/s",
+    e2e = {"value": round(sum_over_ranks(pg, sstep_bytes(ym, hr.outer_iters)) / e2e_s / 1e9, 1), "unit": "GB/s",
            "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": round(e2e_s * 1e3, 3)}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         o = oracle_sample(sysm, a.s, a.cpu_seconds, a.tol)
-        per = (sstep_bytes(bm, o["steps"]) - bm["init"] - bm["final"]) / o["steps"]
+        per = (sstep_bytes(ym, o["steps"]) - ym["init"] - ym["final"]) / o["steps"]
         cpu = {"value": round(per * o["steps"] / o["seconds"] / 1e9, 3), "unit": "GB/s", "cores": o["threads"],
                "kind": "oracle",
                "sample": f"{o['steps']} outer steps of the same s={a.s} solve (tol 0), FP64 C oracle, "
-                         f"{o['seconds']:.1f} s; bytes by the same model, outer steps only"}
+                         f"{o['seconds']:.1f} s; bytes by the same yardstick, outer steps only"}
 
     if rank == 0:
         line = {
@@ -364,12 +393,14 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": a.arith, "data": "synthetic",
             "config": {"workload": workload_name(a.N, a.s, a.arith), "n": n, "nnz": nnz, "s": a.s,
                        "basis": "monomial", "preconditioner": "jacobi", "tol": a.tol,
+                       "matrix_format": "diagonal form (7 offsets, presence mask)" if dia else "csr",
                        "parallelism": f"replicas x{world}",
-                       "l2": f"inputs larger than L2 ({bytes_solve / max(r0.outer_iters, 1) / 1e9:.2f} GB moved "
-                             "per outer step, working set > 4 GB); no flush needed"},
+                       "l2": f"inputs larger than L2 ({kernel_bytes_solve / max(r0.outer_iters, 1) / 1e9:.2f} GB "
+                             "moved per outer step, working set > 4 GB); no flush needed"},
             "solve_ms": round(ms_per_step, 3), "outer_iters": r0.outer_iters, "equiv_iters": r0.equiv_iters,
             "status": r0.status, "rel_res_recursive": r0.rel_res_recursive, "rel_res_true": r0.rel_res_true,
-            "bytes_per_solve": bytes_solve, "wall_s_timed": round(t_wall, 3),
+            "bytes_per_solve": bytes_solve, "kernel_bytes_per_solve": kernel_bytes_solve,
+            "wall_s_timed": round(t_wall, 3),
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(sum(r.profile["kernel_launches"] for r in res)),
             "clocks": clk, "cpu_baseline": cpu,
         }
@@ -528,7 +559,7 @@ def reference_arm(a, world, rank, pg):
 
     sysm = inputs.system("poisson7", a.N, seed=0)
     n, nnz = sysm["n"], len(sysm["col"])
-    bm = byte_model(n, nnz, 8, a.s, "f64")
+    bm = yardstick(n, nnz, a.s)
     M = oracle.as_matrix(sysm)
     t0 = time.perf_counter()
     oracle.pcgs(M, sysm["b"], a.s, tol=0.0, maxit=1)

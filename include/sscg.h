@@ -73,6 +73,17 @@ typedef enum { SSCG_ARITH_F64 = 0, SSCG_ARITH_DF64 = 1, SSCG_ARITH_MIXED = 2 } s
 #define SSCG_DIRECT_GRAM 0x4u  /* form the Gram blocks directly even for the monomial basis */
 #define SSCG_FUSED_MPK 0x8u    /* several matrix-powers levels per launch, intermediate levels kept in L2 */
 #define SSCG_HOST_ARRAYS 0x1u  /* CSR arrays are host pointers (sscg_mat_create_csr) */
+#define SSCG_MAT_CSR_ONLY 0x2u /* keep CSR kernels even for a constant-coefficient diagonal pattern */
+
+/* Storage forms a matrix is multiplied in (sscg_mat_props.format).  CSR is
+ * always kept; a matrix whose rows all hold entries on at most 32 fixed
+ * offsets (j - i), each offset with one FP32-exact value, and a positive
+ * constant diagonal (the constant-coefficient 7- and 27-point stencils) is
+ * also stored as one 32-bit presence mask per row plus the offsets and their
+ * values.  The s-step solver (monomial basis, Jacobi or no preconditioner)
+ * and plain PCG with a diagonal preconditioner then read no column indices,
+ * values or 1/diag; other solves use CSR. */
+enum sscg_format { SSCG_FORMAT_CSR = 0, SSCG_FORMAT_DIA_CONST = 1 };
 
 typedef struct sscg_ctx sscg_ctx;
 typedef struct sscg_mat sscg_mat;
@@ -118,6 +129,8 @@ typedef struct {
     double diag_min, diag_max;
     int prec, prec_degree;
     double prec_lmin, prec_lmax;
+    int format;       /* sscg_format used by the s-step and PCG kernels */
+    int dia_offsets;  /* offsets of the diagonal form (0 for CSR) */
 } sscg_mat_props;
 
 /* ------------------------------------------------------------ context */

@@ -22,6 +22,8 @@ struct Analysis {
     unsigned long long bandwidth;
     unsigned long long dmin_bits;  // positive doubles order like their bit patterns
     unsigned long long dmax_bits;
+    unsigned dia_bad;  // entries violating the constant-coefficient diagonal form
+    unsigned pad;
 };
 
 // Per row: check column range and finiteness, split values into FP32
@@ -97,6 +99,53 @@ __global__ void __launch_bounds__(kThreads) k_analyze(int n, const int32_t* __re
     }
 }
 
+struct DiaDesc {
+    int k;
+    int off[kDiaMax];  // ascending
+    double c[kDiaMax];
+};
+
+// Check the constant-coefficient diagonal form: every entry (i, j) has
+// j - i equal to one of the offsets and the value of that offset; no offset
+// twice in a row.  Writes the presence mask of every row; any violation sets
+// *bad.
+__global__ void __launch_bounds__(kThreads) k_dia_check(int n, const int32_t* __restrict__ rowptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const double* __restrict__ val, DiaDesc d,
+                                                        uint32_t* __restrict__ mask, unsigned* bad) {
+    __shared__ long long s_off[kDiaMax];
+    __shared__ double s_c[kDiaMax];
+    for (int t = threadIdx.x; t < d.k; t += blockDim.x) {
+        s_off[t] = d.off[t];
+        s_c[t] = d.c[t];
+    }
+    __syncthreads();
+    unsigned nbad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t m = 0;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; k++) {
+            const long long o = (long long)col[k] - i;
+            int lo = 0, hi = d.k - 1, t = -1;
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_off[mid] == o) {
+                    t = mid;
+                    break;
+                }
+                if (s_off[mid] < o) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            if (t < 0 || ((m >> t) & 1u) || val[k] != s_c[t]) {
+                nbad++;
+                continue;
+            }
+            m |= 1u << t;
+        }
+        mask[i] = m;
+    }
+    if (nbad) atomicAdd(bad, nbad);
+}
+
 struct MatLayout {
     int32_t* rowptr;
     int32_t* col;
@@ -108,6 +157,7 @@ struct MatLayout {
     float2* dinv_df;
     float2* diag_df;
     float* dinv_f;
+    uint32_t* mask;
     Analysis* an;
     size_t bytes;
 };
@@ -127,9 +177,56 @@ MatLayout mat_layout(int64_t n, int64_t nnz, void* base) {
     L.dinv_df = c.take<float2>((size_t)n + 16);
     L.diag_df = c.take<float2>((size_t)n + 16);
     L.dinv_f = c.take<float>((size_t)n + 16);
+    L.mask = c.take<uint32_t>((size_t)n + 16);
     L.an = c.take<Analysis>(1);
     L.bytes = c.used;
     return L;
+}
+
+// Try the constant-coefficient diagonal form: take the offsets and values
+// of the densest row (row i0, its entries from position k0), require them
+// FP32-exact with a positive diagonal, and check every row on the device.
+int detect_dia(sscg_ctx* ctx, sscg_mat* m, uint32_t* mask, Analysis* an, int32_t k0, int64_t i0, int len) {
+    cudaStream_t st = ctx->stream;
+    std::vector<int32_t> c((size_t)len);
+    std::vector<double> v((size_t)len);
+    SSCG_CUDA(ctx, cudaMemcpyAsync(c.data(), m->col + k0, len * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SSCG_CUDA(ctx, cudaMemcpyAsync(v.data(), m->val + k0, len * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SSCG_CUDA(ctx, cudaStreamSynchronize(st));
+    std::vector<std::pair<long long, double>> e;
+    for (int t = 0; t < len; t++) e.push_back({(long long)c[t] - i0, v[t]});
+    std::sort(e.begin(), e.end());
+    DiaDesc d;
+    memset(&d, 0, sizeof(d));
+    d.k = len;
+    int diag_t = -1;
+    for (int t = 0; t < len; t++) {
+        if (t > 0 && e[t].first == e[t - 1].first) return SSCG_OK;       // duplicate entry: keep CSR
+        if ((double)(float)e[t].second != e[t].second) return SSCG_OK;  // not FP32-exact
+        if (e[t].first < INT32_MIN || e[t].first > INT32_MAX) return SSCG_OK;
+        d.off[t] = (int)e[t].first;
+        d.c[t] = e[t].second;
+        if (e[t].first == 0) diag_t = t;
+    }
+    if (diag_t < 0 || !(d.c[diag_t] > 0.0)) return SSCG_OK;
+    SSCG_CUDA(ctx, cudaMemsetAsync(&an->dia_bad, 0, sizeof(unsigned), st));
+    k_dia_check<<<grid_for(ctx, m->n, 4), kThreads, 0, st>>>((int)m->n, m->rowptr, m->col, m->val, d, mask,
+                                                             &an->dia_bad);
+    SSCG_CUDA(ctx, cudaGetLastError());
+    unsigned bad = 1;
+    SSCG_CUDA(ctx, cudaMemcpyAsync(&bad, &an->dia_bad, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    SSCG_CUDA(ctx, cudaStreamSynchronize(st));
+    if (bad != 0) return SSCG_OK;
+    m->dia = 1;
+    m->dia_k = d.k;
+    for (int t = 0; t < d.k; t++) {
+        m->dia_off[t] = d.off[t];
+        m->dia_c[t] = d.c[t];
+    }
+    m->dia_mask = mask;
+    m->dia_d = d.c[diag_t];
+    m->dia_dinv = 1.0 / d.c[diag_t];
+    return SSCG_OK;
 }
 
 }  // namespace
@@ -227,10 +324,14 @@ int sscg_mat_create_csr(sscg_ctx* ctx, int64_t n, int64_t nnz, const int32_t* ro
     if (hr[0] != 0 || hr[(size_t)n] != nnz)
         return set_err(ctx, SSCG_ERR_INVALID, "rowptr[0] must be 0 and rowptr[n] must be nnz");
     int max_row = 0, max_tile = 0;
+    int64_t max_row_at = 0;
     for (int64_t i = 0; i < n; i++) {
         int len = hr[i + 1] - hr[i];
         if (len < 0) return set_err(ctx, SSCG_ERR_INVALID, "rowptr decreases at row %lld", (long long)i);
-        max_row = std::max(max_row, len);
+        if (len > max_row) {
+            max_row = len;
+            max_row_at = i;
+        }
     }
     for (int64_t t = 0; t < n; t += kTileRows) {
         int64_t e = std::min<int64_t>(n, t + kTileRows);
@@ -275,6 +376,12 @@ int sscg_mat_create_csr(sscg_ctx* ctx, int64_t n, int64_t nnz, const int32_t* ro
     m->dmin = dmn;
     m->dmax = dmx;
     m->prec = SSCG_PREC_JACOBI;
+    if (!(flags & SSCG_MAT_CSR_ONLY) && max_row > 0 && max_row <= kDiaMax) {
+        if (int e = detect_dia(ctx, m, L.mask, L.an, hr[(size_t)max_row_at], max_row_at, max_row)) {
+            free(m);
+            return e;
+        }
+    }
     *out = m;
     return SSCG_OK;
 }
@@ -298,6 +405,8 @@ int sscg_mat_props_get(const sscg_mat* m, sscg_mat_props* p) {
     p->prec_degree = m->degree;
     p->prec_lmin = m->plmin;
     p->prec_lmax = m->plmax;
+    p->format = m->dia ? SSCG_FORMAT_DIA_CONST : SSCG_FORMAT_CSR;
+    p->dia_offsets = m->dia ? m->dia_k : 0;
     return SSCG_OK;
 }
 
@@ -429,7 +538,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv_f64(MatView M, const double* 
 
 int spmv_f64(sscg_ctx* ctx, const sscg_mat* m, const double* x, double* y) {
     const int cap = stage_cap(m);
-    MatView M;
+    MatView M{};
     M.n = (int)m->n;
     M.cap = cap;
     M.rowptr = m->rowptr;

@@ -129,6 +129,7 @@ struct ArithF64 {
     __device__ static __forceinline__ R ldg(const S* p) { return __ldg(p); }
     __device__ static __forceinline__ R ldcg(const S* p) { return __ldcg(p); }
     __device__ static __forceinline__ void st(S* p, R v) { *p = v; }
+    __device__ static __forceinline__ void st_stream(S* p, R v) { __stcs(p, v); }
     __device__ static __forceinline__ R add(R a, R b) { return a + b; }
     __device__ static __forceinline__ R sub(R a, R b) { return a - b; }
     __device__ static __forceinline__ R mul(R a, R b) { return a * b; }
@@ -156,6 +157,7 @@ struct ArithDF64 {
         return df_make(v.x, v.y);
     }
     __device__ static __forceinline__ void st(S* p, R v) { *p = make_float2(v.hi, v.lo); }
+    __device__ static __forceinline__ void st_stream(S* p, R v) { __stcs(p, make_float2(v.hi, v.lo)); }
     __device__ static __forceinline__ R add(R a, R b) { return df_add(a, b); }
     __device__ static __forceinline__ R sub(R a, R b) { return df_add(a, df_neg(b)); }
     __device__ static __forceinline__ R mul(R a, R b) { return df_mul(a, b); }

@@ -46,6 +46,14 @@ struct sscg_mat {
     // (device blob owned by the caller), or null
     const double* bounds_model;
     int bounds_h;
+    // constant-coefficient diagonal form (dia != 0): every row's entries lie
+    // on dia_k fixed offsets, each offset carrying one FP32-exact value;
+    // dia_mask[i] bit t set when row i holds offset t
+    int dia, dia_k;
+    int dia_off[32];
+    double dia_c[32];
+    uint32_t* dia_mask;
+    double dia_d, dia_dinv;  // the diagonal's value and its inverse
 };
 
 namespace sscg {

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(MatView M, const typename
     }
 }
 
-template <class A, int VM>
+template <class A, int VM, bool DIA>
 __global__ void __launch_bounds__(kThreads) k_pcg_spmv(MatView M, const typename A::S* __restrict__ p,
                                                        typename A::S* __restrict__ q, double* __restrict__ part,
                                                        Ctrl* ctrl) {
@@ -109,13 +109,14 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv(MatView M, const typename
     char* smem = align128(smem_raw);
     __shared__ double red[kThreads / 32];
     R pq = A::zero();
-    const bool ok = spmv_pipe<A, VM, kStages>(
-        M, smem, [&](int c) { return A::ldg(p + c); },
-        [&](int row, R y) {
-            A::st(q + row, y);
-            pq = A::fma(A::ldg(p + row), y, pq);
-        },
-        ctrl);
+    auto xf = [&](int c) { return A::ldg(p + c); };
+    auto epi = [&](int row, R y) {
+        A::st(q + row, y);
+        pq = A::fma(A::ldg(p + row), y, pq);
+    };
+    bool ok = true;
+    if constexpr (DIA) spmv_dia<A>(M, xf, epi);
+    else ok = spmv_pipe<A, VM, kStages>(M, smem, xf, epi, ctrl);
     if (!ok) return;
     R v[1] = {pq};
     double out[1];
@@ -139,13 +140,14 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, int diag, typena
                                                          typename A::S* __restrict__ r,
                                                          const typename A::S* __restrict__ p,
                                                          const typename A::S* __restrict__ q,
-                                                         const typename A::S* __restrict__ dinv,
+                                                         const typename A::S* __restrict__ dinv, double dinv_c,
                                                          double* __restrict__ part, Ctrl* ctrl,
                                                          double* __restrict__ hist, double* __restrict__ coef) {
     using R = typename A::R;
     if (done_of(ctrl)) return;
     __shared__ double red[2 * (kThreads / 32)];
     const R alpha = A::from_d(ctrl->pcg_alpha);
+    const R dc = A::from_d(dinv_c);
     R rr = A::zero(), ru = A::zero();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         R pi = A::ld(p + i);
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, int diag, typena
         A::st(r + i, ri);
         rr = A::fma(ri, ri, rr);
         if (diag) {
-            R ui = dinv ? A::mul(A::ld(dinv + i), ri) : ri;
+            R ui = dinv ? A::mul(A::ld(dinv + i), ri) : (dinv_c != 0.0 ? A::mul(dc, ri) : ri);
             ru = A::fma(ri, ui, ru);
         }
     }
@@ -236,15 +238,17 @@ template <class A>
 __global__ void __launch_bounds__(kThreads) k_pcg_dir(int n, int diag, typename A::S* __restrict__ p,
                                                       const typename A::S* __restrict__ r,
                                                       const typename A::S* __restrict__ u,
-                                                      const typename A::S* __restrict__ dinv, const Ctrl* ctrl) {
+                                                      const typename A::S* __restrict__ dinv, double dinv_c,
+                                                      const Ctrl* ctrl) {
     using R = typename A::R;
     if (done_of(ctrl)) return;
     const R beta = A::from_d(ctrl->pcg_beta);
+    const R dc = A::from_d(dinv_c);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         R ui;
         if (diag) {
             R ri = A::ld(r + i);
-            ui = dinv ? A::mul(A::ld(dinv + i), ri) : ri;
+            ui = dinv ? A::mul(A::ld(dinv + i), ri) : (dinv_c != 0.0 ? A::mul(dc, ri) : ri);
         } else {
             ui = A::ld(u + i);
         }
@@ -380,7 +384,7 @@ PLayout pplan(const sscg_mat* mat, int maxit, unsigned flags, void* base, size_t
 }
 
 MatView view(const sscg_mat* mat) {
-    MatView M;
+    MatView M{};
     M.n = (int)mat->n;
     M.cap = stage_cap(mat);
     M.rowptr = mat->rowptr;
@@ -388,12 +392,18 @@ MatView view(const sscg_mat* mat) {
     M.val = mat->val;
     M.vhi = mat->vhi;
     M.vlo = mat->vlo;
+    M.dmask = mat->dia_mask;
+    M.dk = mat->dia ? mat->dia_k : 0;
+    for (int t = 0; t < kDiaMax; t++) {
+        M.doff[t] = t < M.dk ? mat->dia_off[t] : 0;
+        M.dc[t] = t < M.dk ? mat->dia_c[t] : 0.0;
+    }
     return M;
 }
 
 // One PCG run.  x may be null (zero start and no export; the Lanczos
 // estimate); coef receives alpha_j, beta_j when not null.
-template <class A, int VM>
+template <class A, int VM, bool DIA>
 int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int maxit, const PLayout& L,
             const typename A::S* dinv, Ctrl* h, Prof& P, double* coef) {
     using S = typename A::S;
@@ -403,16 +413,23 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int 
     const size_t smem = stage_bytes<A, VM>(M.cap), smem64 = stage_bytes<ArithF64, VAL_F64>(M.cap);
     const size_t smem_pipe = pipe_bytes<VM, kStages>(M.cap) + 128;
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_spmv<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pipe));
+    const size_t smem_sp = DIA ? 128 : smem_pipe;
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_spmv<A, VM, DIA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_sp));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_cheb_step<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pipe));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_true_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
     const int Gi = occupancy_grid(ctx, k_pcg_init<A, VM>, smem, n);
-    const int Gs = occupancy_grid(ctx, k_pcg_spmv<A, VM>, smem_pipe, n);
+    const int Gs = occupancy_grid(ctx, k_pcg_spmv<A, VM, DIA>, smem_sp, n);
+    const int Gc = occupancy_grid(ctx, k_cheb_step<A, VM>, smem_pipe, n);
     const int Gu = occupancy_grid(ctx, k_pcg_update<A>, 0, n);
     const int Gd = occupancy_grid(ctx, k_pcg_dir<A>, 0, n);
     const int Gr = occupancy_grid(ctx, k_pcg_rho<A>, 0, n);
     const int Gt = occupancy_grid(ctx, k_pcg_true_res, smem64, n);
     const bool diag = mat->prec != SSCG_PREC_CHEB;
+    // with the diagonal form, a Jacobi D is the constant diagonal value
+    const bool cd = DIA && dinv != nullptr && diag;
+    const typename A::S* dinv_it = cd ? nullptr : dinv;
+    const double dinv_c = cd ? mat->dia_dinv : 0.0;
     ChebPrec<A, VM> cheb(diag ? 1 : mat->degree, diag ? 1.0 : mat->plmin, diag ? 2.0 : mat->plmax);
     const size_t ld = align_up((size_t)mat->n, 64);
     S* xw = (A::kind == 0) ? (S*)x : (S*)L.x;
@@ -426,7 +443,7 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int 
     k_pcg_init<A, VM><<<Gi, kThreads, smem, st>>>(M, dinv, diag ? 1 : 0, b, x, (A::kind == 0 && x) ? nullptr : xw,
                                                   r, p, L.part, L.ctrl, L.hist);
     if (!diag) {
-        P.launches += cheb.apply(M, dinv, r, p, tmp, ld, Gd, Gs, smem_pipe, st, L.ctrl);
+        P.launches += cheb.apply(M, dinv, r, p, tmp, ld, Gd, Gc, smem_pipe, st, L.ctrl);
         k_pcg_rho<A><<<Gr, kThreads, 0, st>>>(n, r, p, 1, L.part, L.ctrl, coef);
         P.launches++;
     }
@@ -442,19 +459,19 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int 
         for (int k = 0; k < c; k++) {
             const int it = launched + k;
             P.begin();
-            k_pcg_spmv<A, VM><<<Gs, kThreads, smem_pipe, st>>>(M, p, q, L.part, L.ctrl);
+            k_pcg_spmv<A, VM, DIA><<<Gs, kThreads, smem_sp, st>>>(M, p, q, L.part, L.ctrl);
             P.end(FAM_MPK, it);
             P.begin();
-            k_pcg_update<A><<<Gu, kThreads, 0, st>>>(n, diag ? 1 : 0, xw, r, p, q, dinv, L.part, L.ctrl, L.hist,
-                                                     coef);
+            k_pcg_update<A><<<Gu, kThreads, 0, st>>>(n, diag ? 1 : 0, xw, r, p, q, dinv_it, dinv_c, L.part, L.ctrl,
+                                                     L.hist, coef);
             P.end(FAM_UPDATE, it);
             P.begin();
             if (!diag) {
-                P.launches += cheb.apply(M, dinv, r, u, tmp, ld, Gd, Gs, smem_pipe, st, L.ctrl);
+                P.launches += cheb.apply(M, dinv, r, u, tmp, ld, Gd, Gc, smem_pipe, st, L.ctrl);
                 k_pcg_rho<A><<<Gr, kThreads, 0, st>>>(n, r, u, 0, L.part, L.ctrl, coef);
                 P.launches++;
             }
-            k_pcg_dir<A><<<Gd, kThreads, 0, st>>>(n, diag ? 1 : 0, p, r, u, dinv, L.ctrl);
+            k_pcg_dir<A><<<Gd, kThreads, 0, st>>>(n, diag ? 1 : 0, p, r, u, dinv_it, dinv_c, L.ctrl);
             P.end(FAM_DIR, it);
         }
         if (cudaGetLastError() != cudaSuccess) {
@@ -491,11 +508,17 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int 
 int dispatch_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int maxit, int arith,
                  const PLayout& L, Ctrl* h, Prof& P, double* coef) {
     const bool scale = mat->prec != SSCG_PREC_NONE;  // Jacobi and Chebyshev scale by D^-1
-    if (arith == SSCG_ARITH_F64)
-        return run_pcg<ArithF64, VAL_F64>(ctx, mat, b, x, maxit, L, scale ? mat->dinv : nullptr, h, P, coef);
+    // the diagonal form serves the SpMV of a diagonal preconditioner (the
+    // Chebyshev preconditioner's steps stage CSR tiles)
+    const bool dia = mat->dia && mat->prec != SSCG_PREC_CHEB;
+    if (arith == SSCG_ARITH_F64) {
+        if (dia) return run_pcg<ArithF64, VAL_F64, true>(ctx, mat, b, x, maxit, L, scale ? mat->dinv : nullptr, h, P, coef);
+        return run_pcg<ArithF64, VAL_F64, false>(ctx, mat, b, x, maxit, L, scale ? mat->dinv : nullptr, h, P, coef);
+    }
+    if (dia) return run_pcg<ArithDF64, VAL_F32, true>(ctx, mat, b, x, maxit, L, scale ? mat->dinv_df : nullptr, h, P, coef);
     if (mat->exact_fp32)
-        return run_pcg<ArithDF64, VAL_F32>(ctx, mat, b, x, maxit, L, scale ? mat->dinv_df : nullptr, h, P, coef);
-    return run_pcg<ArithDF64, VAL_DF>(ctx, mat, b, x, maxit, L, scale ? mat->dinv_df : nullptr, h, P, coef);
+        return run_pcg<ArithDF64, VAL_F32, false>(ctx, mat, b, x, maxit, L, scale ? mat->dinv_df : nullptr, h, P, coef);
+    return run_pcg<ArithDF64, VAL_DF, false>(ctx, mat, b, x, maxit, L, scale ? mat->dinv_df : nullptr, h, P, coef);
 }
 
 Ctrl fresh_ctrl(int maxit, double tol) {

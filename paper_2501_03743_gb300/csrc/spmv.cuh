@@ -15,6 +15,8 @@ namespace sscg {
 // How the matrix values are stored and multiplied.
 enum ValMode { VAL_F64 = 0, VAL_F32 = 1, VAL_DF = 2 };
 
+constexpr int kDiaMax = 32;
+
 struct MatView {
     int n;
     int cap;  // staging capacity (entries) of the dynamic shared memory
@@ -23,6 +25,11 @@ struct MatView {
     const double* __restrict__ val;
     const float* __restrict__ vhi;
     const float* __restrict__ vlo;
+    // constant-coefficient diagonal form (used when the kernel is built for it)
+    const uint32_t* __restrict__ dmask;
+    int dk;
+    int doff[kDiaMax];
+    double dc[kDiaMax];
 };
 
 template <class A, int VM>
@@ -95,6 +102,134 @@ __device__ __forceinline__ bool tile_spmv(const MatView& M, int tile, XF xf, typ
     for (int k = ks; k < km; k++) y = V::mac(y, s_val[k], xf(s_col[k]));
     for (int k = max(ks, staged); k < ke; k++) y = V::mac(y, V::load(M, base + k), xf(__ldg(M.col + base + k)));
     return true;
+}
+
+// y = (A x)[i] for every row i of a matrix in constant-coefficient diagonal
+// form: y_i = sum over the offsets t that row i holds of c_t x[i + off_t].
+// No column indices or values are read: one 32-bit presence mask per row.
+// Rows are taken grid-stride, so a warp gathers 32 consecutive x entries per
+// offset.  `epi(row, y)` consumes each result.  Every thread must call it.
+//
+// In double-float the row sum is a cascaded dot product (Dot2 of Ogita,
+// Rump and Oishi, "Accurate sum and dot product", 2005): each c_t x_t is
+// split exactly into p + e (FMA TwoProduct of c_t and x_t.hi, plus c_t x_t.lo
+// folded into e), the p are added by TwoSum into one float, every rounding
+// error and e into a second float, and the pair is renormalised once per
+// row: 11 FP32 operations per entry instead of 14 for a renormalised
+// double-float multiply-add each.
+struct Dot2Acc {
+    float s, e;
+};
+
+__device__ __forceinline__ void dot2_add(Dot2Acc& a, float c, df64 x) {
+    const float p = __fmul_rn(c, x.hi);
+    float q = __fmaf_rn(c, x.hi, -p);
+    q = __fmaf_rn(c, x.lo, q);
+    float s, t;
+    two_sum(a.s, p, s, t);
+    a.s = s;
+    a.e = __fadd_rn(a.e, __fadd_rn(t, q));
+}
+
+// The same for a coefficient that is a power of two (the stencils' -1):
+// c x.hi and c x.lo are exact, so no TwoProduct is needed.
+__device__ __forceinline__ void dot2_add_pow2(Dot2Acc& a, float c, df64 x) {
+    const float p = __fmul_rn(c, x.hi);
+    const float q = __fmul_rn(c, x.lo);
+    float s, t;
+    two_sum(a.s, p, s, t);
+    a.s = s;
+    a.e = __fadd_rn(a.e, __fadd_rn(t, q));
+}
+
+__host__ __device__ inline bool is_pow2_float(float c) {
+    if (!(c != 0.0f)) return false;
+    const float a = c < 0.f ? -c : c;
+    int e = 0;
+    return frexpf(a, &e) == 0.5f;
+}
+
+__device__ __forceinline__ df64 dot2_result(const Dot2Acc& a) {
+    float s, t;
+    fast_two_sum(a.s, a.e, s, t);
+    return df_make(s, t);
+}
+
+template <class A, int KM, class XF, class EPI>
+__device__ __forceinline__ void spmv_dia_rows(const MatView& M, const int* s_off, const double* s_c,
+                                              const float* s_cf, XF xf, EPI epi) {
+    using R = typename A::R;
+    const int K = M.dk;
+    const int last = M.n - 1;
+    // up to 8 offsets: offsets and coefficients in registers
+    int off[KM <= 8 ? KM : 1];
+    float cf[KM <= 8 ? KM : 1];
+    double cd[KM <= 8 ? KM : 1];
+    bool p2[KM <= 8 ? KM : 1];
+    if constexpr (KM <= 8) {
+#pragma unroll
+        for (int t = 0; t < KM; t++) {
+            off[t] = t < K ? s_off[t] : 0;
+            cf[t] = t < K ? s_cf[t] : 0.f;
+            cd[t] = t < K ? s_c[t] : 0.0;
+            p2[t] = is_pow2_float(cf[t]);
+        }
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M.n; i += gridDim.x * blockDim.x) {
+        // The gathers do not wait for the mask: every offset is loaded at an
+        // index clamped into [0, n), and the mask only selects which terms
+        // enter the sum, so the loads issue together with the mask's.
+        const uint32_t m = __ldg(M.dmask + i);
+        if constexpr (KM <= 8) {
+            R xv[KM];
+#pragma unroll
+            for (int t = 0; t < KM; t++)
+                if (t < K) xv[t] = xf(min(max(i + off[t], 0), last));
+            if constexpr (A::kind == 0) {
+                double y = 0.0;
+#pragma unroll
+                for (int t = 0; t < KM; t++)
+                    if (t < K && ((m >> t) & 1u)) y = ::fma(cd[t], xv[t], y);
+                epi(i, y);
+            } else {
+                Dot2Acc acc{0.f, 0.f};
+#pragma unroll
+                for (int t = 0; t < KM; t++)
+                    if (t < K && ((m >> t) & 1u)) {
+                        if (p2[t]) dot2_add_pow2(acc, cf[t], xv[t]);  // uniform: same offset for every row
+                        else dot2_add(acc, cf[t], xv[t]);
+                    }
+                epi(i, R(dot2_result(acc)));
+            }
+        } else {
+            if constexpr (A::kind == 0) {
+                double y = 0.0;
+                for (int t = 0; t < K; t++)
+                    if ((m >> t) & 1u) y = ::fma(s_c[t], xf(i + s_off[t]), y);
+                epi(i, y);
+            } else {
+                Dot2Acc acc{0.f, 0.f};
+                for (int t = 0; t < K; t++)
+                    if ((m >> t) & 1u) dot2_add(acc, s_cf[t], xf(i + s_off[t]));
+                epi(i, R(dot2_result(acc)));
+            }
+        }
+    }
+}
+
+template <class A, class XF, class EPI>
+__device__ __forceinline__ void spmv_dia(const MatView& M, XF xf, EPI epi) {
+    __shared__ int s_off[kDiaMax];
+    __shared__ double s_c[kDiaMax];
+    __shared__ float s_cf[kDiaMax];
+    for (int t = threadIdx.x; t < kDiaMax; t += blockDim.x) {
+        s_off[t] = t < M.dk ? M.doff[t] : 0;
+        s_c[t] = t < M.dk ? M.dc[t] : 0.0;
+        s_cf[t] = (float)s_c[t];  // exact: the form requires FP32-exact values
+    }
+    __syncthreads();
+    if (M.dk <= 8) spmv_dia_rows<A, 8>(M, s_off, s_c, s_cf, xf, epi);
+    else spmv_dia_rows<A, kDiaMax>(M, s_off, s_c, s_cf, xf, epi);
 }
 
 // ---------------------------------------------------------------------------

@@ -28,12 +28,14 @@ namespace sscg {
 namespace {
 
 // One level of the matrix-powers kernel (Algorithm 4): y = A u_j, written to
-// AU_j when au_out != null; u_{j+1} = B^-1 y (when u_next != null); moment partials
+// AU_j when au_out != null; u_{j+1} = B^-1 y (when u_next != null; B^-1 the
+// array dinv, or the constant dinv_c when dinv is null and dinv_c != 0, or
+// none); the matrix in CSR tiles or, with DIA, its diagonal form; moment partials
 // mu_{2j+1} = u_j . y and mu_{2j+2} = y . B^-1 y.  With `last` set, the last
 // CTA reduces mu_1..mu_{2s-1} and runs Algorithm 6.
-template <class A, int VM>
+template <class A, int VM, bool DIA>
 __global__ void __launch_bounds__(kThreads) k_level(MatView M, const typename A::S* __restrict__ dinv,
-                                                    const typename A::S* __restrict__ u_in,
+                                                    double dinv_c, const typename A::S* __restrict__ u_in,
                                                     typename A::S* __restrict__ au_out,
                                                     typename A::S* __restrict__ u_next, double* __restrict__ part,
                                                     int j, int s, int step, int last, Ctrl* ctrl) {
@@ -44,18 +46,20 @@ __global__ void __launch_bounds__(kThreads) k_level(MatView M, const typename A:
     __shared__ double red[2 * (kThreads / 32)];
     R m1 = A::zero(), m2 = A::zero();
     const bool want_m2 = (2 * j + 2) <= (2 * s - 1);
-    const bool ok = spmv_pipe<A, VM, kStages>(
-        M, smem, [&](int c) { return A::ldg(u_in + c); },
-        [&](int row, R y) {
-            if (au_out) A::st(au_out + row, y);
-            m1 = A::fma(A::ldg(u_in + row), y, m1);
-            if (u_next || want_m2) {
-                R z = dinv ? A::mul(A::ld(dinv + row), y) : y;
-                if (u_next) A::st(u_next + row, z);
-                m2 = A::fma(y, z, m2);
-            }
-        },
-        ctrl);
+    const R dc = A::from_d(dinv_c);
+    auto xf = [&](int c) { return A::ldg(u_in + c); };
+    auto epi = [&](int row, R y) {
+        if (au_out) A::st(au_out + row, y);
+        m1 = A::fma(A::ldg(u_in + row), y, m1);
+        if (u_next || want_m2) {
+            R z = dinv ? A::mul(A::ld(dinv + row), y) : (dinv_c != 0.0 ? A::mul(dc, y) : y);
+            if (u_next) A::st(u_next + row, z);
+            m2 = A::fma(y, z, m2);
+        }
+    };
+    bool ok = true;
+    if constexpr (DIA) spmv_dia<A>(M, xf, epi);
+    else ok = spmv_pipe<A, VM, kStages>(M, smem, xf, epi, ctrl);
     if (!ok) return;
     R v[2] = {m1, m2};
     double out[2];
@@ -371,7 +375,7 @@ Layout plan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t c
 }
 
 MatView view_of(const sscg_mat* m, int cap) {
-    MatView v;
+    MatView v{};
     v.n = (int)m->n;
     v.cap = cap;
     v.rowptr = m->rowptr;
@@ -379,11 +383,17 @@ MatView view_of(const sscg_mat* m, int cap) {
     v.val = m->val;
     v.vhi = m->vhi;
     v.vlo = m->vlo;
+    v.dmask = m->dia_mask;
+    v.dk = m->dia ? m->dia_k : 0;
+    for (int t = 0; t < kDiaMax; t++) {
+        v.doff[t] = t < v.dk ? m->dia_off[t] : 0;
+        v.dc[t] = t < v.dk ? m->dia_c[t] : 0.0;
+    }
     return v;
 }
 
 
-template <class A, int VM, int SB>
+template <class A, int VM, int SB, bool DIA>
 int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o,
               const Layout& L, const typename A::S* dinv, const typename A::S* diag, Ctrl* hctrl, Prof& P) {
     using S = typename A::S;
@@ -395,7 +405,15 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     const size_t smem_pipe = std::max(pipe_bytes<VM, kStages>(cap), sizeof(SmallScratch)) + 128;
     const size_t smem64 = stage_bytes<ArithF64, VAL_F64>(cap);
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_level<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pipe));
+    // the diagonal form stages nothing; the last level's solves still use the scratch
+    const size_t smem_lv = DIA ? sizeof(SmallScratch) + 128 : smem_pipe;
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_level<A, VM, DIA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_lv));
+    // with the diagonal form and Jacobi, D is the constant diagonal value
+    const bool cd = DIA && dinv != nullptr;
+    const typename A::S* dinv_l = cd ? nullptr : dinv;
+    const typename A::S* diag_u = cd ? nullptr : diag;
+    const double dinv_c = cd ? mat->dia_dinv : 0.0, diag_c = cd ? mat->dia_d : 0.0;
     const size_t smem_fused = std::max(fused_smem<VM>(cap), sizeof(SmallScratch)) + 128;
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_mpk_fused<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem_fused));
@@ -407,7 +425,7 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
 
     P.begin();
     const int Gi = occupancy_grid(ctx, k_init<A, VM>, smem, n);
-    const int Gl = occupancy_grid(ctx, k_level<A, VM>, smem_pipe, n);
+    const int Gl = occupancy_grid(ctx, k_level<A, VM, DIA>, smem_lv, n);
     int per_sm = 0;
     SSCG_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mpk_fused<A, VM>, kFuseThreads,
                                                                  smem_fused));
@@ -453,9 +471,9 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
                 // u_{j+1} = D^-1 A u_j into column j+1 (all j, u_{s+1} too); A u_j is not stored
                 for (int j = 0; j < s; j++) {
                     P.begin();
-                    k_level<A, VM><<<Gl, kThreads, smem_pipe, st>>>(M, dinv, bn + j * ld, nullptr,
-                                                              bn + (j + 1) * ld, L.part, j, s, k, j == s - 1,
-                                                              L.ctrl);
+                    k_level<A, VM, DIA><<<Gl, kThreads, smem_lv, st>>>(M, dinv_l, dinv_c, bn + j * ld, nullptr,
+                                                                     bn + (j + 1) * ld, L.part, j, s, k, j == s - 1,
+                                                                     L.ctrl);
                     P.end(FAM_MPK, k);
                 }
             }
@@ -464,8 +482,8 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
                 k_update_tma<A, SB><<<Gu, kUpdRows, smem_upd, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dinv, L.part,
                                                                     k == 0, 1, L.ctrl, L.hist);
             else
-                k_update_q<A, SB><<<Gq, kUpdRows, smem_updq, st>>>(n, (int)L.ldn, s, bn, bo, xw, diag, L.part,
-                                                                   k == 0, L.ctrl, L.hist);
+                k_update_q<A, SB><<<Gq, kThreads, 0, st>>>(n, (int)L.ldn, s, bn, bo, xw, diag_u, diag_c,
+                                                           L.part, k == 0, L.ctrl, L.hist);
             P.end(FAM_UPDATE, k);
         }
         if (cudaGetLastError() != cudaSuccess) { err = 1; break; }
@@ -547,6 +565,8 @@ int solve_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, 
     h.tol = o->tol;
     SSCG_CUDA(ctx, cudaMemcpyAsync(L.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
     const bool jac = mat->prec == SSCG_PREC_JACOBI;
+    // the diagonal form serves the sequential levels (the fused kernel stages CSR tiles)
+    const bool dia = mat->dia && !(o->flags & SSCG_FUSED_MPK);
     int rc;
     const int s = o->s;
     Prof* prof = new Prof(ctx, (o->flags & SSCG_PROFILE) != 0);
@@ -557,20 +577,28 @@ int solve_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, 
     if (o->arith == SSCG_ARITH_F64) {
         const double* dinv = jac ? mat->dinv : nullptr;
         const double* diag = jac ? mat->diag : nullptr;
-        if (s <= 4) rc = run_sstep<ArithF64, VAL_F64, 4>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-        else if (s <= 8) rc = run_sstep<ArithF64, VAL_F64, 8>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-        else rc = run_sstep<ArithF64, VAL_F64, 16>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        if (dia) {
+            if (s <= 4) rc = run_sstep<ArithF64, VAL_F64, 4, true>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            else if (s <= 8) rc = run_sstep<ArithF64, VAL_F64, 8, true>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            else rc = run_sstep<ArithF64, VAL_F64, 16, true>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        } else if (s <= 4) rc = run_sstep<ArithF64, VAL_F64, 4, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        else if (s <= 8) rc = run_sstep<ArithF64, VAL_F64, 8, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        else rc = run_sstep<ArithF64, VAL_F64, 16, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
     } else {
         const float2* dinv = jac ? mat->dinv_df : nullptr;
         const float2* diag = jac ? mat->diag_df : nullptr;
-        if (mat->exact_fp32) {
-            if (s <= 4) rc = run_sstep<ArithDF64, VAL_F32, 4>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-            else if (s <= 8) rc = run_sstep<ArithDF64, VAL_F32, 8>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-            else rc = run_sstep<ArithDF64, VAL_F32, 16>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        if (dia) {
+            if (s <= 4) rc = run_sstep<ArithDF64, VAL_F32, 4, true>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            else if (s <= 8) rc = run_sstep<ArithDF64, VAL_F32, 8, true>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            else rc = run_sstep<ArithDF64, VAL_F32, 16, true>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        } else if (mat->exact_fp32) {
+            if (s <= 4) rc = run_sstep<ArithDF64, VAL_F32, 4, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            else if (s <= 8) rc = run_sstep<ArithDF64, VAL_F32, 8, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            else rc = run_sstep<ArithDF64, VAL_F32, 16, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
         } else {
-            if (s <= 4) rc = run_sstep<ArithDF64, VAL_DF, 4>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-            else if (s <= 8) rc = run_sstep<ArithDF64, VAL_DF, 8>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-            else rc = run_sstep<ArithDF64, VAL_DF, 16>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            if (s <= 4) rc = run_sstep<ArithDF64, VAL_DF, 4, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            else if (s <= 8) rc = run_sstep<ArithDF64, VAL_DF, 8, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+            else rc = run_sstep<ArithDF64, VAL_DF, 16, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
         }
     }
     if (rc) {

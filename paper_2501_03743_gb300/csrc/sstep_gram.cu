@@ -77,7 +77,7 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
     cudaStream_t st = ctx->stream;
     const int n = (int)mat->n, s = o->s;
     const int cap = stage_cap(mat);
-    MatView M;
+    MatView M{};
     M.n = n;
     M.cap = cap;
     M.rowptr = mat->rowptr;

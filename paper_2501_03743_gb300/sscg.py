@@ -23,6 +23,8 @@ PREC = {"none": 0, "jacobi": 1, "cheb": 2}
 ARITH = {"f64": 0, "df64": 1, "mixed": 2}
 HOST_VECTORS = 0x1
 HOST_ARRAYS = 0x1
+MAT_CSR_ONLY = 0x2
+FORMAT = {0: "csr", 1: "dia_const"}
 
 # Every symbol include/sscg.h declares, for the export check.
 EXPORTS = (
@@ -70,7 +72,8 @@ _PROFILE_FIELDS = ("kernel_launches", "t_init_ms", "t_mpk_ms", "t_update_ms", "t
 class MatProps(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("bandwidth", C.c_int64), ("values_exact_fp32", C.c_int),
                 ("max_row_nnz", C.c_int), ("diag_min", C.c_double), ("diag_max", C.c_double), ("prec", C.c_int),
-                ("prec_degree", C.c_int), ("prec_lmin", C.c_double), ("prec_lmax", C.c_double)]
+                ("prec_degree", C.c_int), ("prec_lmin", C.c_double), ("prec_lmax", C.c_double),
+                ("format", C.c_int), ("dia_offsets", C.c_int)]
 
 
 _lib = None
@@ -187,7 +190,7 @@ class Context:
 class Matrix:
     """CSR SPD matrix copied into torch-allocated device storage."""
 
-    def __init__(self, ctx: Context, rowptr, col, val):
+    def __init__(self, ctx: Context, rowptr, col, val, csr_only=False):
         torch = _torch()
         self.ctx = ctx
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -207,7 +210,8 @@ class Matrix:
         self.storage = torch.empty(nbytes.value, dtype=torch.uint8, device=dev)
         h = C.c_void_p()
         ctx.check(ctx.lib.sscg_mat_create_csr(ctx.h, self.n, self.nnz, C.c_void_p(rp.data_ptr()),
-                                              C.c_void_p(ci.data_ptr()), C.c_void_p(vv.data_ptr()), 0,
+                                              C.c_void_p(ci.data_ptr()), C.c_void_p(vv.data_ptr()),
+                                              MAT_CSR_ONLY if csr_only else 0,
                                               C.c_void_p(self.storage.data_ptr()), nbytes.value, C.byref(h)))
         self.h = h
         self.prec = "jacobi"

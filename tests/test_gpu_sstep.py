@@ -348,3 +348,43 @@ def test_full_size_256_s4_against_oracle(ctx):
     if ref.iters != res.outer_iters:
         ref = oracle.pcgs(M, S["b"], 4, tol=0.0, maxit=res.outer_iters)
     assert rel(x, ref.x) < 1e-7
+
+
+# ------------------------------------------------------- diagonal form
+
+def test_diagonal_form_detection(ctx):
+    """Constant stencils are multiplied in the diagonal form; variable
+    coefficients, a perturbed stencil and CSR-only creation stay CSR."""
+    for kind, N, want in (("poisson7", 9, 7), ("poisson27", 7, 27)):
+        S = system(kind, N, 0)
+        assert gpu_matrix(ctx, S).props()["format"] == 1
+        assert gpu_matrix(ctx, S).props()["dia_offsets"] == want
+        assert sscg.Matrix(ctx, S["rowptr"], S["col"], S["val"], csr_only=True).props()["format"] == 0
+    assert gpu_matrix(ctx, system("varcoef7", 9, 0, 1.0)).props()["format"] == 0
+    S = system("poisson7", 6, 0)
+    val = S["val"].copy()
+    val[100] *= 1.0 + 2.0 ** -40  # one value off the stencil (and not FP32-exact)
+    assert sscg.Matrix(ctx, S["rowptr"], S["col"], val).props()["format"] == 0
+    val = S["val"].copy()
+    val[100] = -2.0  # FP32-exact, but not the diagonal's constant
+    assert sscg.Matrix(ctx, S["rowptr"], S["col"], val).props()["format"] == 0
+
+
+@pytest.mark.parametrize("arith", ["f64", "df64"])
+@pytest.mark.parametrize("kind,N", [("poisson7", 21), ("poisson27", 13)])
+def test_diagonal_form_matches_csr_and_oracle(ctx, arith, kind, N):
+    S = system(kind, N, 3)
+    Ad = gpu_matrix(ctx, S)
+    Ac = sscg.Matrix(ctx, S["rowptr"], S["col"], S["val"], csr_only=True)
+    assert Ad.props()["format"] == 1 and Ac.props()["format"] == 0
+    for method, s in (("sstep", 4), ("sstep", 2), ("pcg", 1)):
+        xd, rd = gpu_solve(Ad, S["b"], method=method, s=s, tol=1e-9, maxit=2000, arith=arith)
+        xc, rc = gpu_solve(Ac, S["b"], method=method, s=s, tol=1e-9, maxit=2000, arith=arith)
+        assert rd.status == rc.status == sscg.OK
+        assert rd.outer_iters == rc.outer_iters
+        assert rel(xd, xc) < 1e-11
+    ref = oracle.pcgs(oracle.as_matrix(S), S["b"], 4, tol=1e-9, maxit=2000)
+    xd, rd = gpu_solve(Ad, S["b"], s=4, tol=1e-9, maxit=2000, arith=arith)
+    assert abs(rd.outer_iters - ref.iters) <= 1
+    same = oracle.pcgs(oracle.as_matrix(S), S["b"], 4, tol=0.0, maxit=rd.outer_iters)
+    assert rel(xd, same.x) < 1e-7
