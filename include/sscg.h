@@ -332,23 +332,29 @@ int sscg_set_bounds_model(sscg_mat* mat, int h, const double* model);
 /* ------------------------------------------------------ batched solves
  *
  * Many independent SPD systems, each with 1..SSCG_BATCH_MAX_RHS right-hand
- * sides, solved together by one persistent cooperative kernel (captured in
- * a CUDA graph when the driver allows).  Every (system, right-hand side)
- * runs Algorithm 3 with the monomial basis and the moment recurrence of
- * Algorithm 6 under the Jacobi preconditioner, exactly as sscg_solve does
- * for one system; the kernel interleaves the systems' matrix-powers levels,
- * s x s solves and block updates, separated by grid-wide barriers, and
- * gathers A's columns once for all right-hand sides of a system.  The paper
- * has no batched form; this is the library's serving path.
+ * sides, solved together.  Every (system, right-hand side) runs Algorithm 3
+ * with the monomial basis and the moment recurrence of Algorithm 6 under the
+ * Jacobi preconditioner, as sscg_solve does for one system (in the z = D^-1 r,
+ * Q = D^-1 A P form).  The kernels work on all systems at once: per outer
+ * step, s matrix-powers levels (each gathering A's column once for all of a
+ * system's right-hand sides, whose vectors are interleaved row by row), one
+ * launch of per-system s x s solves, one block update.  By default each
+ * phase is one launch over every system and an outer step is one CUDA graph,
+ * replayed until every system is done; with SSCG_BATCH_PERSISTENT in
+ * opts->flags the whole solve is one persistent cooperative launch whose
+ * phases are separated by grid-wide barriers (waits bounded by %globaltimer).
+ * The paper has no batched form; this is the library's serving path.
  *
  * The plan binds the matrices (not copied: they must outlive the plan), the
  * options (s <= SSCG_BATCH_MAX_S, monomial basis, f64 or df64 arithmetic,
- * tol, maxit) and the caller's workspace.  Rows are processed in items of T
- * rows per system; T depends on the system's size class (n < 2^16, < 2^19,
- * < 2^21, larger).  With `tune` set, sscg_batch_create times two outer steps
- * of each class's systems (synthetic right-hand sides) for T in {256, 512,
- * 1024, 2048, 4096} and keeps the fastest; otherwise fixed defaults apply.
+ * tol, maxit, flags) and the caller's workspace.  Rows are processed in items
+ * of T rows per system; T depends on the system's size class (n < 2^16,
+ * < 2^19, < 2^21, larger).  With `tune` set, sscg_batch_create times two
+ * outer steps of each class's systems (synthetic right-hand sides) for T in
+ * {256, 512, 1024, 2048, 4096} and keeps the fastest; otherwise fixed
+ * defaults apply.
  */
+#define SSCG_BATCH_PERSISTENT 0x10u /* sscg_opts.flags: the batched solve as one cooperative launch */
 #define SSCG_BATCH_MAX_RHS 8
 #define SSCG_BATCH_MAX_S 8
 #define SSCG_BATCH_MAX_SYSTEMS 4096
@@ -376,9 +382,11 @@ int sscg_batch_destroy(sscg_batch* plan);
  * expired (x then undefined). */
 int sscg_batch_solve(sscg_batch* plan, const double* const* B, double* const* X, sscg_info* infos,
                      sscg_info* rhs_infos, double* latency_ms);
-/* Plan facts: rows per item of every system (nsys entries), the persistent
- * grid size, whether solves replay a CUDA graph, and the last solve's time
- * in ms (CUDA events around the graph).  Any pointer may be NULL. */
+/* Plan facts: rows per item of every system (nsys entries), the grid of the
+ * phase launches (the co-resident grid in the persistent mode), whether
+ * solves replay a CUDA graph (an outer step; the whole solve in the
+ * persistent mode), and the last solve's device time in ms (CUDA events
+ * around it).  Any pointer may be NULL. */
 int sscg_batch_props(const sscg_batch* plan, int* tile_rows, int* grid, int* graph, float* last_ms);
 
 #ifdef __cplusplus

@@ -7,14 +7,17 @@
 // outer step for all systems at once, separated by grid-wide barriers:
 //
 //   level j = 0..s-1   matrix-powers level (Algorithm 4) of every active
-//                      system: AU_j = A U_j, U_{j+1} = D^-1 AU_j for all its
-//                      right-hand sides in one pass over the matrix (SpMM),
+//                      system: U_{j+1} = D^-1 A U_j for all its right-hand
+//                      sides in one pass over the matrix (SpMM; CSR, or the
+//                      constant-coefficient diagonal form for stencils),
 //                      moment partials mu_{2j+1}, mu_{2j+2} per item
 //   solve              per system (one CTA): reduce the partials, test
 //                      convergence, run Algorithm 6 per right-hand side
 //                      (one warp each)
-//   update             block updates of Algorithm 3 plus z = D^-1 r and the
-//                      partials of ||r||^2 and mu_0 for the next step
+//   update             block updates of Algorithm 3 in the z = D^-1 r,
+//                      Q = D^-1 A P form (A U is never stored, as in the
+//                      single-system path) and the partials of ||r||^2 and
+//                      mu_0 for the next step
 //
 // Work is divided into items of T consecutive rows of one system (T chosen
 // per size class, by the autotuner when asked); CTA c takes items c, c+G,
@@ -50,6 +53,10 @@ constexpr int kTileCand[] = {256, 512, 1024, 2048, 4096};
 constexpr int kNumCand = 5;
 constexpr int kMinTile = 256;
 constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;
+// Per-phase level kernel: CSR entries of a 256-row sub-tile staged in shared
+// memory (column index + value as hi/lo floats or a double: 12 bytes).
+constexpr int kLevelCap = 3072;
+constexpr size_t kLevelSmem = (size_t)(kBThreads + 4) * 4 + (size_t)kLevelCap * 12 + 64;
 
 enum SysState { SYS_ACTIVE = 0, SYS_EXPORT = 1, SYS_FINISHED = 2 };
 
@@ -59,15 +66,55 @@ struct BSys {
     const double* val;
     const float* vhi;
     const float* vlo;
-    const void* dinv;  // double (F64) or float2 (double-float)
-    void* blk[2];      // 2s columns of n x R each: U | AU, later P | AP
+    const void* dinv;  // 1/diag: double (F64) or float2 (double-float); null: the constant dinv_c
+    const void* diag;  // diag, the same way (constant diag_c)
+    void* blk[2];      // 2s+1 columns of n x R each: U_1..U_{s+1} | Q; P overwrites U_1..U_s
     void* xw;          // correction to x0, n x R
-    void* r;           // residual, n x R
     double* lpart;     // (2s-1) R rows of `items` moment partials
     double* upart;     // 3 R rows: ||r||^2, mu_0, ||b||^2 (step 0) / true residual^2
+    const uint32_t* dmask;  // constant-coefficient diagonal form (dk > 0), else CSR
+    int dk, pad0;
+    int doff[kDiaMax];
+    float dcf[kDiaMax];
+    double dinv_c, diag_c;
     int n, R, exact, T;
     int items, item0, rhs0, pad;
 };
+
+// The per-row fields of a system, copied into registers once per item (the
+// loops below store to global memory, so fields read through the BSys
+// reference would be reloaded on every element).
+struct BReg {
+    const int32_t* rowptr;
+    const int32_t* col;
+    const double* val;
+    const float* vhi;
+    const float* vlo;
+    const uint32_t* dmask;
+    const void* dinv;
+    const void* diag;
+    double dinv_c, diag_c;
+    int n, R, exact, dk;
+};
+
+__device__ __forceinline__ BReg breg(const BSys& y) {
+    BReg b;
+    b.rowptr = y.rowptr;
+    b.col = y.col;
+    b.val = y.val;
+    b.vhi = y.vhi;
+    b.vlo = y.vlo;
+    b.dmask = y.dmask;
+    b.dinv = y.dinv;
+    b.diag = y.diag;
+    b.dinv_c = y.dinv_c;
+    b.diag_c = y.diag_c;
+    b.n = y.n;
+    b.R = y.R;
+    b.exact = y.exact;
+    b.dk = y.dk;
+    return b;
+}
 
 struct GridBar {
     unsigned count;
@@ -162,78 +209,78 @@ struct BK {
         return reinterpret_cast<S*>(base) + (size_t)c * y.n * y.R;
     }
 
-    // Load the R interleaved values of row i of an n x R vector (data written
-    // in this kernel: through L2).
-    static __device__ __forceinline__ void ld_row(const S* v, int i, int R, Rv (&out)[kMaxR]) {
-        const S* p = v + (size_t)i * R;
-#pragma unroll
-        for (int r = 0; r < kMaxR; r++)
-            if (r < R) out[r] = A::ldcg(p + r);
+    static __device__ __forceinline__ Rv dinv_of(const BReg& y, int i) {
+        return y.dinv ? A::ldg(reinterpret_cast<const S*>(y.dinv) + i) : A::from_d(y.dinv_c);
     }
 
-    static __device__ __forceinline__ Rv dinv_of(const BSys& y, int i) {
-        return A::ldg(reinterpret_cast<const S*>(y.dinv) + i);
+    static __device__ __forceinline__ Rv diag_of(const BReg& y, int i) {
+        return y.diag ? A::ldg(reinterpret_cast<const S*>(y.diag) + i) : A::from_d(y.diag_c);
     }
 
-    // acc[r] = (A v_r)[i] for the R interleaved vectors v (device, this kernel).
-    static __device__ __forceinline__ void spmm_row(const BSys& y, int i, const S* v, Rv (&acc)[kMaxR]) {
+    // (A v_r)[i] for right-hand side r of the interleaved vectors v.  The R
+    // threads of a row read the same matrix entries (broadcast through L1);
+    // their gathers are contiguous.  RO: v was written by an earlier launch
+    // (read-only path); otherwise through L2.  soff/scf: the diagonal form's
+    // offsets and values in shared memory.
+    template <bool RO>
+    static __device__ __forceinline__ Rv spmv_elem(const BReg& y, const int* soff, const float* scf, int i, int r,
+                                                   const S* v) {
         const int R = y.R;
-#pragma unroll
-        for (int r = 0; r < kMaxR; r++) acc[r] = A::zero();
+        Rv acc = A::zero();
+        if (y.dk) {
+            const uint32_t m = __ldg(y.dmask + i);
+            for (int t = 0; t < y.dk; t++) {
+                if (!((m >> t) & 1u)) continue;
+                const S* px = v + (size_t)(i + soff[t]) * R + r;
+                const Rv x = RO ? A::ldg(px) : A::ldcg(px);
+                if constexpr (A::kind == 1) acc = df_fma_f(x, scf[t], acc);
+                else acc = ::fma((double)scf[t], x, acc);
+            }
+            return acc;
+        }
         const int k0 = __ldg(y.rowptr + i), k1 = __ldg(y.rowptr + i + 1);
         for (int k = k0; k < k1; k++) {
-            const int c = __ldg(y.col + k);
-            const S* p = v + (size_t)c * R;
+            const S* px = v + (size_t)__ldg(y.col + k) * R + r;
+            const Rv x = RO ? A::ldg(px) : A::ldcg(px);
             if constexpr (A::kind == 1) {
-                if (y.exact) {
-                    const float a = __ldg(y.vhi + k);
-#pragma unroll
-                    for (int r = 0; r < kMaxR; r++)
-                        if (r < R) acc[r] = df_fma_f(A::ldcg(p + r), a, acc[r]);
-                } else {
-                    const df64 a = df_make(__ldg(y.vhi + k), __ldg(y.vlo + k));
-#pragma unroll
-                    for (int r = 0; r < kMaxR; r++)
-                        if (r < R) acc[r] = df_fma(A::ldcg(p + r), a, acc[r]);
-                }
+                if (y.exact) acc = df_fma_f(x, __ldg(y.vhi + k), acc);
+                else acc = df_fma(x, df_make(__ldg(y.vhi + k), __ldg(y.vlo + k)), acc);
             } else {
-                const double a = __ldg(y.val + k);
-#pragma unroll
-                for (int r = 0; r < kMaxR; r++)
-                    if (r < R) acc[r] = ::fma(a, A::ldcg(p + r), acc[r]);
+                acc = ::fma(__ldg(y.val + k), x, acc);
             }
         }
+        return acc;
     }
 
-    // acc[r] = (A x_r)[i] for FP64 column-major user vectors X (n x R).
-    static __device__ __forceinline__ void spmm_row_user(const BSys& y, int i, const double* X, Rv (&acc)[kMaxR]) {
-        const int R = y.R;
-#pragma unroll
-        for (int r = 0; r < kMaxR; r++) acc[r] = A::zero();
+    // (A x_r)[i] for FP64 column-major user vectors X (n x R, column r at r n).
+    static __device__ __forceinline__ Rv spmv_user_elem(const BReg& y, int i, int r, const double* X) {
+        Rv acc = A::zero();
+        const double* xr = X + (size_t)r * y.n;
         const int k0 = __ldg(y.rowptr + i), k1 = __ldg(y.rowptr + i + 1);
         for (int k = k0; k < k1; k++) {
             const int c = __ldg(y.col + k);
             Rv a;
             if constexpr (A::kind == 1) a = y.exact ? df_make(__ldg(y.vhi + k), 0.f) : df_make(__ldg(y.vhi + k), __ldg(y.vlo + k));
             else a = __ldg(y.val + k);
-#pragma unroll
-            for (int r = 0; r < kMaxR; r++)
-                if (r < R) acc[r] = A::fma(a, A::from_d(__ldcg(X + (size_t)r * y.n + c)), acc[r]);
+            acc = A::fma(a, A::from_d(__ldcg(xr + c)), acc);
         }
+        return acc;
     }
 };
 
-// Sum NV per-thread values over the CTA in a fixed order; thread q < NV
-// receives sum q.  sh holds kMaxR*2 x kBWarps doubles.
+// Sum over the CTA of the values of slot 0..ns-1 (a thread's value belongs
+// to slot `slot`; slot >= ns contributes nothing), each by warp shuffles and
+// then warps in a fixed order; thread q < ns receives slot q's sum.
 template <class A>
-__device__ __forceinline__ void cta_sum_n(typename A::R* v, int NV, double (*sh)[kBWarps], double* out) {
+__device__ __forceinline__ void cta_sum_slots(typename A::R val, int slot, int ns, double (*sh)[kBWarps],
+                                              double* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = 0; q < NV; q++) {
-        typename A::R w = warp_sum<A>(v[q]);
+    for (int q = 0; q < ns; q++) {
+        typename A::R w = warp_sum<A>(slot == q ? val : A::zero());
         if (lane == 0) sh[q][warp] = A::to_d(w);
     }
     __syncthreads();
-    if (threadIdx.x < NV) {
+    if (threadIdx.x < ns) {
         double t = 0.0;
         for (int w = 0; w < kBWarps; w++) t += sh[threadIdx.x][w];
         *out = t;
@@ -241,337 +288,432 @@ __device__ __forceinline__ void cta_sum_n(typename A::R* v, int NV, double (*sh)
     __syncthreads();
 }
 
+// Work mapping inside an item of a system with R right-hand sides: thread t
+// takes right-hand side r = t mod R of rows r0 + t / R, + 256 / R, ...
+// (interleaved element i R + r), so a warp's loads of any column are
+// contiguous and each thread keeps one accumulator per quantity.
+#define ITEM_MAP(y)                                              \
+    const BReg yb = breg(y);                                     \
+    const int R = yb.R;                                          \
+    const int rows_it = kBThreads / R;                           \
+    const int tr = (int)threadIdx.x / R;                         \
+    const int r = (int)threadIdx.x - tr * R;                     \
+    const int slot = tr < rows_it ? r : kMaxR;                   \
+    (void)slot
+
+// Init phase: items it0, it0 + itstep, ... of every system.
 template <class A>
-__global__ void __launch_bounds__(kBThreads, 2) k_batch(BArgs a) {
+__device__ void ph_init(const BArgs& a, int it0, int itstep) {
     using K = BK<A>;
     using Rv = typename A::R;
     using S = typename A::S;
     __shared__ double red[2 * kMaxR][kBWarps];
-    __shared__ double sw_red[(2 * kMaxSB + 2) * kMaxR];
-    __shared__ SmallScratchT<kMaxSB> scratch[kBWarps];
-    __shared__ double s_alpha[kMaxR][kMaxSB];
-    __shared__ double s_beta[kMaxR][kMaxSB * kMaxSB];
-    __shared__ int s_act[kMaxR];
-    const int s = a.s;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.g->t0 = globaltimer();
-
     // ---------------------------------------------------------- init
-    // r = b - A x0, z = D^-1 r = U_0, correction 0; partials ||r||^2, mu_0, ||b||^2
-    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+    // r = b - A x0, z = D^-1 r = U_1, correction 0; partials ||r||^2, mu_0, ||b||^2
+    for (int it = it0; it < a.nitems; it += itstep) {
         const int k = __ldg(a.item_sys + it);
         const BSys& y = a.sys[k];
-        const int li = it - y.item0, R = y.R;
+        ITEM_MAP(y);
+        const int li = it - y.item0;
         const int r0 = li * y.T, r1 = min(y.n, r0 + y.T);
         const double* B = a.tuning ? nullptr : a.io[2 * k];
         const double* X = a.tuning ? nullptr : a.io[2 * k + 1];
-        Rv rr[kMaxR], rz[kMaxR], bb[kMaxR];
-#pragma unroll
-        for (int r = 0; r < kMaxR; r++) rr[r] = rz[r] = bb[r] = A::zero();
+        Rv rr = A::zero(), rz = A::zero(), bb = A::zero();
+        const Rv dinv_cst = A::from_d(yb.dinv_c);
         S* u0 = K::col(y.blk[0], 0, y);
-        S* rv = reinterpret_cast<S*>(y.r);
         S* xw = reinterpret_cast<S*>(y.xw);
-        for (int i = r0 + threadIdx.x; i < r1; i += kBThreads) {
-            Rv ax[kMaxR];
-            if (X) K::spmm_row_user(y, i, X, ax);
-            else
-#pragma unroll
-                for (int r = 0; r < kMaxR; r++) ax[r] = A::zero();
-            const Rv di = K::dinv_of(y, i);
-#pragma unroll
-            for (int r = 0; r < kMaxR; r++) {
-                if (r >= R) continue;
-                const double bv = B ? __ldg(B + (size_t)r * y.n + i) : splitmix_u(0xBA7C5EEDull + k, (size_t)i * R + r);
-                const Rv b = A::from_d(bv);
-                const Rv res = A::sub(b, ax[r]);
-                const Rv z = A::mul(di, res);
-                A::st(rv + (size_t)i * R + r, res);
-                A::st(u0 + (size_t)i * R + r, z);
-                A::st(xw + (size_t)i * R + r, A::zero());
-                rr[r] = A::fma(res, res, rr[r]);
-                rz[r] = A::fma(res, z, rz[r]);
-                bb[r] = A::fma(b, b, bb[r]);
-            }
-        }
-        Rv v[3 * kMaxR];
-        for (int r = 0; r < R; r++) {
-            v[r] = rr[r];
-            v[R + r] = rz[r];
-            v[2 * R + r] = bb[r];
+        for (int i = r0 + tr; tr < rows_it && i < r1; i += rows_it) {
+            const size_t o = (size_t)i * R + r;
+            const Rv ax = X ? K::spmv_user_elem(yb, i, r, X) : A::zero();
+            const double bv = B ? __ldg(B + (size_t)r * y.n + i) : splitmix_u(0xBA7C5EEDull + k, o);
+            const Rv b = A::from_d(bv);
+            const Rv res = A::sub(b, ax);
+            const Rv z = A::mul(yb.dinv ? A::ldg(reinterpret_cast<const S*>(yb.dinv) + i) : dinv_cst, res);
+            A::st(u0 + o, z);
+            A::st(xw + o, A::zero());
+            rr = A::fma(res, res, rr);
+            rz = A::fma(res, z, rz);
+            bb = A::fma(b, b, bb);
         }
         double out = 0.0;
-        // 3R <= 24 values: two passes through the 2*kMaxR-row buffer
-        cta_sum_n<A>(v, 2 * R, red, &out);
-        if (threadIdx.x < 2 * R) y.upart[(size_t)threadIdx.x * y.items + li] = out;
-        cta_sum_n<A>(v + 2 * R, R, red, &out);
+        cta_sum_slots<A>(rr, slot, R, red, &out);
+        if (threadIdx.x < R) y.upart[(size_t)threadIdx.x * y.items + li] = out;
+        cta_sum_slots<A>(rz, slot, R, red, &out);
+        if (threadIdx.x < R) y.upart[(size_t)(R + threadIdx.x) * y.items + li] = out;
+        cta_sum_slots<A>(bb, slot, R, red, &out);
         if (threadIdx.x < R) y.upart[(size_t)(2 * R + threadIdx.x) * y.items + li] = out;
     }
-    if (!grid_sync(a.g)) return;
+}
 
-    for (int outer = 0;; outer++) {
-        // ------------------------------------------------------ levels
-        for (int j = 0; j < s; j++) {
-            for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
-                const int k = __ldg(a.item_sys + it);
-                const BSys& y = a.sys[k];
-                const int state = __ldcg(&a.bctl[k].state);
-                if (state == SYS_FINISHED || (state == SYS_EXPORT && (j > 0 || a.tuning))) continue;
-                const int li = it - y.item0, R = y.R;
-                const int r0 = li * y.T, r1 = min(y.n, r0 + y.T);
-                if (state == SYS_EXPORT) {
-                    // true residual of the exported x: b - A x
-                    const double* B = a.io[2 * k];
-                    const double* X = a.io[2 * k + 1];
-                    Rv tr[kMaxR];
-#pragma unroll
-                    for (int r = 0; r < kMaxR; r++) tr[r] = A::zero();
-                    for (int i = r0 + threadIdx.x; i < r1; i += kBThreads) {
-                        Rv ax[kMaxR];
-                        K::spmm_row_user(y, i, X, ax);
-#pragma unroll
-                        for (int r = 0; r < kMaxR; r++) {
-                            if (r >= R) continue;
-                            const Rv e = A::sub(A::from_d(__ldg(B + (size_t)r * y.n + i)), ax[r]);
-                            tr[r] = A::fma(e, e, tr[r]);
-                        }
-                    }
-                    double out = 0.0;
-                    cta_sum_n<A>(tr, R, red, &out);
-                    if (threadIdx.x < R) y.upart[(size_t)(2 * R + threadIdx.x) * y.items + li] = out;
-                    continue;
-                }
-                const int step = __ldcg(&a.bctl[k].step);
-                void* blk = y.blk[step & 1];
-                const S* uj = K::col(blk, j, y);
-                S* au = K::col(blk, s + j, y);
-                S* un = j < s - 1 ? K::col(blk, j + 1, y) : nullptr;
-                const bool want_m2 = 2 * j + 2 <= 2 * s - 1;
-                Rv m1[kMaxR], m2[kMaxR];
-#pragma unroll
-                for (int r = 0; r < kMaxR; r++) m1[r] = m2[r] = A::zero();
-                for (int i = r0 + threadIdx.x; i < r1; i += kBThreads) {
-                    Rv acc[kMaxR], u[kMaxR];
-                    K::spmm_row(y, i, uj, acc);
-                    K::ld_row(uj, i, R, u);
-                    const Rv di = K::dinv_of(y, i);
-#pragma unroll
-                    for (int r = 0; r < kMaxR; r++) {
-                        if (r >= R) continue;
-                        A::st(au + (size_t)i * R + r, acc[r]);
-                        m1[r] = A::fma(u[r], acc[r], m1[r]);
-                        if (un || want_m2) {
-                            const Rv z = A::mul(di, acc[r]);
-                            if (un) A::st(un + (size_t)i * R + r, z);
-                            m2[r] = A::fma(acc[r], z, m2[r]);
-                        }
-                    }
-                }
-                Rv v[2 * kMaxR];
-                for (int r = 0; r < R; r++) {
-                    v[r] = m1[r];
-                    v[R + r] = m2[r];
-                }
-                const int nv = want_m2 ? 2 * R : R;
-                double out = 0.0;
-                cta_sum_n<A>(v, nv, red, &out);
-                if (threadIdx.x < nv) {
-                    const int q = threadIdx.x < R ? 2 * j : 2 * j + 1;  // moment slot: mu_{q+1}
-                    const int r = threadIdx.x % R;
-                    y.lpart[(size_t)(q * R + r) * y.items + li] = out;
-                }
+// Level j of every active system (RO: u_j was written by an earlier launch,
+// so the gathers may use the read-only path; inside one cooperative launch
+// they go through L2).
+template <class A, bool RO>
+__device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
+    using K = BK<A>;
+    using Rv = typename A::R;
+    using S = typename A::S;
+    __shared__ double red[2 * kMaxR][kBWarps];
+    __shared__ int s_doff[kDiaMax];
+    __shared__ float s_dcf[kDiaMax];
+    const int s = a.s;
+    for (int it = it0; it < a.nitems; it += itstep) {
+        const int k = __ldg(a.item_sys + it);
+        const BSys& y = a.sys[k];
+        const int state = __ldcg(&a.bctl[k].state);
+        if (state == SYS_FINISHED || (state == SYS_EXPORT && (j > 0 || a.tuning))) continue;
+        ITEM_MAP(y);
+        const int li = it - y.item0;
+        const int r0 = li * y.T, r1 = min(y.n, r0 + y.T);
+        if (state == SYS_EXPORT) {
+            // true residual of the exported x: b - A x
+            const double* B = a.io[2 * k];
+            const double* X = a.io[2 * k + 1];
+            Rv tres = A::zero();
+            for (int i = r0 + tr; tr < rows_it && i < r1; i += rows_it) {
+                const Rv e = A::sub(A::from_d(__ldg(B + (size_t)r * yb.n + i)), K::spmv_user_elem(yb, i, r, X));
+                tres = A::fma(e, e, tres);
             }
-            if (!grid_sync(a.g)) return;
+            double out = 0.0;
+            cta_sum_slots<A>(tres, slot, R, red, &out);
+            if (threadIdx.x < R) y.upart[(size_t)(2 * R + threadIdx.x) * y.items + li] = out;
+            continue;
         }
-
-        // ------------------------------------------------------- solve
-        for (int k = blockIdx.x; k < a.nsys; k += gridDim.x) {
-            const BSys& y = a.sys[k];
-            BCtl* bc = &a.bctl[k];
-            const int state = bc->state;
-            if (state == SYS_FINISHED) continue;
-            const int R = y.R, items = y.items, step = bc->step;
-            // rows to reduce: EXPORT: true residual (R); ACTIVE: ||r||^2, mu_0
-            // (+ ||b||^2 at step 0) and the 2s-1 moments
-            const int nu = state == SYS_EXPORT ? R : (step == 0 ? 3 * R : 2 * R);
-            const int ubase = state == SYS_EXPORT ? 2 * R : 0;
-            const int nl = state == SYS_EXPORT ? 0 : (2 * s - 1) * R;
-            for (int q = warp; q < nu + nl; q += kBWarps) {
-                const double* src = q < nu ? y.upart + (size_t)(ubase + q) * items
-                                           : y.lpart + (size_t)(q - nu) * items;
-                double t = 0.0;
-                for (int b = lane; b < items; b += 32) t += __ldcg(src + b);
-#pragma unroll
-                for (int m = 16; m > 0; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
-                if (lane == 0) sw_red[q] = t;
-            }
-            __syncthreads();
-            if (state == SYS_EXPORT) {
-                if (threadIdx.x < R) {
-                    Ctrl* c = &a.rc[y.rhs0 + threadIdx.x];
-                    c->true_res2 = sw_red[threadIdx.x];
-                }
-                if (threadIdx.x == 0) {
-                    bc->state = SYS_FINISHED;
-                    bc->t_fin = globaltimer();
-                    atomicAdd(&a.g->finished, 1);
+        const int step = __ldcg(&a.bctl[k].step);
+        void* blk = y.blk[step & 1];
+        const S* uj = K::col(blk, j, y);
+        S* un = K::col(blk, j + 1, y);  // u_{j+1} = D^-1 A u_j; A u_j is not stored
+        const bool want_m2 = 2 * j + 2 <= 2 * s - 1;
+        const Rv dinv_cst = A::from_d(yb.dinv_c);
+        Rv m1 = A::zero(), m2 = A::zero();
+        auto epi = [&](int i, Rv av) {
+            const size_t o = (size_t)i * R + r;
+            m1 = A::fma(RO ? A::ldg(uj + o) : A::ldcg(uj + o), av, m1);
+            const Rv z = A::mul(yb.dinv ? A::ldg(reinterpret_cast<const S*>(yb.dinv) + i) : dinv_cst, av);
+            A::st(un + o, z);
+            if (want_m2) m2 = A::fma(av, z, m2);
+        };
+        if (!RO || yb.dk) {
+            if (yb.dk) {
+                __syncthreads();  // the previous item is done with the offsets
+                if (threadIdx.x < yb.dk) {
+                    s_doff[threadIdx.x] = y.doff[threadIdx.x];
+                    s_dcf[threadIdx.x] = y.dcf[threadIdx.x];
                 }
                 __syncthreads();
-                continue;
             }
-            if (warp < R) {
-                Ctrl* c = &a.rc[y.rhs0 + warp];
-                int decided = 0;
-                if (lane == 0 && !c->done) {
-                    if (step == 0) {
-                        c->bnorm = sqrt(sw_red[2 * R + warp]);
-                        if (c->bnorm == 0.0) {
-                            c->zero_rhs = 1;
-                            c->relres = 0.0;
-                            c->status = 0;
-                            c->step = 0;
-                            c->done = 1;
-                            decided = 1;
+            for (int i = r0 + tr; tr < rows_it && i < r1; i += rows_it)
+                epi(i, K::template spmv_elem<RO>(yb, s_doff, s_dcf, i, r, uj));
+        } else {
+            // CSR: stage each 256-row sub-tile's row pointers, column indices
+            // and values in shared memory with coalesced loads; the R threads
+            // of a row then read them from there
+            extern __shared__ __align__(16) char lsm[];
+            int* s_rp = reinterpret_cast<int*>(lsm);
+            int* s_col = s_rp + kBThreads + 4;
+            char* vbase = reinterpret_cast<char*>(s_col + kLevelCap);
+            float2* s_vf = reinterpret_cast<float2*>(vbase);
+            double* s_vd = reinterpret_cast<double*>(vbase);
+            for (int t0 = r0; t0 < r1; t0 += kBThreads) {
+                const int rows_t = min(kBThreads, r1 - t0);
+                __syncthreads();  // the previous sub-tile is done with the buffers
+                for (int q = threadIdx.x; q <= rows_t; q += kBThreads) s_rp[q] = __ldg(yb.rowptr + t0 + q);
+                __syncthreads();
+                const int base = s_rp[0];
+                const int staged = min(s_rp[rows_t] - base, kLevelCap);
+                for (int q = threadIdx.x; q < staged; q += kBThreads) {
+                    s_col[q] = __ldg(yb.col + base + q);
+                    if constexpr (A::kind == 1) s_vf[q] = make_float2(__ldg(yb.vhi + base + q), __ldg(yb.vlo + base + q));
+                    else s_vd[q] = __ldg(yb.val + base + q);
+                }
+                __syncthreads();
+                for (int rl = tr; tr < rows_it && rl < rows_t; rl += rows_it) {
+                    const int ks = s_rp[rl] - base, ke = s_rp[rl + 1] - base;
+                    Rv acc = A::zero();
+                    for (int q = ks; q < ke; q++) {
+                        const bool in = q < staged;
+                        const int c = in ? s_col[q] : __ldg(yb.col + base + q);
+                        const Rv x = A::ldg(uj + (size_t)c * R + r);
+                        if constexpr (A::kind == 1) {
+                            const float2 v = in ? s_vf[q] : make_float2(__ldg(yb.vhi + base + q), __ldg(yb.vlo + base + q));
+                            acc = yb.exact ? df_fma_f(x, v.x, acc) : df_fma(x, df_make(v.x, v.y), acc);
+                        } else {
+                            acc = ::fma(in ? s_vd[q] : __ldg(yb.val + base + q), x, acc);
                         }
                     }
-                    if (!decided) {
-                        const double rel = sqrt(sw_red[warp]) / c->bnorm;
-                        c->relres = rel;
-                        c->step = step;
-                        if (!isfinite(rel)) {
-                            c->status = SSCG_BREAKDOWN;
-                            c->done = 1;
-                        } else if (rel < a.tol) {
-                            c->status = 0;
-                            c->done = 1;
-                        } else if (step >= a.maxit) {
-                            c->status = SSCG_NOT_CONVERGED;
-                            c->done = 1;
-                        }
-                    }
-                    if (!c->done) {
-                        c->mu[0] = sw_red[R + warp];
-                        for (int q = 0; q < 2 * s - 1; q++) c->mu[q + 1] = sw_red[nu + q * R + warp];
+                    epi(t0 + rl, acc);
+                }
+            }
+        }
+        double out = 0.0;
+        cta_sum_slots<A>(m1, slot, R, red, &out);
+        if (threadIdx.x < R) y.lpart[(size_t)(2 * j * R + threadIdx.x) * y.items + li] = out;  // mu_{2j+1}
+        if (want_m2) {
+            cta_sum_slots<A>(m2, slot, R, red, &out);
+            if (threadIdx.x < R) y.lpart[(size_t)((2 * j + 1) * R + threadIdx.x) * y.items + li] = out;
+        }
+    }
+}
+
+// Solve phase: systems k0, k0 + kstep, ..., one CTA each.
+template <class A>
+__device__ void ph_solve(const BArgs& a, int k0, int kstep) {
+    __shared__ double sw_red[(2 * kMaxSB + 2) * kMaxR];
+    __shared__ SmallScratchT<kMaxSB> scratch[kBWarps];
+    const int s = a.s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = k0; k < a.nsys; k += kstep) {
+        const BSys& y = a.sys[k];
+        BCtl* bc = &a.bctl[k];
+        const int state = bc->state;
+        if (state == SYS_FINISHED) continue;
+        const int R = y.R, items = y.items, step = bc->step;
+        // rows to reduce: EXPORT: true residual (R); ACTIVE: ||r||^2, mu_0
+        // (+ ||b||^2 at step 0) and the 2s-1 moments
+        const int nu = state == SYS_EXPORT ? R : (step == 0 ? 3 * R : 2 * R);
+        const int ubase = state == SYS_EXPORT ? 2 * R : 0;
+        const int nl = state == SYS_EXPORT ? 0 : (2 * s - 1) * R;
+        for (int q = warp; q < nu + nl; q += kBWarps) {
+            const double* src = q < nu ? y.upart + (size_t)(ubase + q) * items
+                                       : y.lpart + (size_t)(q - nu) * items;
+            // four independent sums per lane keep four loads in flight
+            double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+            int b = lane;
+            for (; b + 96 < items; b += 128) {
+                t0 += __ldcg(src + b);
+                t1 += __ldcg(src + b + 32);
+                t2 += __ldcg(src + b + 64);
+                t3 += __ldcg(src + b + 96);
+            }
+            for (; b < items; b += 32) t0 += __ldcg(src + b);
+            double t = (t0 + t1) + (t2 + t3);
+#pragma unroll
+            for (int m = 16; m > 0; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
+            if (lane == 0) sw_red[q] = t;
+        }
+        __syncthreads();
+        if (state == SYS_EXPORT) {
+            if (threadIdx.x < R) {
+                Ctrl* c = &a.rc[y.rhs0 + threadIdx.x];
+                c->true_res2 = sw_red[threadIdx.x];
+            }
+            if (threadIdx.x == 0) {
+                bc->state = SYS_FINISHED;
+                bc->t_fin = globaltimer();
+                atomicAdd(&a.g->finished, 1);
+            }
+            __syncthreads();
+            continue;
+        }
+        if (warp < R) {
+            Ctrl* c = &a.rc[y.rhs0 + warp];
+            int decided = 0;
+            if (lane == 0 && !c->done) {
+                if (step == 0) {
+                    c->bnorm = sqrt(sw_red[2 * R + warp]);
+                    if (c->bnorm == 0.0) {
+                        c->zero_rhs = 1;
+                        c->relres = 0.0;
+                        c->status = 0;
+                        c->step = 0;
+                        c->done = 1;
+                        decided = 1;
                     }
                 }
-                __syncwarp();
-                const int run = __shfl_sync(0xffffffffu, c->done ? 0 : 1, 0);
-                if (run) {
-                    const int st = warp_sw_monomial(c, s, step, &scratch[warp]);
-                    if (lane == 0 && st != 0) {
+                if (!decided) {
+                    const double rel = sqrt(sw_red[warp]) / c->bnorm;
+                    c->relres = rel;
+                    c->step = step;
+                    if (!isfinite(rel)) {
                         c->status = SSCG_BREAKDOWN;
+                        c->done = 1;
+                    } else if (rel < a.tol) {
+                        c->status = 0;
+                        c->done = 1;
+                    } else if (step >= a.maxit) {
+                        c->status = SSCG_NOT_CONVERGED;
                         c->done = 1;
                     }
                 }
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int all = 1;
-                for (int r = 0; r < R; r++) all &= a.rc[y.rhs0 + r].done ? 1 : 0;
-                if (all) bc->state = SYS_EXPORT;
-                else bc->step = step + 1;
-            }
-            __syncthreads();
-        }
-        if (!grid_sync(a.g)) return;
-        if (*(volatile int*)&a.g->finished >= a.nsys) break;
-
-        // ------------------------------------------------------ update
-        for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
-            const int k = __ldg(a.item_sys + it);
-            const BSys& y = a.sys[k];
-            const int state = __ldcg(&a.bctl[k].state);
-            if (state == SYS_FINISHED) continue;
-            const int li = it - y.item0, R = y.R;
-            const int r0 = li * y.T, r1 = min(y.n, r0 + y.T);
-            if (state == SYS_EXPORT) {
-                if (a.tuning) continue;
-                double* X = const_cast<double*>(a.io[2 * k + 1]);
-                const S* xw = reinterpret_cast<const S*>(y.xw);
-                for (int i = r0 + threadIdx.x; i < r1; i += kBThreads) {
-#pragma unroll
-                    for (int r = 0; r < kMaxR; r++) {
-                        if (r >= R) continue;
-                        const Ctrl* c = &a.rc[y.rhs0 + r];
-                        double* px = X + (size_t)r * y.n + i;
-                        *px = __ldcg(&c->zero_rhs) ? 0.0 : *px + A::to_d(A::ldcg(xw + (size_t)i * R + r));
-                    }
+                if (!c->done) {
+                    c->mu[0] = sw_red[R + warp];
+                    for (int q = 0; q < 2 * s - 1; q++) c->mu[q + 1] = sw_red[nu + q * R + warp];
                 }
+            }
+            __syncwarp();
+            const int run = __shfl_sync(0xffffffffu, c->done ? 0 : 1, 0);
+            if (run) {
+                const int st = warp_sw_monomial(c, s, step, &scratch[warp]);
+                if (lane == 0 && st != 0) {
+                    c->status = SSCG_BREAKDOWN;
+                    c->done = 1;
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int all = 1;
+            for (int q = 0; q < R; q++) all &= a.rc[y.rhs0 + q].done ? 1 : 0;
+            if (all) bc->state = SYS_EXPORT;
+            else bc->step = step + 1;
+        }
+        __syncthreads();
+    }
+}
+
+// Update phase of every active (or exporting) system.
+template <class A, int SB>
+__device__ void ph_update(const BArgs& a, int it0, int itstep) {
+    using K = BK<A>;
+    using Rv = typename A::R;
+    using S = typename A::S;
+    __shared__ double red[2 * kMaxR][kBWarps];
+    // alpha and beta converted once per item (a double-to-double-float
+    // conversion runs on the FP64 pipe, 1/57 of the FP32 rate)
+    __shared__ Rv s_alpha[kMaxR][kMaxSB];
+    __shared__ Rv s_beta[kMaxR][kMaxSB * kMaxSB];
+    __shared__ int s_act[kMaxR];
+    const int s = a.s;
+    for (int it = it0; it < a.nitems; it += itstep) {
+        const int k = __ldg(a.item_sys + it);
+        const BSys& y = a.sys[k];
+        const int state = __ldcg(&a.bctl[k].state);
+        if (state == SYS_FINISHED) continue;
+        ITEM_MAP(y);
+        const int li = it - y.item0;
+        const int r0 = li * y.T, r1 = min(y.n, r0 + y.T);
+        if (state == SYS_EXPORT) {
+            if (a.tuning) continue;
+            double* X = const_cast<double*>(a.io[2 * k + 1]);
+            const S* xw = reinterpret_cast<const S*>(y.xw);
+            const int zero = __ldcg(&a.rc[y.rhs0 + r].zero_rhs);
+            for (int i = r0 + tr; tr < rows_it && i < r1; i += rows_it) {
+                double* px = X + (size_t)r * y.n + i;
+                *px = zero ? 0.0 : *px + A::to_d(A::ldcg(xw + (size_t)i * R + r));
+            }
+            continue;
+        }
+        const int kk = __ldcg(&a.bctl[k].step) - 1;  // the outer step being completed
+        __syncthreads();
+        for (int e = threadIdx.x; e < R * (s + s * s + 1); e += kBThreads) {
+            const int rq = e / (s + s * s + 1), q = e % (s + s * s + 1);
+            const Ctrl* c = &a.rc[y.rhs0 + rq];
+            if (q < s) s_alpha[rq][q] = A::from_d(__ldcg(c->alpha + q));
+            else if (q < s + s * s) s_beta[rq][q - s] = A::from_d(__ldcg(c->beta + (q - s)));
+            else s_act[rq] = __ldcg(&c->done) ? 0 : 1;
+        }
+        __syncthreads();
+        // z / Q form (Algorithm 3 multiplied by D^-1, as the single-system
+        // path): P_j = U_j + sum P_old beta, Q_j = U_{j+1} + sum Q_old beta,
+        // x += P alpha, z -= Q alpha; the next z goes to column 0 of the old block
+        S* nb = reinterpret_cast<S*>(y.blk[kk & 1]);
+        S* ob = reinterpret_cast<S*>(y.blk[(kk + 1) & 1]);
+        const size_t nR = (size_t)y.n * R;
+        S* xw = reinterpret_cast<S*>(y.xw);
+        const bool act = s_act[r] != 0;
+        const Rv dcst = A::from_d(yb.diag_c);
+        Rv rr = A::zero(), rz = A::zero();
+        for (int i = r0 + tr; tr < rows_it && i < r1; i += rows_it) {
+            const size_t o = (size_t)i * R + r;
+            if (!act) {
+                A::st(ob + o, A::ldcg(nb + o));  // frozen: carry z to the next step
                 continue;
             }
-            const int kk = __ldcg(&a.bctl[k].step) - 1;  // the outer step being completed
-            __syncthreads();
-            for (int e = threadIdx.x; e < R * (s + s * s + 1); e += kBThreads) {
-                const int r = e / (s + s * s + 1), q = e % (s + s * s + 1);
-                const Ctrl* c = &a.rc[y.rhs0 + r];
-                if (q < s) s_alpha[r][q] = __ldcg(c->alpha + q);
-                else if (q < s + s * s) s_beta[r][q - s] = __ldcg(c->beta + (q - s));
-                else s_act[r] = __ldcg(&c->done) ? 0 : 1;
-            }
-            __syncthreads();
-            S* nb = reinterpret_cast<S*>(y.blk[kk & 1]);
-            S* ob = reinterpret_cast<S*>(y.blk[(kk + 1) & 1]);
-            const size_t nR = (size_t)y.n * R;
-            S* xw = reinterpret_cast<S*>(y.xw);
-            S* rv = reinterpret_cast<S*>(y.r);
-            Rv rr[kMaxR], rz[kMaxR];
+            Rv u[SB + 1], po[SB], qo[SB];
 #pragma unroll
-            for (int r = 0; r < kMaxR; r++) rr[r] = rz[r] = A::zero();
-            for (int i = r0 + threadIdx.x; i < r1; i += kBThreads) {
-                const Rv di = K::dinv_of(y, i);
-                for (int r = 0; r < R; r++) {
-                    const size_t o = (size_t)i * R + r;
-                    Rv res = A::ldcg(rv + o);
-                    if (s_act[r]) {
-                        Rv po[kMaxSB], apo[kMaxSB];
-                        if (kk > 0) {
+            for (int c = 0; c <= SB; c++)
+                if (c <= s) u[c] = A::ldcg(nb + c * nR + o);
+            if (kk > 0) {
 #pragma unroll
-                            for (int l = 0; l < kMaxSB; l++)
-                                if (l < s) {
-                                    po[l] = A::ldcg(ob + l * nR + o);
-                                    apo[l] = A::ldcg(ob + (s + l) * nR + o);
-                                }
-                        }
-                        Rv x = A::ldcg(xw + o);
-#pragma unroll
-                        for (int jj = 0; jj < kMaxSB; jj++) {
-                            if (jj >= s) continue;
-                            Rv p = A::ldcg(nb + jj * nR + o);
-                            Rv ap = A::ldcg(nb + (s + jj) * nR + o);
-                            if (kk > 0) {
-#pragma unroll
-                                for (int l = 0; l < kMaxSB; l++)
-                                    if (l < s) {
-                                        const Rv bl = A::from_d(s_beta[r][l + jj * s]);
-                                        p = A::fma(po[l], bl, p);
-                                        ap = A::fma(apo[l], bl, ap);
-                                    }
-                                A::st(nb + jj * nR + o, p);
-                                A::st(nb + (s + jj) * nR + o, ap);
-                            }
-                            const double al = s_alpha[r][jj];
-                            x = A::fma(p, A::from_d(al), x);
-                            res = A::fma(ap, A::from_d(-al), res);
-                        }
-                        A::st(xw + o, x);
-                        A::st(rv + o, res);
-                        rr[r] = A::fma(res, res, rr[r]);
+                for (int l = 0; l < SB; l++)
+                    if (l < s) {
+                        po[l] = A::ldcg(ob + l * nR + o);
+                        qo[l] = A::ldcg(ob + (s + 1 + l) * nR + o);
                     }
-                    const Rv z = A::mul(di, res);
-                    A::st(ob + o, z);  // U_0 of the next step (P_old_0 already read)
-                    if (s_act[r]) rz[r] = A::fma(res, z, rz[r]);
+            }
+            Rv x = A::ldcg(xw + o), za = A::zero();
+#pragma unroll
+            for (int jj = 0; jj < SB; jj++) {
+                if (jj >= s) continue;
+                Rv p = u[jj], q = u[jj + 1];
+                if (kk > 0) {
+#pragma unroll
+                    for (int l = 0; l < SB; l++)
+                        if (l < s) {
+                            const Rv bl = s_beta[r][l + jj * s];
+                            p = A::fma(po[l], bl, p);
+                            q = A::fma(qo[l], bl, q);
+                        }
+                    A::st_stream(nb + jj * nR + o, p);
                 }
+                A::st_stream(nb + (s + 1 + jj) * nR + o, q);
+                const Rv al = s_alpha[r][jj];
+                x = A::fma(p, al, x);
+                za = A::fma(q, al, za);
             }
-            Rv v[2 * kMaxR];
-            for (int r = 0; r < R; r++) {
-                v[r] = rr[r];
-                v[R + r] = rz[r];
-            }
-            double out = 0.0;
-            cta_sum_n<A>(v, 2 * R, red, &out);
-            if (threadIdx.x < 2 * R) y.upart[(size_t)threadIdx.x * y.items + li] = out;
+            const Rv z = A::sub(u[0], za);
+            A::st(xw + o, x);
+            A::st(ob + o, z);
+            const Rv rn = A::mul(yb.diag ? A::ldg(reinterpret_cast<const S*>(yb.diag) + i) : dcst, z);
+            rr = A::fma(rn, rn, rr);
+            rz = A::fma(rn, z, rz);
         }
+        double out = 0.0;
+        cta_sum_slots<A>(rr, slot, R, red, &out);
+        if (threadIdx.x < R) y.upart[(size_t)threadIdx.x * y.items + li] = out;
+        cta_sum_slots<A>(rz, slot, R, red, &out);
+        if (threadIdx.x < R) y.upart[(size_t)(R + threadIdx.x) * y.items + li] = out;
+    }
+}
+
+#undef ITEM_MAP
+
+// The whole batched solve in one cooperative launch: the phases separated by
+// grid-wide barriers (bounded waits).
+template <class A, int SB>
+__global__ void __launch_bounds__(kBThreads, 3) k_batch(BArgs a) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.g->t0 = globaltimer();
+    ph_init<A>(a, blockIdx.x, gridDim.x);
+    if (!grid_sync(a.g)) return;
+    for (;;) {
+        for (int j = 0; j < a.s; j++) {
+            ph_level<A, false>(a, j, blockIdx.x, gridDim.x);
+            if (!grid_sync(a.g)) return;
+        }
+        ph_solve<A>(a, blockIdx.x, gridDim.x);
+        if (!grid_sync(a.g)) return;
+        if (*(volatile int*)&a.g->finished >= a.nsys) break;
+        ph_update<A, SB>(a, blockIdx.x, gridDim.x);
         if (!grid_sync(a.g)) return;
     }
+}
+
+// One launch per phase (captured in a CUDA graph per outer step).  Launches
+// queued after every system finished return at once.
+__device__ __forceinline__ bool batch_done(const BArgs& a) { return *(volatile int*)&a.g->finished >= a.nsys; }
+
+template <class A>
+__global__ void __launch_bounds__(kBThreads) k_bp_init(BArgs a) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.g->t0 = globaltimer();
+    ph_init<A>(a, blockIdx.x, gridDim.x);
+}
+
+template <class A>
+__global__ void __launch_bounds__(kBThreads) k_bp_level(BArgs a, int j) {
+    if (batch_done(a)) return;
+    ph_level<A, true>(a, j, blockIdx.x, gridDim.x);
+}
+
+template <class A>
+__global__ void __launch_bounds__(kBThreads) k_bp_solve(BArgs a) {
+    if (batch_done(a)) return;
+    ph_solve<A>(a, blockIdx.x, gridDim.x);
+}
+
+template <class A, int SB>
+__global__ void __launch_bounds__(kBThreads, 3) k_bp_update(BArgs a) {
+    if (batch_done(a)) return;
+    ph_update<A, SB>(a, blockIdx.x, gridDim.x);
 }
 
 int size_class(int64_t n) {
@@ -592,6 +734,9 @@ using namespace sscg;
 struct sscg_batch {
     sscg_ctx* ctx;
     int nsys, s, arith, maxit, total_rhs, nitems, grid, graph_ok;
+    int persistent;              // one cooperative launch instead of per-phase launches
+    int g_init, g_level, g_update;  // per-phase grids
+    cudaGraphExec_t step_exec;   // per-phase mode: one outer step
     double tol;
     std::vector<const sscg_mat*> mats;
     std::vector<int> R, T;
@@ -616,7 +761,7 @@ namespace {
 
 struct BLayout {
     size_t bytes;
-    std::vector<size_t> off_blk0, off_blk1, off_xw, off_r, off_l, off_u;
+    std::vector<size_t> off_blk0, off_blk1, off_xw, off_l, off_u;
     size_t off_sys, off_items, off_g, off_bctl, off_rc, off_io;
 };
 
@@ -652,10 +797,9 @@ BLayout batch_layout(int nsys, const sscg_mat* const* mats, const int* nrhs, int
             c.used += align_up(bytes, 256);
             return o;
         };
-        L.off_blk0.push_back(take(2 * (size_t)s * nR * eb));
-        L.off_blk1.push_back(take(2 * (size_t)s * nR * eb));
+        L.off_blk0.push_back(take((2 * (size_t)s + 1) * nR * eb));
+        L.off_blk1.push_back(take((2 * (size_t)s + 1) * nR * eb));
         L.off_xw.push_back(take(nR * eb));
-        L.off_r.push_back(take(nR * eb));
         L.off_l.push_back(take((size_t)(2 * s - 1) * nrhs[k] * it * sizeof(double)));
         L.off_u.push_back(take((size_t)3 * nrhs[k] * it * sizeof(double)));
     }
@@ -704,8 +848,7 @@ int upload_plan(sscg_batch* b) {
     return SSCG_OK;
 }
 
-template <class A>
-int launch_batch(sscg_batch* b, int tuning, int maxit) {
+BArgs make_args(const sscg_batch* b, int tuning, int maxit) {
     BArgs a;
     a.nsys = b->nsys;
     a.nitems = b->nitems;
@@ -719,23 +862,97 @@ int launch_batch(sscg_batch* b, int tuning, int maxit) {
     a.g = b->d_g;
     a.bctl = b->d_bctl;
     a.rc = b->d_rc;
+    return a;
+}
+
+template <class A, int SB>
+int launch_persistent(sscg_batch* b, int tuning, int maxit, cudaStream_t st) {
+    const BArgs a = make_args(b, tuning, maxit);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(b->grid);
     cfg.blockDim = dim3(kBThreads);
     cfg.dynamicSmemBytes = 0;
-    cfg.stream = b->ctx->stream;
+    cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    SSCG_CUDA(b->ctx, cudaLaunchKernelEx(&cfg, k_batch<A>, a));
+    SSCG_CUDA(b->ctx, cudaLaunchKernelEx(&cfg, k_batch<A, SB>, a));
     return SSCG_OK;
 }
 
-int launch_any(sscg_batch* b, int tuning, int maxit) {
-    return b->arith == SSCG_ARITH_F64 ? launch_batch<ArithF64>(b, tuning, maxit)
-                                      : launch_batch<ArithDF64>(b, tuning, maxit);
+// Per-phase mode: the init launch, and the launches of one outer step.
+template <class A, int SB>
+int launch_init(sscg_batch* b, int tuning, int maxit, cudaStream_t st) {
+    const BArgs a = make_args(b, tuning, maxit);
+    k_bp_init<A><<<b->g_init, kBThreads, 0, st>>>(a);
+    SSCG_CUDA(b->ctx, cudaGetLastError());
+    return SSCG_OK;
+}
+
+template <class A, int SB>
+int launch_step(sscg_batch* b, int tuning, int maxit, cudaStream_t st) {
+    const BArgs a = make_args(b, tuning, maxit);
+    for (int j = 0; j < b->s; j++) k_bp_level<A><<<b->g_level, kBThreads, kLevelSmem, st>>>(a, j);
+    k_bp_solve<A><<<std::min(b->nsys, kMaxGrid), kBThreads, 0, st>>>(a);
+    k_bp_update<A, SB><<<b->g_update, kBThreads, 0, st>>>(a);
+    SSCG_CUDA(b->ctx, cudaGetLastError());
+    return SSCG_OK;
+}
+
+enum LaunchKind { L_PERSISTENT = 0, L_INIT = 1, L_STEP = 2 };
+
+template <class A, int SB>
+int launch_kind(sscg_batch* b, int kind, int tuning, int maxit, cudaStream_t st) {
+    if (kind == L_PERSISTENT) return launch_persistent<A, SB>(b, tuning, maxit, st);
+    if (kind == L_INIT) return launch_init<A, SB>(b, tuning, maxit, st);
+    return launch_step<A, SB>(b, tuning, maxit, st);
+}
+
+// Launch on `st` (default: the context's stream).
+int launch_any(sscg_batch* b, int kind, int tuning, int maxit, cudaStream_t st) {
+    if (b->arith == SSCG_ARITH_F64)
+        return b->s <= 4 ? launch_kind<ArithF64, 4>(b, kind, tuning, maxit, st)
+                         : launch_kind<ArithF64, kMaxSB>(b, kind, tuning, maxit, st);
+    return b->s <= 4 ? launch_kind<ArithDF64, 4>(b, kind, tuning, maxit, st)
+                     : launch_kind<ArithDF64, kMaxSB>(b, kind, tuning, maxit, st);
+}
+
+int launch_any(sscg_batch* b, int kind, int tuning, int maxit) {
+    return launch_any(b, kind, tuning, maxit, b->ctx->stream);
+}
+
+template <class A, int SB>
+int phase_grids(sscg_batch* b) {
+    sscg_ctx* ctx = b->ctx;
+    auto grid_of = [&](auto kernel) {
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBThreads, 0) != cudaSuccess || per < 1) per = 1;
+        return std::min(kMaxGrid, ctx->sm_count * std::min(per, 8));
+    };
+    b->g_init = grid_of(k_bp_init<A>);
+    cudaFuncSetAttribute(k_bp_level<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevelSmem);
+    {
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bp_level<A>, kBThreads, kLevelSmem) != cudaSuccess ||
+            per < 1)
+            per = 1;
+        b->g_level = std::min(kMaxGrid, ctx->sm_count * std::min(per, 8));
+    }
+    b->g_update = grid_of(k_bp_update<A, SB>);
+    int per = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<A, SB>, kBThreads, 0);
+    if (e != cudaSuccess || per < 1)
+        return set_err(ctx, SSCG_ERR_CUDA, "batched kernel cannot be resident: %s", cudaGetErrorString(e));
+    b->grid = per * ctx->sm_count;  // co-resident grid of the cooperative kernel
+    cudaGetLastError();
+    return SSCG_OK;
+}
+
+int setup_grids(sscg_batch* b) {
+    if (b->arith == SSCG_ARITH_F64) return b->s <= 4 ? phase_grids<ArithF64, 4>(b) : phase_grids<ArithF64, kMaxSB>(b);
+    return b->s <= 4 ? phase_grids<ArithDF64, 4>(b) : phase_grids<ArithDF64, kMaxSB>(b);
 }
 
 // Reset the per-solve state on the stream: control blocks zeroed.
@@ -744,6 +961,17 @@ int reset_state(sscg_batch* b) {
     SSCG_CUDA(ctx, cudaMemsetAsync(b->d_g, 0, sizeof(GCtl), ctx->stream));
     SSCG_CUDA(ctx, cudaMemsetAsync(b->d_bctl, 0, sizeof(BCtl) * b->nsys, ctx->stream));
     SSCG_CUDA(ctx, cudaMemsetAsync(b->d_rc, 0, sizeof(Ctrl) * b->total_rhs, ctx->stream));
+    return SSCG_OK;
+}
+
+// One solve without a graph or polling: the cooperative launch, or the init
+// launch and maxit + 3 outer-step launches (each returns at once after the
+// last system finished).  Used by the autotuner and when capture fails.
+int run_plain(sscg_batch* b, int tuning, int maxit) {
+    if (b->persistent) return launch_any(b, L_PERSISTENT, tuning, maxit);
+    if (int rc = launch_any(b, L_INIT, tuning, maxit)) return rc;
+    for (int q = 0; q < maxit + 3; q++)
+        if (int rc = launch_any(b, L_STEP, tuning, maxit)) return rc;
     return SSCG_OK;
 }
 
@@ -780,7 +1008,7 @@ int autotune(sscg_batch* b) {
             for (int rep = 0; rep < 2 && rc == SSCG_OK; rep++) {
                 if ((rc = reset_state(b))) break;
                 cudaEventRecord(e0, ctx->stream);
-                if ((rc = launch_any(b, 1, 2))) break;
+                if ((rc = run_plain(b, 1, 2))) break;
                 cudaEventRecord(e1, ctx->stream);
                 if (cudaEventSynchronize(e1) != cudaSuccess) {
                     rc = set_err(ctx, SSCG_ERR_CUDA, "autotune run failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -810,36 +1038,105 @@ int autotune(sscg_batch* b) {
     return upload_plan(b);
 }
 
-// Capture one solve (state reset, io table upload, kernel, results back) as
-// a CUDA graph; on a capture failure the plan launches directly.
+// Capture the graph a solve replays: the whole solve for the cooperative mode
+// (state reset, pointer upload, kernel, results back), one outer step
+// (s level launches, the solve launch, the update launch) for the per-phase
+// mode.  On a capture failure the plan launches directly.
 void build_graph(sscg_batch* b) {
     sscg_ctx* ctx = b->ctx;
-    cudaStream_t st = ctx->stream;
+    // capture on a private stream: the context's stream may be the legacy
+    // default stream, which cannot be captured; the graph is replayed on it
+    cudaStream_t st = nullptr;
     cudaGraph_t graph = nullptr;
     b->graph_ok = 0;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
+        cudaStreamDestroy(st);
         return;
     }
-    bool ok = reset_state(b) == SSCG_OK;
-    ok = ok && cudaMemcpyAsync(b->d_io, b->h_io, sizeof(double*) * 2 * b->nsys, cudaMemcpyHostToDevice, st) ==
-                   cudaSuccess;
-    ok = ok && launch_any(b, 0, b->maxit) == SSCG_OK;
-    ok = ok && cudaMemcpyAsync(b->h_rc, b->d_rc, sizeof(Ctrl) * b->total_rhs, cudaMemcpyDeviceToHost, st) ==
-                   cudaSuccess;
-    ok = ok && cudaMemcpyAsync(b->h_bctl, b->d_bctl, sizeof(BCtl) * b->nsys, cudaMemcpyDeviceToHost, st) ==
-                   cudaSuccess;
-    ok = ok && cudaMemcpyAsync(b->h_g, b->d_g, sizeof(GCtl), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    bool ok = true;
+    if (b->persistent) {
+        ok = cudaMemsetAsync(b->d_g, 0, sizeof(GCtl), st) == cudaSuccess &&
+             cudaMemsetAsync(b->d_bctl, 0, sizeof(BCtl) * b->nsys, st) == cudaSuccess &&
+             cudaMemsetAsync(b->d_rc, 0, sizeof(Ctrl) * b->total_rhs, st) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(b->d_io, b->h_io, sizeof(double*) * 2 * b->nsys, cudaMemcpyHostToDevice, st) ==
+                       cudaSuccess;
+        ok = ok && launch_any(b, L_PERSISTENT, 0, b->maxit, st) == SSCG_OK;
+        ok = ok && cudaMemcpyAsync(b->h_rc, b->d_rc, sizeof(Ctrl) * b->total_rhs, cudaMemcpyDeviceToHost, st) ==
+                       cudaSuccess;
+        ok = ok && cudaMemcpyAsync(b->h_bctl, b->d_bctl, sizeof(BCtl) * b->nsys, cudaMemcpyDeviceToHost, st) ==
+                       cudaSuccess;
+        ok = ok && cudaMemcpyAsync(b->h_g, b->d_g, sizeof(GCtl), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    } else {
+        ok = launch_any(b, L_STEP, 0, b->maxit, st) == SSCG_OK;
+    }
     cudaError_t e = cudaStreamEndCapture(st, &graph);
-    if (!ok || e != cudaSuccess || !graph) {
-        if (graph) cudaGraphDestroy(graph);
-        cudaGetLastError();
-        return;
+    if (ok && e == cudaSuccess && graph) {
+        cudaGraphExec_t ex = nullptr;
+        if (cudaGraphInstantiate(&ex, graph, 0) == cudaSuccess) {
+            b->graph_ok = 1;
+            if (b->persistent) b->exec = ex;
+            else b->step_exec = ex;
+        }
     }
-    if (cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess) b->graph_ok = 1;
-    else b->exec = nullptr;
-    cudaGraphDestroy(graph);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(st);
     cudaGetLastError();
+}
+
+// Per-phase mode: init launch, then outer steps replayed in chunks until the
+// device's count of finished systems reaches nsys (read back through pinned
+// memory one chunk behind, so the host never stalls the stream).
+int run_phases(sscg_batch* b) {
+    sscg_ctx* ctx = b->ctx;
+    cudaStream_t st = ctx->stream;
+    if (int rc = reset_state(b)) return rc;
+    SSCG_CUDA(ctx, cudaMemcpyAsync(b->d_io, b->h_io, sizeof(double*) * 2 * b->nsys, cudaMemcpyHostToDevice, st));
+    if (int rc = launch_any(b, L_INIT, 0, b->maxit)) return rc;
+    const int limit = b->maxit + 4, per_chunk = 8;
+    cudaEvent_t ev[2];
+    SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    int launched = 0, chunk = 0, pending = -1, rc = SSCG_OK;
+    while (launched < limit) {
+        const int c = std::min(per_chunk, limit - launched);
+        for (int q = 0; q < c && rc == SSCG_OK; q++) {
+            if (b->graph_ok) {
+                if (cudaGraphLaunch(b->step_exec, st) != cudaSuccess)
+                    rc = set_err(ctx, SSCG_ERR_CUDA, "graph launch: %s", cudaGetErrorString(cudaGetLastError()));
+            } else {
+                rc = launch_any(b, L_STEP, 0, b->maxit);
+            }
+        }
+        if (rc) break;
+        launched += c;
+        const int slot = chunk & 1;
+        if (cudaMemcpyAsync((void*)(ctx->pinned + slot), &b->d_g->finished, sizeof(int), cudaMemcpyDeviceToHost,
+                            st) != cudaSuccess ||
+            cudaEventRecord(ev[slot], st) != cudaSuccess) {
+            rc = set_err(ctx, SSCG_ERR_CUDA, "polling copy failed");
+            break;
+        }
+        if (pending >= 0) {
+            if (cudaEventSynchronize(ev[pending & 1]) != cudaSuccess) {
+                rc = set_err(ctx, SSCG_ERR_CUDA, "polling wait failed");
+                break;
+            }
+            if (ctx->pinned[pending & 1] >= b->nsys) break;
+        }
+        pending = chunk++;
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc) return rc;
+    SSCG_CUDA(ctx, cudaMemcpyAsync(b->h_rc, b->d_rc, sizeof(Ctrl) * b->total_rhs, cudaMemcpyDeviceToHost, st));
+    SSCG_CUDA(ctx, cudaMemcpyAsync(b->h_bctl, b->d_bctl, sizeof(BCtl) * b->nsys, cudaMemcpyDeviceToHost, st));
+    SSCG_CUDA(ctx, cudaMemcpyAsync(b->h_g, b->d_g, sizeof(GCtl), cudaMemcpyDeviceToHost, st));
+    return SSCG_OK;
 }
 
 }  // namespace
@@ -886,11 +1183,26 @@ int sscg_batch_create(sscg_ctx* ctx, int nsys, const sscg_mat* const* mats, cons
         y.val = m->val;
         y.vhi = m->vhi;
         y.vlo = m->vlo;
-        y.dinv = opts->arith == SSCG_ARITH_F64 ? (const void*)m->dinv : (const void*)m->dinv_df;
+        const bool f64 = opts->arith == SSCG_ARITH_F64;
+        if (m->dia) {
+            // constant-coefficient diagonal form: masks, offsets, values; D is one constant
+            y.dmask = m->dia_mask;
+            y.dk = m->dia_k;
+            for (int t = 0; t < m->dia_k; t++) {
+                y.doff[t] = m->dia_off[t];
+                y.dcf[t] = (float)m->dia_c[t];
+            }
+            y.dinv = nullptr;
+            y.diag = nullptr;
+            y.dinv_c = m->dia_dinv;
+            y.diag_c = m->dia_d;
+        } else {
+            y.dinv = f64 ? (const void*)m->dinv : (const void*)m->dinv_df;
+            y.diag = f64 ? (const void*)m->diag : (const void*)m->diag_df;
+        }
         y.blk[0] = base + L.off_blk0[k];
         y.blk[1] = base + L.off_blk1[k];
         y.xw = base + L.off_xw[k];
-        y.r = base + L.off_r[k];
         y.lpart = (double*)(base + L.off_l[k]);
         y.upart = (double*)(base + L.off_u[k]);
         y.n = (int)m->n;
@@ -908,13 +1220,8 @@ int sscg_batch_create(sscg_ctx* ctx, int nsys, const sscg_mat* const* mats, cons
         sscg_batch_destroy(b);
         return rc;
     };
-    int per_sm = 0;
-    cudaError_t e = opts->arith == SSCG_ARITH_F64
-                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<ArithF64>, kBThreads, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<ArithDF64>, kBThreads, 0);
-    if (e != cudaSuccess || per_sm < 1)
-        return fail(set_err(ctx, SSCG_ERR_CUDA, "batched kernel cannot be resident: %s", cudaGetErrorString(e)));
-    b->grid = per_sm * ctx->sm_count;
+    b->persistent = (opts->flags & SSCG_BATCH_PERSISTENT) ? 1 : 0;
+    if (int rc = setup_grids(b)) return fail(rc);
     if (cudaMallocHost((void**)&b->h_io, sizeof(double*) * 2 * nsys) != cudaSuccess ||
         cudaMallocHost((void**)&b->h_rc, sizeof(Ctrl) * rhs) != cudaSuccess ||
         cudaMallocHost((void**)&b->h_bctl, sizeof(BCtl) * nsys) != cudaSuccess ||
@@ -932,6 +1239,7 @@ int sscg_batch_create(sscg_ctx* ctx, int nsys, const sscg_mat* const* mats, cons
 int sscg_batch_destroy(sscg_batch* b) {
     if (!b) return SSCG_ERR_INVALID;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->step_exec) cudaGraphExecDestroy(b->step_exec);
     if (b->h_io) cudaFreeHost(b->h_io);
     if (b->h_rc) cudaFreeHost(b->h_rc);
     if (b->h_bctl) cudaFreeHost(b->h_bctl);
@@ -955,12 +1263,14 @@ int sscg_batch_solve(sscg_batch* b, const double* const* B, double* const* X, ss
     SSCG_CUDA(ctx, cudaEventCreate(&e0));
     SSCG_CUDA(ctx, cudaEventCreate(&e1));
     SSCG_CUDA(ctx, cudaEventRecord(e0, st));
-    if (b->graph_ok) {
+    if (!b->persistent) {
+        if (int rc = run_phases(b)) return rc;
+    } else if (b->graph_ok) {
         SSCG_CUDA(ctx, cudaGraphLaunch(b->exec, st));
     } else {
         if (int rc = reset_state(b)) return rc;
         SSCG_CUDA(ctx, cudaMemcpyAsync(b->d_io, b->h_io, sizeof(double*) * 2 * b->nsys, cudaMemcpyHostToDevice, st));
-        if (int rc = launch_any(b, 0, b->maxit)) return rc;
+        if (int rc = launch_any(b, L_PERSISTENT, 0, b->maxit)) return rc;
         SSCG_CUDA(ctx, cudaMemcpyAsync(b->h_rc, b->d_rc, sizeof(Ctrl) * b->total_rhs, cudaMemcpyDeviceToHost, st));
         SSCG_CUDA(ctx, cudaMemcpyAsync(b->h_bctl, b->d_bctl, sizeof(BCtl) * b->nsys, cudaMemcpyDeviceToHost, st));
         SSCG_CUDA(ctx, cudaMemcpyAsync(b->h_g, b->d_g, sizeof(GCtl), cudaMemcpyDeviceToHost, st));
@@ -1017,7 +1327,7 @@ int sscg_batch_props(const sscg_batch* b, int* tile_rows, int* grid, int* graph,
     if (!b) return SSCG_ERR_INVALID;
     if (tile_rows)
         for (int k = 0; k < b->nsys; k++) tile_rows[k] = b->T[k];
-    if (grid) *grid = b->grid;
+    if (grid) *grid = b->persistent ? b->grid : b->g_update;
     if (graph) *graph = b->graph_ok;
     if (last_ms) *last_ms = b->last_ms;
     return SSCG_OK;

@@ -38,6 +38,7 @@ EXPORTS = (
     "sscg_batch_destroy", "sscg_batch_solve", "sscg_batch_props",
 )
 BATCH_MAX_RHS = 8
+BATCH_PERSISTENT = 0x10
 BATCH_MAX_S = 8
 NFEAT = 10
 STATIC_SCRATCH_BYTES = 16 << 20
@@ -356,7 +357,7 @@ class BatchSolver:
     """Plan for solving many systems (each with 1..8 right-hand sides) in one
     persistent launch; see sscg_batch_create."""
 
-    def __init__(self, mats, nrhs, s=4, tol=1e-8, maxit=1000, arith="df64", tune=False):
+    def __init__(self, mats, nrhs, s=4, tol=1e-8, maxit=1000, arith="df64", tune=False, persistent=False):
         torch = _torch()
         self.mats = list(mats)
         self.nrhs = [int(r) for r in nrhs]
@@ -367,6 +368,8 @@ class BatchSolver:
         self._mh = (C.c_void_p * k)(*[m.h.value for m in self.mats])
         self._nr = (C.c_int * k)(*self.nrhs)
         self.opts = make_opts(s=s, tol=tol, maxit=maxit, arith=arith)
+        if persistent:
+            self.opts.flags |= BATCH_PERSISTENT
         nbytes = C.c_size_t()
         rc = lib.sscg_batch_workspace_bytes(k, self._mh, self._nr, C.byref(self.opts), C.byref(nbytes))
         if rc != OK:

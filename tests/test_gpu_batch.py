@@ -68,11 +68,12 @@ def make_batch(ctx, spec, rhs_seed=100):
     return mats, csrs, B, X
 
 
+@pytest.mark.parametrize("persistent", [False, True], ids=["phases", "persistent"])
 @pytest.mark.parametrize("arith", ["df64", "f64"])
 @pytest.mark.parametrize("s", [2, 4])
-def test_batch_matches_oracle_per_rhs(ctx, arith, s):
+def test_batch_matches_oracle_per_rhs(ctx, arith, s, persistent):
     mats, csrs, B, X = make_batch(ctx, MIX)
-    plan = sscg.BatchSolver(mats, [m[3] for m in MIX], s=s, tol=1e-8, maxit=500, arith=arith)
+    plan = sscg.BatchSolver(mats, [m[3] for m in MIX], s=s, tol=1e-8, maxit=500, arith=arith, persistent=persistent)
     res = plan.solve(B, X)
     assert res.status == sscg.OK
     q = 0
@@ -96,10 +97,11 @@ def test_batch_matches_oracle_per_rhs(ctx, arith, s):
     assert np.all(res.latency_ms > 0) and np.all(res.latency_ms <= res.solve_ms * 1.01 + 0.05)
 
 
-def test_batch_matches_single_system_solver(ctx):
+@pytest.mark.parametrize("persistent", [False, True], ids=["phases", "persistent"])
+def test_batch_matches_single_system_solver(ctx, persistent):
     spec = [("varcoef7", 16, 3, 3), ("poisson27", 9, 0, 1), ("poisson7", 20, 0, 2)]
     mats, csrs, B, X = make_batch(ctx, spec, rhs_seed=7)
-    res = sscg.BatchSolver(mats, [m[3] for m in spec], s=4, tol=1e-9, maxit=400).solve(B, X)
+    res = sscg.BatchSolver(mats, [m[3] for m in spec], s=4, tol=1e-9, maxit=400, persistent=persistent).solve(B, X)
     q = 0
     for i, (sp, A) in enumerate(zip(spec, mats)):
         for r in range(sp[3]):
