@@ -80,8 +80,10 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--fused-mpk", action="store_true", help="several matrix-powers levels per launch (L2-resident)")
-    p.add_argument("--workload", default="poisson", choices=["poisson", "batch"],
-                   help="poisson: one 7-point solve (the headline); batch: the batched serving mix")
+    p.add_argument("--workload", default="poisson", choices=["poisson", "batch", "mixed27", "cheb"],
+                   help="poisson: one 7-point solve (the headline); batch: the batched serving mix; "
+                        "mixed27: 27-point 192^3 in mixed precision to 1e-10; cheb: Chebyshev basis with "
+                        "network vs Lanczos intervals on variable-coefficient 128^3 fields")
     p.add_argument("--batch-systems", type=int, default=64)
     p.add_argument("--no-tune", action="store_true", help="batch: fixed tiles instead of the autotuner")
     p.add_argument("--no-seq", action="store_true", help="batch: skip the one-at-a-time comparison")
@@ -258,6 +260,10 @@ def main():
         return reference_arm(a, world, rank, pg)
     if a.workload == "batch":
         return run_batch(a, world, rank, local, pg)
+    if a.workload == "mixed27":
+        return run_mixed27(a, world, rank, local, pg)
+    if a.workload == "cheb":
+        return run_cheb(a, world, rank, local, pg)
 
     import torch
 
@@ -549,6 +555,167 @@ def run_batch(a, world, rank, local, pg):
         }
         if seq:
             line.update(seq)
+        print(json.dumps(line), flush=True)
+    barrier(pg)
+
+
+MIXED_METRIC = "mixed-precision s-step PCG: 27-point 192^3 to rel. residual 1e-10, error vs the FP64 oracle"
+
+
+def run_mixed27(a, world, rank, local, pg):
+    """27-point stencil on 192^3 (a.N overrides), mixed precision (FP32 values
+    and basis, double-float Gram, P, AP, x, r, true-residual replacement every
+    outer step) to 1e-10, beside the double-float path to the same tolerance.
+    The cpu_baseline leg solves the same system with the FP64 CPU oracle's PCG
+    (timed on the host cores); its solution is also what the GPU solutions'
+    error is measured against."""
+    import torch
+
+    from paper_2501_03743_gb300 import inputs
+    import oracle
+
+    N = a.N if a.N != 256 else 192
+    sysm = inputs.system("poisson27", N, seed=rank)
+    n, nnz = sysm["n"], len(sysm["col"])
+    t0 = time.perf_counter()
+    ref = oracle.pcg(oracle.as_matrix(sysm), sysm["b"], tol=1e-10, maxit=20000)  # host cores, before CUDA
+    t_oracle = time.perf_counter() - t0
+    if rank == 0:
+        from paper_2501_03743_gb300 import build
+
+        build.build()
+    barrier(pg)
+    torch.cuda.set_device(local)
+    from paper_2501_03743_gb300 import sscg
+
+    ctx = sscg.Context()
+    A = sscg.Matrix(ctx, sysm["rowptr"], sysm["col"], sysm["val"])
+    b = torch.from_numpy(sysm["b"]).cuda()
+    x = torch.zeros_like(b)
+    out = {}
+    for name, kw in (("mixed", dict(arith="mixed", replace_every=1)), ("df64", dict(arith="df64"))):
+        solver = sscg.Solver(A, s=a.s, tol=1e-10, maxit=5000, **kw)
+        x.zero_()
+        solver.solve(b, x)
+        ms, res = [], None
+        for _ in range(max(1, a.steps)):
+            x.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            res = solver.solve(b, x)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        xs = x.cpu().numpy()
+        out[name] = dict(ms=statistics.median(ms), outer=res.outer_iters, status=res.status,
+                         rel_res_true=res.rel_res_true,
+                         err_vs_oracle=float(np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x)),
+                         err_vs_x_true=float(np.linalg.norm(xs - sysm["x_true"]) / np.linalg.norm(sysm["x_true"])))
+    m = out["mixed"]
+    if rank == 0:
+        line = {"metric": MIXED_METRIC, "value": round(m["ms"], 3), "unit": "ms", "n_gpus": world,
+                "steps": a.steps, "warmup": 1, "ms_per_step": round(m["ms"], 3), "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "mixed (fp32 basis, df64 accumulation)",
+                "data": "synthetic",
+                "config": {"workload": f"poisson27 {N}^3 (n={n:,}, nnz={nnz:,}), Jacobi, s={a.s} monomial, "
+                                       "b=A x_true, x0=0, tol 1e-10, true-residual replacement every outer step",
+                           "parallelism": f"replicas x{world}"},
+                "mixed": {k: (round(v, 3) if k == "ms" else v) for k, v in m.items()},
+                "df64": {k: (round(v, 3) if k == "ms" else v) for k, v in out["df64"].items()},
+                "speedup_mixed_vs_df64": round(out["df64"]["ms"] / m["ms"], 3),
+                "cpu_baseline": {"value": round(t_oracle * 1e3, 1), "unit": "ms", "cores": oracle.num_threads(),
+                                 "kind": "oracle",
+                                 "sample": f"the whole solve: FP64 CPU oracle PCG to 1e-10, {ref.iters} iterations"}}
+        print(json.dumps(line), flush=True)
+    barrier(pg)
+
+
+CHEB_METRIC = "Chebyshev-basis s-step PCG with network vs Lanczos intervals: time to 1e-8 incl. the interval"
+
+
+def run_cheb(a, world, rank, local, pg):
+    """Variable-coefficient 7-point 128^3 fields with sigma in {0.5, 1, 2, 3}:
+    the Chebyshev-basis solve at s = 8 and 12 with its interval from the
+    trained spectral-bound network vs from 20 Lanczos steps (the library's
+    fallback), time including the interval; monomial s = 8 / 12 beside it.
+    The network is trained on the device first (seeded recipe)."""
+    import torch
+
+    from paper_2501_03743_gb300 import inputs
+
+    N = a.N if a.N != 256 else 128
+    if rank == 0:
+        from paper_2501_03743_gb300 import build
+
+        build.build()
+    barrier(pg)
+    torch.cuda.set_device(local)
+    from paper_2501_03743_gb300 import spectral, sscg
+
+    ctx = sscg.Context()
+    t0 = time.perf_counter()
+    samples = spectral.default_samples(seeds_per=6)
+    samples += [spectral.Sample("varcoef7", M, 3.0, ell, 700 + q)
+                for q, (M, ell) in enumerate([(32, 4.0), (48, 2.0), (64, 8.0), (96, 4.0), (128, 4.0), (80, 2.0)])]
+    X, T = spectral.dataset(ctx, samples)
+    net, hist = spectral.fit(ctx, X, T, hidden=64, epochs=4000, lr=3e-3, seed=0)
+    blob = net.blob()
+    t_train = time.perf_counter() - t0
+    rows = []
+    for q, sig in enumerate((0.5, 1.0, 2.0, 3.0)):
+        c = inputs.varcoef7(N, sig, 5000 + q)
+        A = sscg.Matrix(ctx, *c)
+        bt = torch.from_numpy(inputs.matvec(*c, inputs.uniform(91 + q, A.n))).cuda()
+        x = torch.zeros_like(bt)
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            out = fn()
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            return out, e0.elapsed_time(e1)
+
+        for s in (8, 12):
+            row = {"sigma": sig, "s": s}
+            for name in ("network", "lanczos", "monomial"):
+                if name == "network":
+                    A.set_bounds_model(net.h, blob)
+                else:
+                    A.set_bounds_model(net.h, None)
+                basis = "monomial" if name == "monomial" else "chebyshev"
+                solver = sscg.Solver(A, s=s, basis=basis, tol=1e-8, maxit=4000)
+
+                def go():
+                    x.zero_()
+                    return solver.solve(bt, x)
+
+                r, ms = timed(go)
+                row[name] = {"ms": round(ms, 3), "status": r.status, "outer": r.outer_iters,
+                             "rel_res_true": r.rel_res_true}
+            A.set_bounds_model(net.h, None)
+            (lo, hi), t_net = timed(lambda: net.bounds(A, blob))
+            (llo, lhi), t_lz = timed(lambda: A.estimate_bounds(20))
+            row["interval_ms"] = {"network": round(t_net, 3), "lanczos20": round(t_lz, 3)}
+            row["interval"] = {"network": [lo, hi], "lanczos20": [llo, lhi]}
+            rows.append(row)
+        A.close()
+    if rank == 0:
+        ok = [r for r in rows if r["network"]["status"] == 0 and r["lanczos"]["status"] == 0]
+        gain = [r["lanczos"]["ms"] / r["network"]["ms"] for r in ok]
+        line = {"metric": CHEB_METRIC, "value": round(statistics.median(gain), 3) if gain else None,
+                "unit": "x (Lanczos-interval time / network-interval time, median)", "n_gpus": world,
+                "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "df64", "data": "synthetic",
+                "config": {"workload": f"varcoef7 {N}^3, k = exp(sigma g), sigma in {{0.5,1,2,3}}, Jacobi, "
+                                       "Chebyshev basis s in {8,12}, tol 1e-8",
+                           "training": f"{len(samples)} seeded systems at 8^3..128^3, labels from device "
+                                       f"Lanczos, {len(hist)} Adam epochs, {t_train:.1f} s",
+                           "parallelism": f"replicas x{world}"},
+                "rows": rows}
         print(json.dumps(line), flush=True)
     barrier(pg)
 
