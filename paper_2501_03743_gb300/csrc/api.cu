@@ -226,6 +226,17 @@ int detect_dia(sscg_ctx* ctx, sscg_mat* m, uint32_t* mask, Analysis* an, int32_t
     m->dia_mask = mask;
     m->dia_d = d.c[diag_t];
     m->dia_dinv = 1.0 / d.c[diag_t];
+    m->dia_cen = diag_t;
+    m->dia_lap = 1;
+    m->dia_co = 0.0;
+    m->dia_reach = 0;
+    for (int t = 0; t < d.k; t++) {
+        m->dia_reach = std::max<int64_t>(m->dia_reach, std::abs((int64_t)d.off[t]));
+        if (t == diag_t) continue;
+        if (m->dia_co == 0.0) m->dia_co = d.c[t];
+        else if (d.c[t] != m->dia_co) m->dia_lap = 0;
+    }
+    if (m->dia_co == 0.0) m->dia_lap = 0;
     return SSCG_OK;
 }
 

@@ -115,6 +115,51 @@ __device__ __forceinline__ df64 df_from_double(double x) {
 
 __device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
 
+// Running double-float dot product in the cascaded form of Dot2 (Ogita, Rump
+// and Oishi, "Accurate sum and dot product", 2005): the high parts of the
+// products are added by TwoSum into s, every rounding error and the low-order
+// product terms into e.  dot_renorm folds e back into s (FastTwoSum); called
+// every couple of terms it keeps the accumulated error at the level of a
+// renormalised double-float sum while a term costs 12 FP32 operations instead
+// of 15.
+struct DotAcc {
+    float s, e;
+};
+
+__device__ __forceinline__ void dot_add(DotAcc& a, df64 x, df64 y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float q = __fmaf_rn(x.hi, y.hi, -p);
+    q = __fmaf_rn(x.hi, y.lo, q);
+    q = __fmaf_rn(x.lo, y.hi, q);
+    float s, t;
+    two_sum(a.s, p, s, t);
+    a.s = s;
+    a.e = __fadd_rn(a.e, __fadd_rn(t, q));
+}
+
+// a += y * y (the cross term 2 y.hi y.lo with the exact doubling of y.hi)
+__device__ __forceinline__ void dot_add_sq(DotAcc& a, df64 y) {
+    const float p = __fmul_rn(y.hi, y.hi);
+    float q = __fmaf_rn(y.hi, y.hi, -p);
+    q = __fmaf_rn(__fadd_rn(y.hi, y.hi), y.lo, q);
+    float s, t;
+    two_sum(a.s, p, s, t);
+    a.s = s;
+    a.e = __fadd_rn(a.e, __fadd_rn(t, q));
+}
+
+__device__ __forceinline__ void dot_renorm(DotAcc& a) {
+    float s, t;
+    fast_two_sum(a.s, a.e, s, t);
+    a.s = s;
+    a.e = t;
+}
+
+__device__ __forceinline__ df64 dot_value(DotAcc a) {
+    dot_renorm(a);
+    return df_make(a.s, a.e);
+}
+
 // ------------------------------------------------------- arithmetic traits
 //
 // R: register type.  S: storage type of vectors and basis blocks.

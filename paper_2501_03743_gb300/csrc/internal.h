@@ -54,6 +54,10 @@ struct sscg_mat {
     double dia_c[32];
     uint32_t* dia_mask;
     double dia_d, dia_dinv;  // the diagonal's value and its inverse
+    int dia_cen;             // index of offset 0 among the sorted offsets
+    int dia_lap;             // every off-centre value equals dia_co
+    double dia_co;
+    int64_t dia_reach;       // max |offset|
 };
 
 namespace sscg {
@@ -73,6 +77,25 @@ struct Carve {
     }
     bool ok() const { return used <= cap; }
 };
+
+// Margin (elements) carved before and after every vector that a
+// diagonal-form level gathers from, so its paired-row gathers need no clamps
+// (spmv_dia_df); 0 for a CSR matrix.
+inline size_t dia_margin(const sscg_mat* m) {
+    return m->dia ? align_up((size_t)m->dia_reach + 2, 32) : 0;
+}
+
+// Which diagonal-form SpMV a double-float kernel is built with: 0 CSR; 1
+// clamped (vectors without margins); 7 / 27 the Laplacian class (all
+// off-centre values equal, offset 0 in the middle) with that many offsets;
+// 2 any other diagonal form over margined vectors.
+inline int dia_mode(const sscg_mat* m, bool margins) {
+    if (!m->dia) return 0;
+    if (!margins) return 1;
+    if (m->dia_lap && m->dia_k == 7 && m->dia_cen == 3) return 7;
+    if (m->dia_lap && m->dia_k == 27 && m->dia_cen == 13) return 27;
+    return 2;
+}
 
 inline int set_err(sscg_ctx* ctx, int code, const char* fmt, ...) {
     if (ctx) {

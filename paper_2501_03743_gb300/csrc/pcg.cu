@@ -99,8 +99,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(MatView M, const typename
     }
 }
 
-template <class A, int VM, bool DIA>
-__global__ void __launch_bounds__(kThreads) k_pcg_spmv(MatView M, const typename A::S* __restrict__ p,
+template <class A, int VM, int DM>
+__global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1) k_pcg_spmv(MatView M, const typename A::S* __restrict__ p,
                                                        typename A::S* __restrict__ q, double* __restrict__ part,
                                                        Ctrl* ctrl) {
     using R = typename A::R;
@@ -115,8 +115,21 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv(MatView M, const typename
         pq = A::fma(A::ldg(p + row), y, pq);
     };
     bool ok = true;
-    if constexpr (DIA) spmv_dia<A>(M, xf, epi);
-    else ok = spmv_pipe<A, VM, kStages>(M, smem, xf, epi, ctrl);
+    if constexpr (DM != 0 && A::kind == 1) {
+        DotAcc d{0.f, 0.f};
+        spmv_dia_df<DM>(
+            M, p,
+            [&](int row, df64 y, df64 xc) {
+                A::st(q + row, y);
+                dot_add(d, xc, y);
+            },
+            [&] { dot_renorm(d); });
+        pq = dot_value(d);
+    } else if constexpr (DM != 0) {
+        spmv_dia<A>(M, xf, epi);
+    } else {
+        ok = spmv_pipe<A, VM, kStages>(M, smem, xf, epi, ctrl);
+    }
     if (!ok) return;
     R v[1] = {pq};
     double out[1];
@@ -369,7 +382,11 @@ PLayout pplan(const sscg_mat* mat, int maxit, unsigned flags, void* base, size_t
     L.coef = c.take<double>(2 * ((size_t)maxit + 2));
     L.x = c.take<double>(ldn);
     L.r = c.take<double>(ldn);
+    // margins around p: the diagonal-form SpMV gathers it without clamping
+    const size_t g = dia_margin(mat);
+    if (g) c.take<double>(g);
     L.p = c.take<double>(ldn);
+    if (g) c.take<double>(g);
     L.q = c.take<double>(ldn);
     if (mat->prec == SSCG_PREC_CHEB) {
         L.u = c.take<double>(ldn);
@@ -398,15 +415,19 @@ MatView view(const sscg_mat* mat) {
         M.doff[t] = t < M.dk ? mat->dia_off[t] : 0;
         M.dc[t] = t < M.dk ? mat->dia_c[t] : 0.0;
     }
+    M.dcen = mat->dia_cen;
+    M.dlap = mat->dia_lap;
+    M.dco = (float)mat->dia_co;
     return M;
 }
 
 // One PCG run.  x may be null (zero start and no export; the Lanczos
 // estimate); coef receives alpha_j, beta_j when not null.
-template <class A, int VM, bool DIA>
+template <class A, int VM, int DM>
 int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int maxit, const PLayout& L,
             const typename A::S* dinv, Ctrl* h, Prof& P, double* coef) {
     using S = typename A::S;
+    constexpr bool DIA = DM != 0;
     cudaStream_t st = ctx->stream;
     const int n = (int)mat->n;
     const MatView M = view(mat);
@@ -414,12 +435,12 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int 
     const size_t smem_pipe = pipe_bytes<VM, kStages>(M.cap) + 128;
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const size_t smem_sp = DIA ? 128 : smem_pipe;
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_spmv<A, VM, DIA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_spmv<A, VM, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem_sp));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_cheb_step<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pipe));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_true_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
     const int Gi = occupancy_grid(ctx, k_pcg_init<A, VM>, smem, n);
-    const int Gs = occupancy_grid(ctx, k_pcg_spmv<A, VM, DIA>, smem_sp, n);
+    const int Gs = occupancy_grid(ctx, k_pcg_spmv<A, VM, DM>, smem_sp, n);
     const int Gc = occupancy_grid(ctx, k_cheb_step<A, VM>, smem_pipe, n);
     const int Gu = occupancy_grid(ctx, k_pcg_update<A>, 0, n);
     const int Gd = occupancy_grid(ctx, k_pcg_dir<A>, 0, n);
@@ -459,7 +480,7 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int 
         for (int k = 0; k < c; k++) {
             const int it = launched + k;
             P.begin();
-            k_pcg_spmv<A, VM, DIA><<<Gs, kThreads, smem_sp, st>>>(M, p, q, L.part, L.ctrl);
+            k_pcg_spmv<A, VM, DM><<<Gs, kThreads, smem_sp, st>>>(M, p, q, L.part, L.ctrl);
             P.end(FAM_MPK, it);
             P.begin();
             k_pcg_update<A><<<Gu, kThreads, 0, st>>>(n, diag ? 1 : 0, xw, r, p, q, dinv_it, dinv_c, L.part, L.ctrl,
@@ -512,13 +533,17 @@ int dispatch_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x,
     // Chebyshev preconditioner's steps stage CSR tiles)
     const bool dia = mat->dia && mat->prec != SSCG_PREC_CHEB;
     if (arith == SSCG_ARITH_F64) {
-        if (dia) return run_pcg<ArithF64, VAL_F64, true>(ctx, mat, b, x, maxit, L, scale ? mat->dinv : nullptr, h, P, coef);
-        return run_pcg<ArithF64, VAL_F64, false>(ctx, mat, b, x, maxit, L, scale ? mat->dinv : nullptr, h, P, coef);
+        if (dia) return run_pcg<ArithF64, VAL_F64, 1>(ctx, mat, b, x, maxit, L, scale ? mat->dinv : nullptr, h, P, coef);
+        return run_pcg<ArithF64, VAL_F64, 0>(ctx, mat, b, x, maxit, L, scale ? mat->dinv : nullptr, h, P, coef);
     }
-    if (dia) return run_pcg<ArithDF64, VAL_F32, true>(ctx, mat, b, x, maxit, L, scale ? mat->dinv_df : nullptr, h, P, coef);
-    if (mat->exact_fp32)
-        return run_pcg<ArithDF64, VAL_F32, false>(ctx, mat, b, x, maxit, L, scale ? mat->dinv_df : nullptr, h, P, coef);
-    return run_pcg<ArithDF64, VAL_DF, false>(ctx, mat, b, x, maxit, L, scale ? mat->dinv_df : nullptr, h, P, coef);
+    const float2* d = scale ? mat->dinv_df : nullptr;
+    // every PCG layout carves margins around p, the only vector the SpMV gathers
+    const int dm = dia ? dia_mode(mat, true) : 0;
+    if (dm == 7) return run_pcg<ArithDF64, VAL_F32, 7>(ctx, mat, b, x, maxit, L, d, h, P, coef);
+    if (dm == 27) return run_pcg<ArithDF64, VAL_F32, 27>(ctx, mat, b, x, maxit, L, d, h, P, coef);
+    if (dm != 0) return run_pcg<ArithDF64, VAL_F32, 2>(ctx, mat, b, x, maxit, L, d, h, P, coef);
+    if (mat->exact_fp32) return run_pcg<ArithDF64, VAL_F32, 0>(ctx, mat, b, x, maxit, L, d, h, P, coef);
+    return run_pcg<ArithDF64, VAL_DF, 0>(ctx, mat, b, x, maxit, L, d, h, P, coef);
 }
 
 Ctrl fresh_ctrl(int maxit, double tol) {

@@ -30,6 +30,9 @@ struct MatView {
     int dk;
     int doff[kDiaMax];
     double dc[kDiaMax];
+    int dcen;   // index of offset 0
+    int dlap;   // every off-centre coefficient equals dco
+    float dco;  // that coefficient
 };
 
 template <class A, int VM>
@@ -230,6 +233,111 @@ __device__ __forceinline__ void spmv_dia(const MatView& M, XF xf, EPI epi) {
     __syncthreads();
     if (M.dk <= 8) spmv_dia_rows<A, 8>(M, s_off, s_c, s_cf, xf, epi);
     else spmv_dia_rows<A, kDiaMax>(M, s_off, s_c, s_cf, xf, epi);
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal form in double-float, two rows per thread, over a guarded vector.
+//
+// x must be readable at every index in [-g, n + g) for g > max |offset| + 1;
+// the solvers carve such margins around the vectors their levels gather
+// from.  A thread takes rows i and i + 1 (i even), so a warp covers 64
+// consecutive rows and each offset's two gathers share one address; no index
+// is clamped.  A term whose mask bit is clear is replaced by zero before it
+// enters the sum, so whatever the margins (or a neighbouring column) hold
+// never reaches a result.  epi(row, y, x_row) receives y = (A x)_row and
+// x_row; tick() runs once per row pair (the callers renormalise their running
+// sums there).
+//
+// Laplacian class (dlap: every off-centre coefficient is dco): the masked
+// neighbours are first summed as double-float values (TwoSum of the high
+// parts, the low parts and the errors gathered in a second float: 8 FP32
+// operations a term), then y = c_centre x_i + dco * sum by one Dot2 step.
+// The general case takes each term as a Dot2 step (dot2_add).
+template <int K, class EPI, class TICK>
+__device__ __forceinline__ void spmv_dia_lap(const MatView& M, const float2* __restrict__ x, EPI epi, TICK tick) {
+    constexpr int C = K / 2;  // symmetric pattern: offset 0 sits in the middle
+    const float cc = (float)M.dc[C], co = M.dco;
+    const int n = M.n;
+    const int stride = 2 * gridDim.x * blockDim.x;
+    for (int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x); i < n; i += stride) {
+        const uint2 mm = __ldg(reinterpret_cast<const uint2*>(M.dmask + i));
+        float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f;
+#pragma unroll
+        for (int t = 0; t < K; t++) {
+            if (t == C) continue;
+            const float2* a = x + (i + M.doff[t]);
+            const float2 v0 = __ldg(a), v1 = __ldg(a + 1);
+            const bool b0 = (mm.x >> t) & 1u, b1 = (mm.y >> t) & 1u;
+            float u, w;
+            two_sum(s0, b0 ? v0.x : 0.f, u, w);
+            s0 = u;
+            e0 = __fadd_rn(e0, __fadd_rn(w, b0 ? v0.y : 0.f));
+            two_sum(s1, b1 ? v1.x : 0.f, u, w);
+            s1 = u;
+            e1 = __fadd_rn(e1, __fadd_rn(w, b1 ? v1.y : 0.f));
+        }
+        const float2 c0 = __ldg(x + i), c1 = __ldg(x + i + 1);
+        const df64 xc0 = df_make(c0.x, c0.y), xc1 = df_make(c1.x, c1.y);
+        // co * (s + e): its high part exactly as p + fma residue, e scaled into the error float
+        float p = __fmul_rn(co, s0);
+        Dot2Acc a0{p, __fmaf_rn(co, e0, __fmaf_rn(co, s0, -p))};
+        p = __fmul_rn(co, s1);
+        Dot2Acc a1{p, __fmaf_rn(co, e1, __fmaf_rn(co, s1, -p))};
+        dot2_add(a0, cc, xc0);
+        dot2_add(a1, cc, xc1);
+        epi(i, dot2_result(a0), xc0);
+        if (i + 1 < n) epi(i + 1, dot2_result(a1), xc1);
+        tick();
+    }
+}
+
+template <class EPI, class TICK>
+__device__ __forceinline__ void spmv_dia_gen(const MatView& M, const float2* __restrict__ x, const int* s_off,
+                                             const float* s_cf, EPI epi, TICK tick) {
+    const int n = M.n, K = M.dk;
+    const int stride = 2 * gridDim.x * blockDim.x;
+    for (int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x); i < n; i += stride) {
+        const uint2 mm = __ldg(reinterpret_cast<const uint2*>(M.dmask + i));
+        Dot2Acc a0{0.f, 0.f}, a1{0.f, 0.f};
+        for (int t = 0; t < K; t++) {
+            const float2* a = x + (i + s_off[t]);
+            const float2 v0 = __ldg(a), v1 = __ldg(a + 1);
+            const bool b0 = (mm.x >> t) & 1u, b1 = (mm.y >> t) & 1u;
+            dot2_add(a0, s_cf[t], b0 ? df_make(v0.x, v0.y) : df_make(0.f, 0.f));
+            dot2_add(a1, s_cf[t], b1 ? df_make(v1.x, v1.y) : df_make(0.f, 0.f));
+        }
+        const float2 c0 = __ldg(x + i), c1 = __ldg(x + i + 1);
+        epi(i, dot2_result(a0), df_make(c0.x, c0.y));
+        if (i + 1 < n) epi(i + 1, dot2_result(a1), df_make(c1.x, c1.y));
+        tick();
+    }
+}
+
+// Diagonal-form kernels are built per mode DM (dia_mode() on the host):
+// 7 / 27 the Laplacian class with that many offsets, 2 any other diagonal
+// form over margined vectors, 1 no margins (clamped, one row per thread).
+// Every thread must call it.
+template <int DM, class EPI, class TICK>
+__device__ __forceinline__ void spmv_dia_df(const MatView& M, const float2* __restrict__ x, EPI epi, TICK tick) {
+    if constexpr (DM == 7 || DM == 27) {
+        spmv_dia_lap<DM>(M, x, epi, tick);
+    } else if constexpr (DM == 2) {
+        __shared__ int s_off[kDiaMax];
+        __shared__ float s_cf[kDiaMax];
+        for (int t = threadIdx.x; t < kDiaMax; t += blockDim.x) {
+            s_off[t] = t < M.dk ? M.doff[t] : 0;
+            s_cf[t] = t < M.dk ? (float)M.dc[t] : 0.f;
+        }
+        __syncthreads();
+        spmv_dia_gen(M, x, s_off, s_cf, epi, tick);
+    } else {
+        spmv_dia<ArithDF64>(
+            M, [&](int c) { return ArithDF64::ldg(x + c); },
+            [&](int row, df64 y) {
+                epi(row, y, ArithDF64::ldg(x + row));
+                tick();
+            });
+    }
 }
 
 // ---------------------------------------------------------------------------

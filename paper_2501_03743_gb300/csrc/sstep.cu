@@ -30,11 +30,12 @@ namespace {
 // One level of the matrix-powers kernel (Algorithm 4): y = A u_j, written to
 // AU_j when au_out != null; u_{j+1} = B^-1 y (when u_next != null; B^-1 the
 // array dinv, or the constant dinv_c when dinv is null and dinv_c != 0, or
-// none); the matrix in CSR tiles or, with DIA, its diagonal form; moment partials
+// none); the matrix in CSR tiles or, with DM != 0, its diagonal form (mode DM of
+// spmv_dia_df for double-float); moment partials
 // mu_{2j+1} = u_j . y and mu_{2j+2} = y . B^-1 y.  With `last` set, the last
 // CTA reduces mu_1..mu_{2s-1} and runs Algorithm 6.
-template <class A, int VM, bool DIA>
-__global__ void __launch_bounds__(kThreads) k_level(MatView M, const typename A::S* __restrict__ dinv,
+template <class A, int VM, int DM>
+__global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1) k_level(MatView M, const typename A::S* __restrict__ dinv,
                                                     double dinv_c, const typename A::S* __restrict__ u_in,
                                                     typename A::S* __restrict__ au_out,
                                                     typename A::S* __restrict__ u_next, double* __restrict__ part,
@@ -58,8 +59,33 @@ __global__ void __launch_bounds__(kThreads) k_level(MatView M, const typename A:
         }
     };
     bool ok = true;
-    if constexpr (DIA) spmv_dia<A>(M, xf, epi);
-    else ok = spmv_pipe<A, VM, kStages>(M, smem, xf, epi, ctrl);
+    if constexpr (DM != 0 && A::kind == 1) {
+        // paired rows; moments as running Dot2 sums, renormalised once per pair
+        DotAcc d1{0.f, 0.f}, d2{0.f, 0.f};
+        spmv_dia_df<DM>(
+            M, u_in,
+            [&](int row, df64 y, df64 xc) {
+                if (au_out) A::st(au_out + row, y);
+                dot_add(d1, xc, y);
+                if (u_next || want_m2) {
+                    const df64 z = dinv ? df_mul(A::ld(dinv + row), y) : (dinv_c != 0.0 ? df_mul(dc, y) : y);
+                    if (u_next) A::st(u_next + row, z);
+                    if (dinv) dot_add(d2, y, z);
+                    else dot_add_sq(d2, y);  // y . D^-1 y = dinv_c * (y . y), scaled below
+                }
+            },
+            [&] {
+                dot_renorm(d1);
+                dot_renorm(d2);
+            });
+        m1 = dot_value(d1);
+        m2 = dot_value(d2);
+        if (!dinv && dinv_c != 0.0) m2 = df_mul(dc, m2);
+    } else if constexpr (DM != 0) {
+        spmv_dia<A>(M, xf, epi);
+    } else {
+        ok = spmv_pipe<A, VM, kStages>(M, smem, xf, epi, ctrl);
+    }
     if (!ok) return;
     R v[2] = {m1, m2};
     double out[2];
@@ -361,8 +387,14 @@ Layout plan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t c
     L.hist = c.take<double>((size_t)o->maxit + 2);
     L.part = c.take<double>((size_t)G * (2 * kMaxS + 4));
     size_t blk = (size_t)L.ldn * (2 * o->s + 1);
+    // margins around the blocks: the diagonal-form levels gather columns
+    // 0..s-1 at indices down to -max|offset| without clamping
+    const size_t g = dia_margin(mat);
+    if (g) c.take<double>(g);
     L.blk[0] = c.take<double>(blk);
+    if (g) c.take<double>(g);
     L.blk[1] = c.take<double>(blk);
+    if (g) c.take<double>(g);
     L.r = c.take<double>((size_t)L.ldn);
     L.flags = c.take<unsigned>((size_t)kMaxFuse * ((mat->n + kTileRows - 1) / kTileRows));
     L.xw = (o->arith == SSCG_ARITH_F64) ? nullptr : c.take<double>((size_t)L.ldn);
@@ -389,14 +421,18 @@ MatView view_of(const sscg_mat* m, int cap) {
         v.doff[t] = t < v.dk ? m->dia_off[t] : 0;
         v.dc[t] = t < v.dk ? m->dia_c[t] : 0.0;
     }
+    v.dcen = m->dia_cen;
+    v.dlap = m->dia_lap;
+    v.dco = (float)m->dia_co;
     return v;
 }
 
 
-template <class A, int VM, int SB, bool DIA>
+template <class A, int VM, int SB, int DM>
 int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o,
               const Layout& L, const typename A::S* dinv, const typename A::S* diag, Ctrl* hctrl, Prof& P) {
     using S = typename A::S;
+    constexpr bool DIA = DM != 0;
     cudaStream_t st = ctx->stream;
     const int n = (int)mat->n, s = o->s, G = L.G;
     const int cap = stage_cap(mat);
@@ -407,7 +443,7 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // the diagonal form stages nothing; the last level's solves still use the scratch
     const size_t smem_lv = DIA ? sizeof(SmallScratch) + 128 : smem_pipe;
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_level<A, VM, DIA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_level<A, VM, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem_lv));
     // with the diagonal form and Jacobi, D is the constant diagonal value
     const bool cd = DIA && dinv != nullptr;
@@ -425,7 +461,7 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
 
     P.begin();
     const int Gi = occupancy_grid(ctx, k_init<A, VM>, smem, n);
-    const int Gl = occupancy_grid(ctx, k_level<A, VM, DIA>, smem_lv, n);
+    const int Gl = occupancy_grid(ctx, k_level<A, VM, DM>, smem_lv, n);
     int per_sm = 0;
     SSCG_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mpk_fused<A, VM>, kFuseThreads,
                                                                  smem_fused));
@@ -471,7 +507,7 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
                 // u_{j+1} = D^-1 A u_j into column j+1 (all j, u_{s+1} too); A u_j is not stored
                 for (int j = 0; j < s; j++) {
                     P.begin();
-                    k_level<A, VM, DIA><<<Gl, kThreads, smem_lv, st>>>(M, dinv_l, dinv_c, bn + j * ld, nullptr,
+                    k_level<A, VM, DM><<<Gl, kThreads, smem_lv, st>>>(M, dinv_l, dinv_c, bn + j * ld, nullptr,
                                                                      bn + (j + 1) * ld, L.part, j, s, k, j == s - 1,
                                                                      L.ctrl);
                     P.end(FAM_MPK, k);
@@ -511,6 +547,15 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     SSCG_CUDA(ctx, cudaMemcpyAsync(hctrl, L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     SSCG_CUDA(ctx, cudaStreamSynchronize(st));
     return 0;
+}
+
+// The update kernels are built for block sizes up to 4, 8 and 16.
+template <class A, int VM, int DM>
+int run_sstep_sb(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o,
+                 const Layout& L, const typename A::S* dinv, const typename A::S* diag, Ctrl* hctrl, Prof& P) {
+    if (o->s <= 4) return run_sstep<A, VM, 4, DM>(ctx, mat, b, x, o, L, dinv, diag, hctrl, P);
+    if (o->s <= 8) return run_sstep<A, VM, 8, DM>(ctx, mat, b, x, o, L, dinv, diag, hctrl, P);
+    return run_sstep<A, VM, 16, DM>(ctx, mat, b, x, o, L, dinv, diag, hctrl, P);
 }
 
 }  // namespace
@@ -577,29 +622,18 @@ int solve_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, 
     if (o->arith == SSCG_ARITH_F64) {
         const double* dinv = jac ? mat->dinv : nullptr;
         const double* diag = jac ? mat->diag : nullptr;
-        if (dia) {
-            if (s <= 4) rc = run_sstep<ArithF64, VAL_F64, 4, true>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-            else if (s <= 8) rc = run_sstep<ArithF64, VAL_F64, 8, true>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-            else rc = run_sstep<ArithF64, VAL_F64, 16, true>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-        } else if (s <= 4) rc = run_sstep<ArithF64, VAL_F64, 4, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-        else if (s <= 8) rc = run_sstep<ArithF64, VAL_F64, 8, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-        else rc = run_sstep<ArithF64, VAL_F64, 16, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        if (dia) rc = run_sstep_sb<ArithF64, VAL_F64, 1>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        else rc = run_sstep_sb<ArithF64, VAL_F64, 0>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
     } else {
         const float2* dinv = jac ? mat->dinv_df : nullptr;
         const float2* diag = jac ? mat->diag_df : nullptr;
-        if (dia) {
-            if (s <= 4) rc = run_sstep<ArithDF64, VAL_F32, 4, true>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-            else if (s <= 8) rc = run_sstep<ArithDF64, VAL_F32, 8, true>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-            else rc = run_sstep<ArithDF64, VAL_F32, 16, true>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-        } else if (mat->exact_fp32) {
-            if (s <= 4) rc = run_sstep<ArithDF64, VAL_F32, 4, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-            else if (s <= 8) rc = run_sstep<ArithDF64, VAL_F32, 8, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-            else rc = run_sstep<ArithDF64, VAL_F32, 16, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-        } else {
-            if (s <= 4) rc = run_sstep<ArithDF64, VAL_DF, 4, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-            else if (s <= 8) rc = run_sstep<ArithDF64, VAL_DF, 8, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-            else rc = run_sstep<ArithDF64, VAL_DF, 16, false>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
-        }
+        // plan() carves margins around both blocks whenever the matrix has the diagonal form
+        const int dm = dia ? dia_mode(mat, true) : 0;
+        if (dm == 7) rc = run_sstep_sb<ArithDF64, VAL_F32, 7>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        else if (dm == 27) rc = run_sstep_sb<ArithDF64, VAL_F32, 27>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        else if (dm != 0) rc = run_sstep_sb<ArithDF64, VAL_F32, 2>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        else if (mat->exact_fp32) rc = run_sstep_sb<ArithDF64, VAL_F32, 0>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        else rc = run_sstep_sb<ArithDF64, VAL_DF, 0>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
     }
     if (rc) {
         delete prof;
