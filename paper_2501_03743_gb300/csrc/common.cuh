@@ -155,6 +155,12 @@ __device__ __forceinline__ void dot_renorm(DotAcc& a) {
     a.e = t;
 }
 
+// Two consecutive double-float elements p[0], p[1] in one 16-byte store
+// (p 16-byte aligned).
+__device__ __forceinline__ void st_pair(float2* p, df64 a, df64 b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
 __device__ __forceinline__ df64 dot_value(DotAcc a) {
     dot_renorm(a);
     return df_make(a.s, a.e);

@@ -29,28 +29,55 @@ __device__ __forceinline__ typename A::R basis_next(const Basis& B, int j, typen
     return A::sub(A::mul(t, A::from_d(2.0 / B.delta)), A::ld(ujm1 + row));
 }
 
-// AU_j = A u_j; with a diagonal preconditioner also u_{j+1}.
-template <class A, int VM>
-__global__ void __launch_bounds__(kThreads) k_level_gen(MatView M, const typename A::S* __restrict__ dinv,
-                                                        const typename A::S* __restrict__ u_in,
-                                                        const typename A::S* __restrict__ u_prev,
-                                                        typename A::S* __restrict__ au_out,
-                                                        typename A::S* __restrict__ u_next, int j, Basis B,
-                                                        int diag_prec, const Ctrl* ctrl) {
+// AU_j = A u_j; with a diagonal preconditioner also u_{j+1}.  The matrix in
+// CSR tiles or, with DM != 0 (double-float only), its diagonal form (mode DM
+// of spmv_dia_df); there B^-1 is the constant dinv_c (Jacobi) or the identity
+// (dinv_c = 0), and the vectors gathered carry margins.
+template <class A, int VM, int DM = 0>
+__global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1)
+    k_level_gen(MatView M, const typename A::S* __restrict__ dinv, double dinv_c,
+                const typename A::S* __restrict__ u_in, const typename A::S* __restrict__ u_prev,
+                typename A::S* __restrict__ au_out, typename A::S* __restrict__ u_next, int j, Basis B,
+                int diag_prec, const Ctrl* ctrl) {
     using R = typename A::R;
     if (ctrl_done(ctrl)) return;
-    extern __shared__ __align__(16) char smem_raw[];
-    char* smem = align128(smem_raw);
-    spmv_pipe<A, VM, kStages>(
-        M, smem, [&](int c) { return A::ldg(u_in + c); },
-        [&](int row, R y) {
-            A::st(au_out + row, y);
-            if (u_next && diag_prec) {
-                R w = dinv ? A::mul(A::ld(dinv + row), y) : y;
-                A::st(u_next + row, basis_next<A>(B, j, w, u_in, u_prev, row));
+    if constexpr (DM != 0 && A::kind == 1) {
+        const df64 dcv = dinv_c != 0.0 ? df_from_double(dinv_c) : df_make(1.f, 0.f);
+        const df64 cb = df_from_double(B.c);
+        const df64 sc = df_from_double(B.cheb ? (j == 0 ? 1.0 : 2.0) / B.delta : 1.0);
+        const bool nxt = u_next && diag_prec;
+        spmv_dia_df<DM>(M, u_in, [&](int i, df64 y0, df64 x0, df64 y1, df64 x1, bool has1) {
+            if (has1) st_pair(au_out + i, y0, y1);
+            else A::st(au_out + i, y0);
+            if (!nxt) return;
+            df64 w0 = df_mul(dcv, y0), w1 = df_mul(dcv, y1);
+            if (B.cheb) {  // Chebyshev recurrence on w = B^-1 A u_j
+                w0 = df_mul(df_add(w0, df_neg(df_mul(cb, x0))), sc);
+                w1 = df_mul(df_add(w1, df_neg(df_mul(cb, x1))), sc);
+                if (j > 0) {
+                    df64 p0, p1;
+                    DiaVec<float2>::ld_pair(u_prev + i, p0, p1);
+                    w0 = df_add(w0, df_neg(p0));
+                    w1 = df_add(w1, df_neg(p1));
+                }
             }
-        },
-        const_cast<Ctrl*>(ctrl));
+            if (has1) st_pair(u_next + i, w0, w1);
+            else A::st(u_next + i, w0);
+        });
+    } else {
+        extern __shared__ __align__(16) char smem_raw[];
+        char* smem = align128(smem_raw);
+        spmv_pipe<A, VM, kStages>(
+            M, smem, [&](int c) { return A::ldg(u_in + c); },
+            [&](int row, R y) {
+                A::st(au_out + row, y);
+                if (u_next && diag_prec) {
+                    R w = dinv ? A::mul(A::ld(dinv + row), y) : y;
+                    A::st(u_next + row, basis_next<A>(B, j, w, u_in, u_prev, row));
+                }
+            },
+            const_cast<Ctrl*>(ctrl));
+    }
 }
 
 // u_{j+1} from w = B^-1 A u_j (general preconditioner).

@@ -39,13 +39,39 @@ __global__ void k_mx_prep(int n, const float2* __restrict__ r, float2* __restric
 }
 
 // AU_j = A u_j in double-float from the FP32 u_j; u_{j+1} from B^-1 AU_j by
-// the basis recurrence, rounded to FP32.
-template <int VM>
-__global__ void __launch_bounds__(kThreads) k_mx_level(MatView M, const float2* __restrict__ dinv_df,
-                                                       const float* __restrict__ u_in,
-                                                       const float* __restrict__ u_prev, float2* __restrict__ au_out,
-                                                       float* __restrict__ u_next, int j, Basis B, Ctrl* ctrl) {
+// the basis recurrence, rounded to FP32.  With DM != 0 the matrix's diagonal
+// form (mode DM of spmv_dia_df; B^-1 the constant dinv_c or the identity, the
+// FP32 basis columns carry margins).
+template <int VM, int DM = 0>
+__global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1)
+    k_mx_level(MatView M, const float2* __restrict__ dinv_df, double dinv_c, const float* __restrict__ u_in,
+               const float* __restrict__ u_prev, float2* __restrict__ au_out, float* __restrict__ u_next, int j,
+               Basis B, Ctrl* ctrl) {
     if (__ldcg(&ctrl->done)) return;
+    if constexpr (DM != 0) {
+        const df64 dcv = dinv_c != 0.0 ? df_from_double(dinv_c) : df_make(1.f, 0.f);
+        const df64 cb = df_from_double(B.c);
+        const df64 sc = df_from_double(B.cheb ? (j == 0 ? 1.0 : 2.0) / B.delta : 1.0);
+        spmv_dia_df<DM>(M, u_in, [&](int i, df64 y0, df64 x0, df64 y1, df64 x1, bool has1) {
+            if (has1) st_pair(au_out + i, y0, y1);
+            else au_out[i] = make_float2(y0.hi, y0.lo);
+            if (!u_next) return;
+            df64 w0 = df_mul(dcv, y0), w1 = df_mul(dcv, y1);
+            if (B.cheb) {
+                w0 = df_mul(df_add(w0, df_neg(df_mul(cb, x0))), sc);
+                w1 = df_mul(df_add(w1, df_neg(df_mul(cb, x1))), sc);
+                if (j > 0) {
+                    df64 p0, p1;
+                    DiaVec<float>::ld_pair(u_prev + i, p0, p1);
+                    w0 = df_add(w0, df_neg(p0));
+                    w1 = df_add(w1, df_neg(p1));
+                }
+            }
+            if (has1) *reinterpret_cast<float2*>(u_next + i) = make_float2(w0.hi, w1.hi);
+            else u_next[i] = w0.hi;
+        });
+        return;
+    }
     extern __shared__ __align__(16) char smem_raw[];
     char* smem = align128(smem_raw);
     spmv_pipe<ArithDF64, VM, kStages>(
@@ -160,28 +186,52 @@ __global__ void __launch_bounds__(kThreads) k_mx_update(int n, int ldn, int s, f
 }
 
 // Residual replacement: r = r0 - A (x - x0) in double-float, u_1 = B^-1 r
-// in FP32; the stop test on this true residual.
-template <int VM>
+// in FP32; the stop test on this true residual.  DM as in k_mx_level (x - x0
+// carries margins; B^-1 is then the constant dinv_c or the identity).
+template <int VM, int DM = 0>
 __global__ void __launch_bounds__(kThreads) k_mx_replace(MatView M, const float2* __restrict__ xw,
                                                          const float2* __restrict__ r0, float2* __restrict__ r,
-                                                         const float* __restrict__ dinv_f, float* __restrict__ u0,
-                                                         double* __restrict__ part, Ctrl* ctrl,
-                                                         double* __restrict__ hist) {
+                                                         const float* __restrict__ dinv_f, double dinv_c,
+                                                         float* __restrict__ u0, double* __restrict__ part,
+                                                         Ctrl* ctrl, double* __restrict__ hist) {
     if (__ldcg(&ctrl->done)) return;
     extern __shared__ __align__(16) char smem_raw[];
     char* smem = align128(smem_raw);
     __shared__ double red[kThreads / 32];
     df64 rr = df_make(0.f, 0.f);
-    const bool ok = spmv_pipe<ArithDF64, VM, kStages>(
-        M, smem, [&](int c) { return ArithDF64::ldg(xw + c); },
-        [&](int row, df64 y) {
-            float2 a = r0[row];
-            df64 rn = df_add(df_make(a.x, a.y), df_neg(y));
-            r[row] = make_float2(rn.hi, rn.lo);
-            u0[row] = dinv_f ? dinv_f[row] * rn.hi : rn.hi;
-            rr = df_fma(rn, rn, rr);
-        },
-        ctrl);
+    bool ok = true;
+    if constexpr (DM != 0) {
+        const float dcf = dinv_c != 0.0 ? (float)dinv_c : 1.f;  // 1/d rounded to FP32, as dinv_f holds it
+        DotAcc acc{0.f, 0.f};
+        spmv_dia_df<DM>(M, xw, [&](int i, df64 y0, df64, df64 y1, df64, bool has1) {
+            df64 a0, a1;
+            DiaVec<float2>::ld_pair(r0 + i, a0, a1);
+            const df64 rn0 = df_add(a0, df_neg(y0));
+            const df64 rn1 = has1 ? df_add(a1, df_neg(y1)) : df_make(0.f, 0.f);
+            if (has1) {
+                st_pair(r + i, rn0, rn1);
+                *reinterpret_cast<float2*>(u0 + i) = make_float2(dcf * rn0.hi, dcf * rn1.hi);
+            } else {
+                r[i] = make_float2(rn0.hi, rn0.lo);
+                u0[i] = dcf * rn0.hi;
+            }
+            dot_add_sq(acc, rn0);
+            dot_add_sq(acc, rn1);
+            dot_renorm(acc);
+        });
+        rr = dot_value(acc);
+    } else {
+        ok = spmv_pipe<ArithDF64, VM, kStages>(
+            M, smem, [&](int c) { return ArithDF64::ldg(xw + c); },
+            [&](int row, df64 y) {
+                float2 a = r0[row];
+                df64 rn = df_add(df_make(a.x, a.y), df_neg(y));
+                r[row] = make_float2(rn.hi, rn.lo);
+                u0[row] = dinv_f ? dinv_f[row] * rn.hi : rn.hi;
+                rr = df_fma(rn, rn, rr);
+            },
+            ctrl);
+    }
     if (!ok) return;
     df64 v[1] = {rr};
     double out[1];
@@ -216,13 +266,20 @@ MLayout mplan(const sscg_mat* mat, const sscg_opts* o, void* base, size_t cap) {
     L.ctrl = c.take<Ctrl>(1);
     L.hist = c.take<double>((size_t)o->maxit + 2);
     L.part = c.take<double>((size_t)kMaxGrid * (o->s * (o->s + 1) / 2 + 2 * o->s + o->s * o->s + 4));
+    // margins: the diagonal-form levels gather U and the replacement gathers
+    // x - x0 without clamping
+    const size_t g = dia_margin(mat);
+    if (g) c.take<float>(g);
     L.ublk = c.take<float>((size_t)L.ldn * o->s);
+    if (g) c.take<float>(g);
     L.aublk = c.take<float2>((size_t)L.ldn * o->s);
     L.pblk[0] = c.take<float2>((size_t)L.ldn * 2 * o->s);
     L.pblk[1] = c.take<float2>((size_t)L.ldn * 2 * o->s);
     L.r = c.take<float2>((size_t)L.ldn);
     L.r0 = c.take<float2>((size_t)L.ldn);
+    if (g) c.take<float2>(g);
     L.xw = c.take<float2>((size_t)L.ldn);
+    if (g) c.take<float2>(g);
     if (o->flags & SSCG_HOST_VECTORS) {
         L.bdev = c.take<double>((size_t)L.ldn);
         L.xdev = c.take<double>((size_t)L.ldn);
@@ -231,43 +288,37 @@ MLayout mplan(const sscg_mat* mat, const sscg_opts* o, void* base, size_t cap) {
     return L;
 }
 
-template <int VM, int SB>
+template <int VM, int SB, int DM>
 int run_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o, const MLayout& L,
               Basis basis, Ctrl* hctrl, Prof& P) {
     cudaStream_t st = ctx->stream;
     const int n = (int)mat->n, s = o->s;
     const int cap = stage_cap(mat);
-    MatView M{};
-    M.n = n;
-    M.cap = cap;
-    M.rowptr = mat->rowptr;
-    M.col = mat->col;
-    M.val = mat->val;
-    M.vhi = mat->vhi;
-    M.vlo = mat->vlo;
+    const MatView M = mat_view(mat);
     const bool jac = mat->prec == SSCG_PREC_JACOBI;
     const float* dinv_f = jac ? mat->dinv_f : nullptr;
     const float2* dinv_df = jac ? mat->dinv_df : nullptr;
+    const double dinv_c = (DM != 0 && jac) ? mat->dia_dinv : 0.0;  // the diagonal form's constant D^-1
     const size_t smem_init = stage_bytes<ArithDF64, VM>(cap);
-    const size_t smem_lvl = pipe_bytes<VAL_F32, kStages>(cap) + 128;
-    const size_t smem_df = pipe_bytes<VM, kStages>(cap) + 128;
+    const size_t smem_lvl = DM != 0 ? 0 : pipe_bytes<VAL_F32, kStages>(cap) + 128;  // the diagonal form stages nothing
+    const size_t smem_df = DM != 0 ? 0 : pipe_bytes<VM, kStages>(cap) + 128;
     const size_t smem64 = stage_bytes<ArithF64, VAL_F64>(cap);
     const GramShape gs_full = gram_shape(s, 1, 1);
     const size_t smem_gram = std::max({(size_t)gs_full.ncols * (kGramTile + 1) * sizeof(float2), sizeof(SmallScratch),
                                        (size_t)kThreads * sizeof(double)});
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<ArithDF64, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem_init));
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_mx_level<VAL_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_mx_level<VAL_F32, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem_lvl));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_gram<ArithDF64, SB, float>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gram));
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_mx_replace<VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_mx_replace<VM, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_true_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
     const int Gi = occupancy_grid(ctx, k_init<ArithDF64, VM>, smem_init, n);
-    const int Gl = occupancy_grid(ctx, k_mx_level<VAL_F32>, smem_lvl, n);
+    const int Gl = occupancy_grid(ctx, k_mx_level<VAL_F32, DM>, smem_lvl, n);
     const int Gg = occupancy_grid(ctx, k_gram<ArithDF64, SB, float>, smem_gram, n);
     const int Gu = occupancy_grid(ctx, k_mx_update<SB>, 0, n);
-    const int Gr = occupancy_grid(ctx, k_mx_replace<VM>, smem_df, n);
+    const int Gr = occupancy_grid(ctx, k_mx_replace<VM, DM>, smem_df, n);
     const int Ge = occupancy_grid(ctx, k_mx_prep, 0, n);
     const int Gt = occupancy_grid(ctx, k_true_res, smem64, n);
     const size_t ld = (size_t)L.ldn;
@@ -297,8 +348,8 @@ int run_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
             for (int j = 0; j < s; j++) {
                 float* unext = j + 1 < s ? ub + (j + 1) * ld : nullptr;
                 const float* uprev = j > 0 ? ub + (j - 1) * ld : nullptr;
-                k_mx_level<VAL_F32><<<Gl, kThreads, smem_lvl, st>>>(M, dinv_df, ub + j * ld, uprev, aub + j * ld,
-                                                                    unext, j, basis, L.ctrl);
+                k_mx_level<VAL_F32, DM><<<Gl, kThreads, smem_lvl, st>>>(M, dinv_df, dinv_c, ub + j * ld, uprev,
+                                                                        aub + j * ld, unext, j, basis, L.ctrl);
                 if (j + 1 < s) P.launches++;
             }
             P.end(FAM_MPK, k);
@@ -311,8 +362,8 @@ int run_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
             k_mx_update<SB><<<Gu, kThreads, 0, st>>>(n, (int)L.ldn, s, ub, aub, pn, po, L.xw, L.r, dinv_f, L.part,
                                                      k == 0, replace ? 0 : 1, L.ctrl, L.hist);
             if (replace) {
-                k_mx_replace<VM><<<Gr, kThreads, smem_df, st>>>(M, L.xw, L.r0, L.r, dinv_f, ub, L.part, L.ctrl,
-                                                                L.hist);
+                k_mx_replace<VM, DM><<<Gr, kThreads, smem_df, st>>>(M, L.xw, L.r0, L.r, dinv_f, dinv_c, ub,
+                                                                    L.part, L.ctrl, L.hist);
                 P.launches++;
             }
             P.end(FAM_UPDATE, k);
@@ -344,6 +395,14 @@ int run_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     SSCG_CUDA(ctx, cudaMemcpyAsync(hctrl, L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     SSCG_CUDA(ctx, cudaStreamSynchronize(st));
     return 0;
+}
+
+template <int VM, int DM>
+int run_mixed_sb(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o,
+                 const MLayout& L, Basis basis, Ctrl* hctrl, Prof& P) {
+    if (o->s <= 4) return run_mixed<VM, 4, DM>(ctx, mat, b, x, o, L, basis, hctrl, P);
+    if (o->s <= 8) return run_mixed<VM, 8, DM>(ctx, mat, b, x, o, L, basis, hctrl, P);
+    return run_mixed<VM, 16, DM>(ctx, mat, b, x, o, L, basis, hctrl, P);
 }
 
 }  // namespace
@@ -388,15 +447,13 @@ int solve_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, 
         return set_err(ctx, SSCG_ERR_CUDA, "could not create profiling events");
     }
     int rc;
-    if (mat->exact_fp32) {
-        if (s <= 4) rc = run_mixed<VAL_F32, 4>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
-        else if (s <= 8) rc = run_mixed<VAL_F32, 8>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
-        else rc = run_mixed<VAL_F32, 16>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
-    } else {
-        if (s <= 4) rc = run_mixed<VAL_DF, 4>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
-        else if (s <= 8) rc = run_mixed<VAL_DF, 8>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
-        else rc = run_mixed<VAL_DF, 16>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
-    }
+    // mplan() carves margins around U and x - x0 whenever the matrix has the diagonal form
+    const int dm = dia_mode(mat, true);
+    if (dm == 7) rc = run_mixed_sb<VAL_F32, 7>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
+    else if (dm == 27) rc = run_mixed_sb<VAL_F32, 27>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
+    else if (dm != 0) rc = run_mixed_sb<VAL_F32, 2>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
+    else if (mat->exact_fp32) rc = run_mixed_sb<VAL_F32, 0>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
+    else rc = run_mixed_sb<VAL_DF, 0>(ctx, mat, bd, xd, o, L, basis, &h, *prof);
     if (rc) {
         delete prof;
         return rc;

@@ -117,13 +117,13 @@ __global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1) k_pcg_spmv(MatView 
     bool ok = true;
     if constexpr (DM != 0 && A::kind == 1) {
         DotAcc d{0.f, 0.f};
-        spmv_dia_df<DM>(
-            M, p,
-            [&](int row, df64 y, df64 xc) {
-                A::st(q + row, y);
-                dot_add(d, xc, y);
-            },
-            [&] { dot_renorm(d); });
+        spmv_dia_df<DM>(M, p, [&](int i, df64 y0, df64 x0, df64 y1, df64 x1, bool has1) {
+            if (has1) st_pair(q + i, y0, y1);
+            else A::st(q + i, y0);
+            dot_add(d, x0, y0);
+            dot_add(d, x1, y1);
+            dot_renorm(d);
+        });
         pq = dot_value(d);
     } else if constexpr (DM != 0) {
         spmv_dia<A>(M, xf, epi);
@@ -400,27 +400,6 @@ PLayout pplan(const sscg_mat* mat, int maxit, unsigned flags, void* base, size_t
     return L;
 }
 
-MatView view(const sscg_mat* mat) {
-    MatView M{};
-    M.n = (int)mat->n;
-    M.cap = stage_cap(mat);
-    M.rowptr = mat->rowptr;
-    M.col = mat->col;
-    M.val = mat->val;
-    M.vhi = mat->vhi;
-    M.vlo = mat->vlo;
-    M.dmask = mat->dia_mask;
-    M.dk = mat->dia ? mat->dia_k : 0;
-    for (int t = 0; t < kDiaMax; t++) {
-        M.doff[t] = t < M.dk ? mat->dia_off[t] : 0;
-        M.dc[t] = t < M.dk ? mat->dia_c[t] : 0.0;
-    }
-    M.dcen = mat->dia_cen;
-    M.dlap = mat->dia_lap;
-    M.dco = (float)mat->dia_co;
-    return M;
-}
-
 // One PCG run.  x may be null (zero start and no export; the Lanczos
 // estimate); coef receives alpha_j, beta_j when not null.
 template <class A, int VM, int DM>
@@ -430,7 +409,7 @@ int run_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, int 
     constexpr bool DIA = DM != 0;
     cudaStream_t st = ctx->stream;
     const int n = (int)mat->n;
-    const MatView M = view(mat);
+    const MatView M = mat_view(mat);
     const size_t smem = stage_bytes<A, VM>(M.cap), smem64 = stage_bytes<ArithF64, VAL_F64>(M.cap);
     const size_t smem_pipe = pipe_bytes<VM, kStages>(M.cap) + 128;
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_pcg_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

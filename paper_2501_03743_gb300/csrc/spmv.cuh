@@ -9,6 +9,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "internal.h"
 
 namespace sscg {
 
@@ -34,6 +35,29 @@ struct MatView {
     int dlap;   // every off-centre coefficient equals dco
     float dco;  // that coefficient
 };
+
+// The kernels' view of a matrix: its CSR arrays and, when it has one, its
+// constant-coefficient diagonal form.
+inline MatView mat_view(const sscg_mat* m) {
+    MatView v{};
+    v.n = (int)m->n;
+    v.cap = stage_cap(m);
+    v.rowptr = m->rowptr;
+    v.col = m->col;
+    v.val = m->val;
+    v.vhi = m->vhi;
+    v.vlo = m->vlo;
+    v.dmask = m->dia_mask;
+    v.dk = m->dia ? m->dia_k : 0;
+    for (int t = 0; t < kDiaMax; t++) {
+        v.doff[t] = t < v.dk ? m->dia_off[t] : 0;
+        v.dc[t] = t < v.dk ? m->dia_c[t] : 0.0;
+    }
+    v.dcen = m->dia_cen;
+    v.dlap = m->dia_lap;
+    v.dco = (float)m->dia_co;
+    return v;
+}
 
 template <class A, int VM>
 struct Val;
@@ -236,25 +260,61 @@ __device__ __forceinline__ void spmv_dia(const MatView& M, XF xf, EPI epi) {
 }
 
 // ---------------------------------------------------------------------------
-// Diagonal form in double-float, two rows per thread, over a guarded vector.
+// Diagonal form in double-float, two rows per thread, over a margined vector.
 //
-// x must be readable at every index in [-g, n + g) for g > max |offset| + 1;
-// the solvers carve such margins around the vectors their levels gather
-// from.  A thread takes rows i and i + 1 (i even), so a warp covers 64
-// consecutive rows and each offset's two gathers share one address; no index
-// is clamped.  A term whose mask bit is clear is replaced by zero before it
+// x (double-float pairs, or FP32 values for the mixed-precision basis) must
+// be readable at every index in [-g, n + g) for g > max |offset| + 1; the
+// solvers carve such margins around the vectors their levels gather from.
+// A thread takes rows i and i + 1 (i even), so a warp covers 64 consecutive
+// rows and each offset's two gathers share one address; no index is
+// clamped.  A term whose mask bit is clear is replaced by zero before it
 // enters the sum, so whatever the margins (or a neighbouring column) hold
-// never reaches a result.  epi(row, y, x_row) receives y = (A x)_row and
-// x_row; tick() runs once per row pair (the callers renormalise their running
-// sums there).
+// never reaches a result.  epi(i, y0, x0, y1, x1, has1) receives
+// y = (A x) and x at rows i and i + 1; has1 is false when i + 1 = n, and then
+// y1 and x1 are zero (callers may fold them into sums unconditionally).
 //
 // Laplacian class (dlap: every off-centre coefficient is dco): the masked
 // neighbours are first summed as double-float values (TwoSum of the high
 // parts, the low parts and the errors gathered in a second float: 8 FP32
 // operations a term), then y = c_centre x_i + dco * sum by one Dot2 step.
 // The general case takes each term as a Dot2 step (dot2_add).
-template <int K, class EPI, class TICK>
-__device__ __forceinline__ void spmv_dia_lap(const MatView& M, const float2* __restrict__ x, EPI epi, TICK tick) {
+template <class TX>
+struct DiaVec;
+
+template <>
+struct DiaVec<float2> {  // double-float elements
+    __device__ static __forceinline__ df64 ld(const float2* p) {
+        const float2 v = __ldg(p);
+        return df_make(v.x, v.y);
+    }
+    __device__ static __forceinline__ void ld_pair(const float2* p, df64& a, df64& b) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));  // p at an even index: 16-byte aligned
+        a = df_make(v.x, v.y);
+        b = df_make(v.z, v.w);
+    }
+};
+
+template <>
+struct DiaVec<float> {  // FP32 elements (exact as double-float)
+    __device__ static __forceinline__ df64 ld(const float* p) { return df_make(__ldg(p), 0.f); }
+    __device__ static __forceinline__ void ld_pair(const float* p, df64& a, df64& b) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));  // p at an even index: 8-byte aligned
+        a = df_make(v.x, 0.f);
+        b = df_make(v.y, 0.f);
+    }
+};
+
+__device__ __forceinline__ void dia_pair_out(df64 c0, df64 c1, int i, int n, const Dot2Acc& a0, const Dot2Acc& a1,
+                                             df64& y0, df64& x0, df64& y1, df64& x1, bool& has1) {
+    has1 = i + 1 < n;
+    x0 = c0;
+    y0 = dot2_result(a0);
+    x1 = has1 ? c1 : df_make(0.f, 0.f);
+    y1 = has1 ? dot2_result(a1) : df_make(0.f, 0.f);
+}
+
+template <int K, class TX, class EPI>
+__device__ __forceinline__ void spmv_dia_lap(const MatView& M, const TX* __restrict__ x, EPI epi) {
     constexpr int C = K / 2;  // symmetric pattern: offset 0 sits in the middle
     const float cc = (float)M.dc[C], co = M.dco;
     const int n = M.n;
@@ -265,62 +325,76 @@ __device__ __forceinline__ void spmv_dia_lap(const MatView& M, const float2* __r
 #pragma unroll
         for (int t = 0; t < K; t++) {
             if (t == C) continue;
-            const float2* a = x + (i + M.doff[t]);
-            const float2 v0 = __ldg(a), v1 = __ldg(a + 1);
+            const TX* a = x + (i + M.doff[t]);
+            const df64 v0 = DiaVec<TX>::ld(a), v1 = DiaVec<TX>::ld(a + 1);
             const bool b0 = (mm.x >> t) & 1u, b1 = (mm.y >> t) & 1u;
-            float u, w;
-            two_sum(s0, b0 ? v0.x : 0.f, u, w);
-            s0 = u;
-            e0 = __fadd_rn(e0, __fadd_rn(w, b0 ? v0.y : 0.f));
-            two_sum(s1, b1 ? v1.x : 0.f, u, w);
-            s1 = u;
-            e1 = __fadd_rn(e1, __fadd_rn(w, b1 ? v1.y : 0.f));
+            const float h0 = b0 ? v0.hi : 0.f, l0 = b0 ? v0.lo : 0.f;
+            const float h1 = b1 ? v1.hi : 0.f, l1 = b1 ? v1.lo : 0.f;
+            if (t == 0) {  // the first term starts the sums
+                s0 = h0;
+                e0 = l0;
+                s1 = h1;
+                e1 = l1;
+            } else {
+                float u, w;
+                two_sum(s0, h0, u, w);
+                s0 = u;
+                e0 = __fadd_rn(e0, __fadd_rn(w, l0));
+                two_sum(s1, h1, u, w);
+                s1 = u;
+                e1 = __fadd_rn(e1, __fadd_rn(w, l1));
+            }
         }
-        const float2 c0 = __ldg(x + i), c1 = __ldg(x + i + 1);
-        const df64 xc0 = df_make(c0.x, c0.y), xc1 = df_make(c1.x, c1.y);
+        df64 c0, c1;
+        DiaVec<TX>::ld_pair(x + i, c0, c1);
         // co * (s + e): its high part exactly as p + fma residue, e scaled into the error float
         float p = __fmul_rn(co, s0);
         Dot2Acc a0{p, __fmaf_rn(co, e0, __fmaf_rn(co, s0, -p))};
         p = __fmul_rn(co, s1);
         Dot2Acc a1{p, __fmaf_rn(co, e1, __fmaf_rn(co, s1, -p))};
-        dot2_add(a0, cc, xc0);
-        dot2_add(a1, cc, xc1);
-        epi(i, dot2_result(a0), xc0);
-        if (i + 1 < n) epi(i + 1, dot2_result(a1), xc1);
-        tick();
+        dot2_add(a0, cc, c0);
+        dot2_add(a1, cc, c1);
+        df64 y0, x0, y1, x1;
+        bool has1;
+        dia_pair_out(c0, c1, i, n, a0, a1, y0, x0, y1, x1, has1);
+        epi(i, y0, x0, y1, x1, has1);
     }
 }
 
-template <class EPI, class TICK>
-__device__ __forceinline__ void spmv_dia_gen(const MatView& M, const float2* __restrict__ x, const int* s_off,
-                                             const float* s_cf, EPI epi, TICK tick) {
+template <class TX, class EPI>
+__device__ __forceinline__ void spmv_dia_gen(const MatView& M, const TX* __restrict__ x, const int* s_off,
+                                             const float* s_cf, EPI epi) {
     const int n = M.n, K = M.dk;
     const int stride = 2 * gridDim.x * blockDim.x;
+    const df64 zero = df_make(0.f, 0.f);
     for (int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x); i < n; i += stride) {
         const uint2 mm = __ldg(reinterpret_cast<const uint2*>(M.dmask + i));
         Dot2Acc a0{0.f, 0.f}, a1{0.f, 0.f};
         for (int t = 0; t < K; t++) {
-            const float2* a = x + (i + s_off[t]);
-            const float2 v0 = __ldg(a), v1 = __ldg(a + 1);
+            const TX* a = x + (i + s_off[t]);
+            const df64 v0 = DiaVec<TX>::ld(a), v1 = DiaVec<TX>::ld(a + 1);
             const bool b0 = (mm.x >> t) & 1u, b1 = (mm.y >> t) & 1u;
-            dot2_add(a0, s_cf[t], b0 ? df_make(v0.x, v0.y) : df_make(0.f, 0.f));
-            dot2_add(a1, s_cf[t], b1 ? df_make(v1.x, v1.y) : df_make(0.f, 0.f));
+            dot2_add(a0, s_cf[t], b0 ? v0 : zero);
+            dot2_add(a1, s_cf[t], b1 ? v1 : zero);
         }
-        const float2 c0 = __ldg(x + i), c1 = __ldg(x + i + 1);
-        epi(i, dot2_result(a0), df_make(c0.x, c0.y));
-        if (i + 1 < n) epi(i + 1, dot2_result(a1), df_make(c1.x, c1.y));
-        tick();
+        df64 c0, c1;
+        DiaVec<TX>::ld_pair(x + i, c0, c1);
+        df64 y0, x0, y1, x1;
+        bool has1;
+        dia_pair_out(c0, c1, i, n, a0, a1, y0, x0, y1, x1, has1);
+        epi(i, y0, x0, y1, x1, has1);
     }
 }
 
 // Diagonal-form kernels are built per mode DM (dia_mode() on the host):
 // 7 / 27 the Laplacian class with that many offsets, 2 any other diagonal
-// form over margined vectors, 1 no margins (clamped, one row per thread).
-// Every thread must call it.
-template <int DM, class EPI, class TICK>
-__device__ __forceinline__ void spmv_dia_df(const MatView& M, const float2* __restrict__ x, EPI epi, TICK tick) {
+// form over margined vectors, 1 no margins (clamped, one row per thread,
+// each row passed as the first of a pair without a second).  Every thread
+// must call it.
+template <int DM, class TX, class EPI>
+__device__ __forceinline__ void spmv_dia_df(const MatView& M, const TX* __restrict__ x, EPI epi) {
     if constexpr (DM == 7 || DM == 27) {
-        spmv_dia_lap<DM>(M, x, epi, tick);
+        spmv_dia_lap<DM>(M, x, epi);
     } else if constexpr (DM == 2) {
         __shared__ int s_off[kDiaMax];
         __shared__ float s_cf[kDiaMax];
@@ -329,14 +403,12 @@ __device__ __forceinline__ void spmv_dia_df(const MatView& M, const float2* __re
             s_cf[t] = t < M.dk ? (float)M.dc[t] : 0.f;
         }
         __syncthreads();
-        spmv_dia_gen(M, x, s_off, s_cf, epi, tick);
+        spmv_dia_gen(M, x, s_off, s_cf, epi);
     } else {
+        const df64 zero = df_make(0.f, 0.f);
         spmv_dia<ArithDF64>(
-            M, [&](int c) { return ArithDF64::ldg(x + c); },
-            [&](int row, df64 y) {
-                epi(row, y, ArithDF64::ldg(x + row));
-                tick();
-            });
+            M, [&](int c) { return DiaVec<TX>::ld(x + c); },
+            [&](int row, df64 y) { epi(row, y, DiaVec<TX>::ld(x + row), zero, zero, false); });
     }
 }
 

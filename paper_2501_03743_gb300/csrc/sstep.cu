@@ -60,27 +60,25 @@ __global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1) k_level(MatView M, 
     };
     bool ok = true;
     if constexpr (DM != 0 && A::kind == 1) {
-        // paired rows; moments as running Dot2 sums, renormalised once per pair
+        // Diagonal form (double-float): B^-1 is the constant dinv_c (Jacobi) or
+        // the identity (dinv_c = 0), the level always writes u_{j+1} and never
+        // AU_j.  Rows come in pairs; the moments are running Dot2 sums,
+        // renormalised once per pair, with mu_{2j+2} = dinv_c * (y . y).
+        const df64 d1c = dinv_c != 0.0 ? dc : df_make(1.f, 0.f);
         DotAcc d1{0.f, 0.f}, d2{0.f, 0.f};
-        spmv_dia_df<DM>(
-            M, u_in,
-            [&](int row, df64 y, df64 xc) {
-                if (au_out) A::st(au_out + row, y);
-                dot_add(d1, xc, y);
-                if (u_next || want_m2) {
-                    const df64 z = dinv ? df_mul(A::ld(dinv + row), y) : (dinv_c != 0.0 ? df_mul(dc, y) : y);
-                    if (u_next) A::st(u_next + row, z);
-                    if (dinv) dot_add(d2, y, z);
-                    else dot_add_sq(d2, y);  // y . D^-1 y = dinv_c * (y . y), scaled below
-                }
-            },
-            [&] {
-                dot_renorm(d1);
-                dot_renorm(d2);
-            });
+        spmv_dia_df<DM>(M, u_in, [&](int i, df64 y0, df64 x0, df64 y1, df64 x1, bool has1) {
+            const df64 z0 = df_mul(d1c, y0), z1 = df_mul(d1c, y1);
+            if (has1) st_pair(u_next + i, z0, z1);
+            else A::st(u_next + i, z0);
+            dot_add(d1, x0, y0);
+            dot_add(d1, x1, y1);
+            dot_add_sq(d2, y0);
+            dot_add_sq(d2, y1);
+            dot_renorm(d1);
+            dot_renorm(d2);
+        });
         m1 = dot_value(d1);
-        m2 = dot_value(d2);
-        if (!dinv && dinv_c != 0.0) m2 = df_mul(dc, m2);
+        m2 = df_mul(d1c, dot_value(d2));
     } else if constexpr (DM != 0) {
         spmv_dia<A>(M, xf, epi);
     } else {
@@ -406,28 +404,6 @@ Layout plan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t c
     return L;
 }
 
-MatView view_of(const sscg_mat* m, int cap) {
-    MatView v{};
-    v.n = (int)m->n;
-    v.cap = cap;
-    v.rowptr = m->rowptr;
-    v.col = m->col;
-    v.val = m->val;
-    v.vhi = m->vhi;
-    v.vlo = m->vlo;
-    v.dmask = m->dia_mask;
-    v.dk = m->dia ? m->dia_k : 0;
-    for (int t = 0; t < kDiaMax; t++) {
-        v.doff[t] = t < v.dk ? m->dia_off[t] : 0;
-        v.dc[t] = t < v.dk ? m->dia_c[t] : 0.0;
-    }
-    v.dcen = m->dia_cen;
-    v.dlap = m->dia_lap;
-    v.dco = (float)m->dia_co;
-    return v;
-}
-
-
 template <class A, int VM, int SB, int DM>
 int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o,
               const Layout& L, const typename A::S* dinv, const typename A::S* diag, Ctrl* hctrl, Prof& P) {
@@ -436,7 +412,7 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     cudaStream_t st = ctx->stream;
     const int n = (int)mat->n, s = o->s, G = L.G;
     const int cap = stage_cap(mat);
-    MatView M = view_of(mat, cap);
+    MatView M = mat_view(mat);
     const size_t smem = std::max(stage_bytes<A, VM>(cap), sizeof(SmallScratch));
     const size_t smem_pipe = std::max(pipe_bytes<VM, kStages>(cap), sizeof(SmallScratch)) + 128;
     const size_t smem64 = stage_bytes<ArithF64, VAL_F64>(cap);

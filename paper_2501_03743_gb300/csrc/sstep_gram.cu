@@ -56,8 +56,13 @@ GLayout gplan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t
     GramShape gs = gram_shape(o->s, 1);
     L.part = c.take<double>((size_t)G * std::max(gs.E, 4));
     size_t blk = (size_t)L.ldn * 2 * o->s;
+    // margins: the diagonal-form levels gather the U columns without clamping
+    const size_t g = dia_margin(mat);
+    if (g) c.take<double>(g);
     L.blk[0] = c.take<double>(blk);
+    if (g) c.take<double>(g);
     L.blk[1] = c.take<double>(blk);
+    if (g) c.take<double>(g);
     L.r = c.take<double>((size_t)L.ldn);
     L.xw = (o->arith == SSCG_ARITH_F64) ? nullptr : c.take<double>((size_t)L.ldn);
     L.w = c.take<double>((size_t)L.ldn);
@@ -70,21 +75,14 @@ GLayout gplan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t
     return L;
 }
 
-template <class A, int VM, int SB>
+template <class A, int VM, int SB, int DM>
 int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o, const GLayout& L,
              const typename A::S* dinv, Basis basis, Ctrl* hctrl, Prof& P) {
     using S = typename A::S;
     cudaStream_t st = ctx->stream;
     const int n = (int)mat->n, s = o->s;
     const int cap = stage_cap(mat);
-    MatView M{};
-    M.n = n;
-    M.cap = cap;
-    M.rowptr = mat->rowptr;
-    M.col = mat->col;
-    M.val = mat->val;
-    M.vhi = mat->vhi;
-    M.vlo = mat->vlo;
+    const MatView M = mat_view(mat);
     const size_t smem = std::max(stage_bytes<A, VM>(cap), sizeof(SmallScratch));
     const size_t smem64 = stage_bytes<ArithF64, VAL_F64>(cap);
     const size_t smem_pipe = pipe_bytes<VM, kStages>(cap) + 128;
@@ -92,12 +90,13 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
     const size_t smem_gram = std::max({(size_t)gs_full.ncols * (kGramTile + 1) * sizeof(S), sizeof(SmallScratch),
                                        (size_t)kThreads * sizeof(double)});
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_level_gen<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pipe));
+    const size_t smem_lv = DM != 0 ? 0 : smem_pipe;  // the diagonal form stages nothing
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_level_gen<A, VM, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_lv));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_cheb_step<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pipe));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_gram<A, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gram));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_true_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
     const int Gi = occupancy_grid(ctx, k_init<A, VM>, smem, n);
-    const int Gl = occupancy_grid(ctx, k_level_gen<A, VM>, smem_pipe, n);
+    const int Gl = occupancy_grid(ctx, k_level_gen<A, VM, DM>, smem_lv, n);
     const int Gg = occupancy_grid(ctx, k_gram<A, SB>, smem_gram, n);
     size_t smem_upd = 0;
     int Gu = 0;
@@ -113,6 +112,8 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
     S* w = (S*)L.w;
     S* tmp = (S*)L.tmp;
     const S* dvec = dinv;  // Jacobi scaling (null: B = I); the Chebyshev preconditioner scales by D^-1 too
+    // under the diagonal form D is the constant diagonal value
+    const double dinv_c = (DM != 0 && dinv) ? mat->dia_dinv : 0.0;
 
     P.begin();
     k_init<A, VM><<<Gi, kThreads, smem, st>>>(M, dvec, b, x, A::kind == 0 ? nullptr : xw, r, diag ? blk[0] : nullptr,
@@ -136,8 +137,9 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
             for (int j = 0; j < s; j++) {
                 S* unext = j + 1 < s ? bn + (j + 1) * ld : nullptr;
                 const S* uprev = j > 0 ? bn + (j - 1) * ld : nullptr;
-                k_level_gen<A, VM><<<Gl, kThreads, smem_pipe, st>>>(M, dvec, bn + j * ld, uprev, bn + (s + j) * ld, unext,
-                                                               j, basis, diag ? 1 : 0, L.ctrl);
+                k_level_gen<A, VM, DM><<<Gl, kThreads, smem_lv, st>>>(M, dvec, dinv_c, bn + j * ld, uprev,
+                                                                       bn + (s + j) * ld, unext, j, basis,
+                                                                       diag ? 1 : 0, L.ctrl);
                 if (!diag && unext) {
                     P.launches += cheb.apply(M, dvec, bn + (s + j) * ld, w, tmp, ld, Ge, Gl, smem_pipe, st, L.ctrl);
                     k_combine<A><<<Ge, kThreads, 0, st>>>(n, w, bn + j * ld, uprev, unext, j, basis, L.ctrl);
@@ -186,6 +188,14 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
     return 0;
 }
 
+template <class A, int VM, int DM>
+int run_gram_sb(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o, const GLayout& L,
+                const typename A::S* dinv, Basis basis, Ctrl* hctrl, Prof& P) {
+    if (o->s <= 4) return run_gram<A, VM, 4, DM>(ctx, mat, b, x, o, L, dinv, basis, hctrl, P);
+    if (o->s <= 8) return run_gram<A, VM, 8, DM>(ctx, mat, b, x, o, L, dinv, basis, hctrl, P);
+    return run_gram<A, VM, 16, DM>(ctx, mat, b, x, o, L, dinv, basis, hctrl, P);
+}
+
 }  // namespace
 
 int gram_workspace(const sscg_mat* mat, const sscg_opts* o, size_t* bytes) {
@@ -232,20 +242,19 @@ int solve_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, c
     int rc;
     if (o->arith == SSCG_ARITH_F64) {
         const double* d = scale ? mat->dinv : nullptr;
-        if (s <= 4) rc = run_gram<ArithF64, VAL_F64, 4>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
-        else if (s <= 8) rc = run_gram<ArithF64, VAL_F64, 8>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
-        else rc = run_gram<ArithF64, VAL_F64, 16>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+        if (s <= 4) rc = run_gram<ArithF64, VAL_F64, 4, 0>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+        else if (s <= 8) rc = run_gram<ArithF64, VAL_F64, 8, 0>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+        else rc = run_gram<ArithF64, VAL_F64, 16, 0>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
     } else {
         const float2* d = scale ? mat->dinv_df : nullptr;
-        if (mat->exact_fp32) {
-            if (s <= 4) rc = run_gram<ArithDF64, VAL_F32, 4>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
-            else if (s <= 8) rc = run_gram<ArithDF64, VAL_F32, 8>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
-            else rc = run_gram<ArithDF64, VAL_F32, 16>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
-        } else {
-            if (s <= 4) rc = run_gram<ArithDF64, VAL_DF, 4>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
-            else if (s <= 8) rc = run_gram<ArithDF64, VAL_DF, 8>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
-            else rc = run_gram<ArithDF64, VAL_DF, 16>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
-        }
+        // the diagonal form serves the levels of a diagonal (or no) preconditioner; gplan()
+        // carves margins around both blocks whenever the matrix has the form
+        const int dm = mat->prec != SSCG_PREC_CHEB ? dia_mode(mat, true) : 0;
+        if (dm == 7) rc = run_gram_sb<ArithDF64, VAL_F32, 7>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+        else if (dm == 27) rc = run_gram_sb<ArithDF64, VAL_F32, 27>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+        else if (dm != 0) rc = run_gram_sb<ArithDF64, VAL_F32, 2>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+        else if (mat->exact_fp32) rc = run_gram_sb<ArithDF64, VAL_F32, 0>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
+        else rc = run_gram_sb<ArithDF64, VAL_DF, 0>(ctx, mat, bd, xd, o, L, d, basis, &h, *prof);
     }
     if (rc) {
         delete prof;
