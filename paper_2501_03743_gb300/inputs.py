@@ -104,6 +104,13 @@ def poisson27(N: int):
     return _stencil(N, offs, w)
 
 
+def aniso7(N: int):
+    """Anisotropic 7-point stencil: couplings -1, -2, -4 along x, y, z and the
+    centre 14 (constant coefficients that are not all equal off the centre)."""
+    w = [-(1.0 if o[2] else 2.0 if o[1] else 4.0) if o != (0, 0, 0) else 14.0 for o in _OFFS7]
+    return _stencil(N, _OFFS7, w)
+
+
 def smoothed_field(N: int, seed: int, ell: float = 4.0) -> np.ndarray:
     """Seeded N(0,1) noise on N^3 cells, Gaussian-smoothed (std ``ell`` cells,
     reflecting boundary, truncated at 3 std), normalised to mean 0, var 1.
@@ -160,6 +167,8 @@ def system(kind: str, N: int, seed: int = 0, sigma: float = 0.0, ell: float = 4.
         rowptr, col, val = poisson7(N)
     elif kind == "poisson27":
         rowptr, col, val = poisson27(N)
+    elif kind == "aniso7":
+        rowptr, col, val = aniso7(N)
     elif kind == "varcoef7":
         rowptr, col, val = varcoef7(N, sigma, seed + 7919, ell)
     else:

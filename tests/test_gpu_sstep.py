@@ -355,7 +355,7 @@ def test_full_size_256_s4_against_oracle(ctx):
 def test_diagonal_form_detection(ctx):
     """Constant stencils are multiplied in the diagonal form; variable
     coefficients, a perturbed stencil and CSR-only creation stay CSR."""
-    for kind, N, want in (("poisson7", 9, 7), ("poisson27", 7, 27)):
+    for kind, N, want in (("poisson7", 9, 7), ("poisson27", 7, 27), ("aniso7", 9, 7)):
         S = system(kind, N, 0)
         assert gpu_matrix(ctx, S).props()["format"] == 1
         assert gpu_matrix(ctx, S).props()["dia_offsets"] == want
@@ -371,7 +371,7 @@ def test_diagonal_form_detection(ctx):
 
 
 @pytest.mark.parametrize("arith", ["f64", "df64"])
-@pytest.mark.parametrize("kind,N", [("poisson7", 21), ("poisson27", 13)])
+@pytest.mark.parametrize("kind,N", [("poisson7", 21), ("poisson27", 13), ("aniso7", 17), ("poisson7", 16)])
 def test_diagonal_form_matches_csr_and_oracle(ctx, arith, kind, N):
     S = system(kind, N, 3)
     Ad = gpu_matrix(ctx, S)
@@ -388,3 +388,30 @@ def test_diagonal_form_matches_csr_and_oracle(ctx, arith, kind, N):
     assert abs(rd.outer_iters - ref.iters) <= 1
     same = oracle.pcgs(oracle.as_matrix(S), S["b"], 4, tol=0.0, maxit=rd.outer_iters)
     assert rel(xd, same.x) < 1e-7
+
+
+@pytest.mark.parametrize("kind,N", [("poisson7", 19), ("aniso7", 15), ("poisson27", 11), ("poisson7", 12)])
+def test_diagonal_form_in_gram_and_mixed_paths(ctx, kind, N):
+    """The direct-Gram levels (Chebyshev and monomial bases) and the
+    mixed-precision levels and residual replacement multiply in the diagonal
+    form; each matches the same solve on the CSR arrays (odd and even n,
+    the Laplacian class and a stencil with unequal couplings)."""
+    S = system(kind, N, 5)
+    Ad = gpu_matrix(ctx, S)
+    Ac = sscg.Matrix(ctx, S["rowptr"], S["col"], S["val"], csr_only=True)
+    assert Ad.props()["format"] == 1 and Ac.props()["format"] == 0
+    cases = (
+        dict(s=6, basis="chebyshev", tol=1e-9, maxit=2000, arith="df64", basis_bounds=(0.05, 2.0)),
+        dict(s=4, tol=1e-9, maxit=2000, arith="df64", direct_gram=True),
+        dict(s=4, tol=1e-9, maxit=2000, arith="mixed", replace_every=1),
+        dict(s=4, basis="chebyshev", tol=1e-9, maxit=2000, arith="mixed", replace_every=2,
+             basis_bounds=(0.05, 2.0)),
+    )
+    for kw in cases:
+        xd, rd = gpu_solve(Ad, S["b"], **kw)
+        xc, rc = gpu_solve(Ac, S["b"], **kw)
+        assert rd.status == rc.status == sscg.OK, kw
+        assert abs(rd.outer_iters - rc.outer_iters) <= (1 if kw["arith"] == "mixed" else 0), kw
+        # mixed: the FP32 basis rounds differently when A u is summed in another order
+        assert rel(xd, xc) < (1e-6 if kw["arith"] == "mixed" else 1e-10), kw
+        assert rel(xd, S["x_true"]) < 1e-6, kw

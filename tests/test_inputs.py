@@ -28,3 +28,21 @@ def test_batch_spec_is_seeded_and_in_range():
     r = inputs.batch_csr(dict(kind="varcoef7", N=6, sigma=2.0, field_seed=3, nrhs=1))
     ref = inputs.varcoef7(6, 2.0, 3)
     assert all(np.array_equal(x, y) for x, y in zip(r, ref))
+
+
+def test_aniso7_couplings():
+    """The anisotropic stencil: symmetric, centre 14, couplings -1/-2/-4 along
+    x/y/z (strides 1, N, N^2), positive definite."""
+    import scipy.sparse as sp
+
+    N = 5
+    rowptr, col, val = inputs.aniso7(N)
+    A = sp.csr_matrix((val, col, rowptr), shape=(N ** 3, N ** 3)).toarray()
+    assert np.array_equal(A, A.T)
+    i = 2 + 2 * N + 2 * N * N  # an interior node
+    assert A[i, i] == 14.0
+    assert A[i, i - 1] == A[i, i + 1] == -1.0
+    assert A[i, i - N] == A[i, i + N] == -2.0
+    assert A[i, i - N * N] == A[i, i + N * N] == -4.0
+    assert np.count_nonzero(A[i]) == 7
+    assert np.linalg.eigvalsh(A).min() > 0.0
