@@ -100,9 +100,7 @@ def parse():
 # captured launches; at that size L2 still holds most of the level's writes
 # when it ends) and the block update.  The roofline's "traffic" scales them
 # to the workload's n; it is null for any other configuration.
-# The level kernel changed (paired-row diagonal form) after its counters were
-# taken; its entry returns when a new capture is in.
-NCU_TRAFFIC_PER_ROW = {"update": 732.694e6 / 4.096e6}
+NCU_TRAFFIC_PER_ROW = {"mpk": 54.0e6 / 4.096e6, "update": 732.694e6 / 4.096e6}
 NCU_TRAFFIC_CONFIG = dict(s=4, arith="df64", fused_mpk=False, dia=True)
 
 
