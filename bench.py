@@ -489,7 +489,10 @@ def run_batch(a, world, rank, local, pg):
     barrier(pg)
     clocks = Clocks(local)
     clocks.start()
-    runs = [one() for _ in range(a.steps)]
+    runs, launches = [], 0
+    for _ in range(a.steps):
+        runs.append(one())
+        launches += plan.props()["launches"]  # kernels of that solve, graph nodes included
     clk = clocks.stop()
     barrier(pg)
     ms = [r.solve_ms for r in runs]
@@ -551,7 +554,7 @@ def run_batch(a, world, rank, local, pg):
                      "autotuned": not a.no_tune, "plan_s": round(t_plan, 2),
                      "mode": ("persistent cooperative launch" if a.persistent else
                               "per-phase launches over all systems, CUDA graph per outer step")},
-            "gpu_launches": a.steps, "setup_s": round(t_gen, 1), "clocks": clk,
+            "gpu_launches": int(launches), "setup_s": round(t_gen, 1), "clocks": clk,
         }
         if seq:
             line.update(seq)
@@ -597,7 +600,7 @@ def run_mixed27(a, world, rank, local, pg):
         solver = sscg.Solver(A, s=a.s, tol=1e-10, maxit=5000, **kw)
         x.zero_()
         solver.solve(b, x)
-        ms, res = [], None
+        ms, res, nl = [], None, 0
         for _ in range(max(1, a.steps)):
             x.zero_()
             torch.cuda.synchronize()
@@ -607,8 +610,9 @@ def run_mixed27(a, world, rank, local, pg):
             e1.record(ctx.stream)
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
+            nl += res.profile["kernel_launches"]
         xs = x.cpu().numpy()
-        out[name] = dict(ms=statistics.median(ms), outer=res.outer_iters, status=res.status,
+        out[name] = dict(ms=statistics.median(ms), outer=res.outer_iters, status=res.status, launches=nl,
                          rel_res_true=res.rel_res_true,
                          err_vs_oracle=float(np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x)),
                          err_vs_x_true=float(np.linalg.norm(xs - sysm["x_true"]) / np.linalg.norm(sysm["x_true"])))
@@ -624,6 +628,7 @@ def run_mixed27(a, world, rank, local, pg):
                 "mixed": {k: (round(v, 3) if k == "ms" else v) for k, v in m.items()},
                 "df64": {k: (round(v, 3) if k == "ms" else v) for k, v in out["df64"].items()},
                 "speedup_mixed_vs_df64": round(out["df64"]["ms"] / m["ms"], 3),
+                "gpu_launches": int(m["launches"]),
                 "cpu_baseline": {"value": round(t_oracle * 1e3, 1), "unit": "ms", "cores": oracle.num_threads(),
                                  "kind": "oracle",
                                  "sample": f"the whole solve: FP64 CPU oracle PCG to 1e-10, {ref.iters} iterations"}}
@@ -695,7 +700,7 @@ def run_cheb(a, world, rank, local, pg):
 
                 r, ms = timed(go)
                 row[name] = {"ms": round(ms, 3), "status": r.status, "outer": r.outer_iters,
-                             "rel_res_true": r.rel_res_true}
+                             "rel_res_true": r.rel_res_true, "launches": r.profile["kernel_launches"]}
             A.set_bounds_model(net.h, None)
             (lo, hi), t_net = timed(lambda: net.bounds(A, blob))
             (llo, lhi), t_lz = timed(lambda: A.estimate_bounds(20))
@@ -715,6 +720,7 @@ def run_cheb(a, world, rank, local, pg):
                            "training": f"{len(samples)} seeded systems at 8^3..128^3, labels from device "
                                        f"Lanczos, {len(hist)} Adam epochs, {t_train:.1f} s",
                            "parallelism": f"replicas x{world}"},
+                "gpu_launches": int(sum(r["network"]["launches"] + r["lanczos"]["launches"] for r in rows)),
                 "rows": rows}
         print(json.dumps(line), flush=True)
     barrier(pg)

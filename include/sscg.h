@@ -388,6 +388,11 @@ int sscg_batch_solve(sscg_batch* plan, const double* const* B, double* const* X,
  * persistent mode), and the last solve's device time in ms (CUDA events
  * around it).  Any pointer may be NULL. */
 int sscg_batch_props(const sscg_batch* plan, int* tile_rows, int* grid, int* graph, float* last_ms);
+/* Kernels the last sscg_batch_solve ran, nodes of replayed CUDA graphs
+ * included (per outer step: s levels, the solves, the update; plus the
+ * initial launch); 1 in the persistent mode.  0 before the first solve.
+ * SSCG_ERR_INVALID for a NULL argument. */
+int sscg_batch_launches(const sscg_batch* plan, int64_t* launches);
 
 #ifdef __cplusplus
 }

@@ -755,6 +755,7 @@ struct sscg_batch {
     GCtl* h_g;
     cudaGraphExec_t exec;
     float last_ms;
+    int64_t last_launches;       // kernels the last solve ran (graph nodes included)
 };
 
 namespace {
@@ -1097,6 +1098,7 @@ int run_phases(sscg_batch* b) {
     if (int rc = reset_state(b)) return rc;
     SSCG_CUDA(ctx, cudaMemcpyAsync(b->d_io, b->h_io, sizeof(double*) * 2 * b->nsys, cudaMemcpyHostToDevice, st));
     if (int rc = launch_any(b, L_INIT, 0, b->maxit)) return rc;
+    b->last_launches = 1;
     const int limit = b->maxit + 4, per_chunk = 8;
     cudaEvent_t ev[2];
     SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
@@ -1114,6 +1116,7 @@ int run_phases(sscg_batch* b) {
         }
         if (rc) break;
         launched += c;
+        b->last_launches += (int64_t)c * (b->s + 2);  // s levels, the solves, the update
         const int slot = chunk & 1;
         if (cudaMemcpyAsync((void*)(ctx->pinned + slot), &b->d_g->finished, sizeof(int), cudaMemcpyDeviceToHost,
                             st) != cudaSuccess ||
@@ -1263,6 +1266,7 @@ int sscg_batch_solve(sscg_batch* b, const double* const* B, double* const* X, ss
     SSCG_CUDA(ctx, cudaEventCreate(&e0));
     SSCG_CUDA(ctx, cudaEventCreate(&e1));
     SSCG_CUDA(ctx, cudaEventRecord(e0, st));
+    b->last_launches = 1;  // the persistent mode: one cooperative kernel
     if (!b->persistent) {
         if (int rc = run_phases(b)) return rc;
     } else if (b->graph_ok) {
@@ -1330,6 +1334,12 @@ int sscg_batch_props(const sscg_batch* b, int* tile_rows, int* grid, int* graph,
     if (grid) *grid = b->persistent ? b->grid : b->g_update;
     if (graph) *graph = b->graph_ok;
     if (last_ms) *last_ms = b->last_ms;
+    return SSCG_OK;
+}
+
+int sscg_batch_launches(const sscg_batch* b, int64_t* launches) {
+    if (!b || !launches) return SSCG_ERR_INVALID;
+    *launches = b->last_launches;
     return SSCG_OK;
 }
 

@@ -35,7 +35,7 @@ EXPORTS = (
     "sscg_solve_static", "sscg_features_workspace_bytes", "sscg_mat_features", "sscg_mlp_nparams",
     "sscg_mlp_workspace_bytes", "sscg_mlp_forward", "sscg_mlp_loss_grad", "sscg_mlp_adam_step", "sscg_mlp_train",
     "sscg_bounds_mlp", "sscg_set_bounds_model", "sscg_batch_workspace_bytes", "sscg_batch_create",
-    "sscg_batch_destroy", "sscg_batch_solve", "sscg_batch_props",
+    "sscg_batch_destroy", "sscg_batch_solve", "sscg_batch_props", "sscg_batch_launches",
 )
 BATCH_MAX_RHS = 8
 BATCH_PERSISTENT = 0x10
@@ -124,6 +124,7 @@ def load(path: str | None = None):
     L.sscg_batch_destroy.argtypes = [vp]
     L.sscg_batch_solve.argtypes = [vp, vp, vp, vp, vp, vp]
     L.sscg_batch_props.argtypes = [vp, vp, P(i32), P(i32), P(C.c_float)]
+    L.sscg_batch_launches.argtypes = [vp, P(C.c_int64)]
     _lib = L
     return L
 
@@ -386,7 +387,10 @@ class BatchSolver:
         tiles = (C.c_int * k)()
         grid, graph, ms = C.c_int(), C.c_int(), C.c_float()
         self.ctx.check(self.ctx.lib.sscg_batch_props(self.h, tiles, C.byref(grid), C.byref(graph), C.byref(ms)))
-        return dict(tile_rows=list(tiles), grid=grid.value, graph=bool(graph.value), last_ms=ms.value)
+        nl = C.c_int64()
+        self.ctx.check(self.ctx.lib.sscg_batch_launches(self.h, C.byref(nl)))
+        return dict(tile_rows=list(tiles), grid=grid.value, graph=bool(graph.value), last_ms=ms.value,
+                    launches=nl.value)
 
     def solve(self, B, X) -> BatchResult:
         """B[k], X[k]: FP64 device tensors of shape (nrhs[k], n_k) (each
