@@ -56,6 +56,7 @@ constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;
 // Per-phase level kernel: CSR entries of a 256-row sub-tile staged in shared
 // memory (column index + value as hi/lo floats or a double: 12 bytes).
 constexpr int kLevelCap = 3072;
+constexpr int kGather = 8;  // CSR entries per row whose gathers a level issues ahead of its arithmetic
 constexpr size_t kLevelSmem = (size_t)(kBThreads + 4) * 4 + (size_t)kLevelCap * 12 + 64;
 
 enum SysState { SYS_ACTIVE = 0, SYS_EXPORT = 1, SYS_FINISHED = 2 };
@@ -301,6 +302,20 @@ __device__ __forceinline__ void cta_sum_slots(typename A::R val, int slot, int n
     const int slot = tr < rows_it ? r : kMaxR;                   \
     (void)slot
 
+// One Dot2 step a += v * x for a double-float matrix value v = (v.x, v.y):
+// the high product exactly (FMA TwoProduct) plus the cross terms in the
+// error float; v.y * x.lo is dropped, as in df_fma.
+__device__ __forceinline__ void dot2_add_df(Dot2Acc& a, float2 v, df64 x) {
+    const float p = __fmul_rn(v.x, x.hi);
+    float e = __fmaf_rn(v.x, x.hi, -p);
+    e = __fmaf_rn(v.x, x.lo, e);
+    e = __fmaf_rn(v.y, x.hi, e);
+    float u, w;
+    two_sum(a.s, p, u, w);
+    a.s = u;
+    a.e = __fadd_rn(a.e, __fadd_rn(w, e));
+}
+
 // Init phase: items it0, it0 + itstep, ... of every system.
 template <class A>
 __device__ void ph_init(const BArgs& a, int it0, int itstep) {
@@ -386,12 +401,21 @@ __device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
         const bool want_m2 = 2 * j + 2 <= 2 * s - 1;
         const Rv dinv_cst = A::from_d(yb.dinv_c);
         Rv m1 = A::zero(), m2 = A::zero();
+        DotAcc d1{0.f, 0.f}, d2{0.f, 0.f};  // double-float: the moments as running Dot2 sums
         auto epi = [&](int i, Rv av) {
             const size_t o = (size_t)i * R + r;
-            m1 = A::fma(RO ? A::ldg(uj + o) : A::ldcg(uj + o), av, m1);
+            const Rv ui = RO ? A::ldg(uj + o) : A::ldcg(uj + o);
             const Rv z = A::mul(yb.dinv ? A::ldg(reinterpret_cast<const S*>(yb.dinv) + i) : dinv_cst, av);
             A::st(un + o, z);
-            if (want_m2) m2 = A::fma(av, z, m2);
+            if constexpr (A::kind == 1) {
+                dot_add(d1, ui, av);
+                dot_add(d2, av, z);
+                dot_renorm(d1);
+                dot_renorm(d2);
+            } else {
+                m1 = A::fma(ui, av, m1);
+                if (want_m2) m2 = A::fma(av, z, m2);
+            }
         };
         if (!RO || yb.dk) {
             if (yb.dk) {
@@ -427,6 +451,36 @@ __device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
                     else s_vd[q] = __ldg(yb.val + base + q);
                 }
                 __syncthreads();
+                if constexpr (A::kind == 1) {
+                  if (s_rp[rows_t] - base <= kLevelCap) {
+                    // Whole sub-tile staged (the common case): the gathers of
+                    // a row's first kGather entries are issued before any
+                    // arithmetic, from shared-memory columns and values only;
+                    // each row is a Dot2 sum (values in double-float, the
+                    // lo * lo product dropped as in df_fma).
+                    const S* ur = uj + r;
+                    for (int rl = tr; tr < rows_it && rl < rows_t; rl += rows_it) {
+                        const int ks = s_rp[rl] - base, ke = s_rp[rl + 1] - base;
+                        Rv xa[kGather];
+#pragma unroll
+                        for (int t = 0; t < kGather; t++)
+                            if (ks + t < ke) {
+                                const S* px = ur + (size_t)s_col[ks + t] * R;
+                                xa[t] = RO ? A::ldg(px) : A::ldcg(px);
+                            }
+                        Dot2Acc aa{0.f, 0.f};
+#pragma unroll
+                        for (int t = 0; t < kGather; t++)
+                            if (ks + t < ke) dot2_add_df(aa, s_vf[ks + t], xa[t]);
+                        for (int q = ks + kGather; q < ke; q++) {  // longer rows
+                            const S* px = ur + (size_t)s_col[q] * R;
+                            dot2_add_df(aa, s_vf[q], RO ? A::ldg(px) : A::ldcg(px));
+                        }
+                        epi(t0 + rl, dot2_result(aa));
+                    }
+                    continue;
+                  }
+                }
                 for (int rl = tr; tr < rows_it && rl < rows_t; rl += rows_it) {
                     const int ks = s_rp[rl] - base, ke = s_rp[rl + 1] - base;
                     Rv acc = A::zero();
@@ -444,6 +498,10 @@ __device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
                     epi(t0 + rl, acc);
                 }
             }
+        }
+        if constexpr (A::kind == 1) {
+            m1 = dot_value(d1);
+            m2 = want_m2 ? dot_value(d2) : A::zero();
         }
         double out = 0.0;
         cta_sum_slots<A>(m1, slot, R, red, &out);
@@ -699,7 +757,7 @@ __global__ void __launch_bounds__(kBThreads) k_bp_init(BArgs a) {
 }
 
 template <class A>
-__global__ void __launch_bounds__(kBThreads) k_bp_level(BArgs a, int j) {
+__global__ void __launch_bounds__(kBThreads, 4) k_bp_level(BArgs a, int j) {
     if (batch_done(a)) return;
     ph_level<A, true>(a, j, blockIdx.x, gridDim.x);
 }
