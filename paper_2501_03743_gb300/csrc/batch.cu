@@ -56,7 +56,6 @@ constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;
 // Per-phase level kernel: CSR entries of a 256-row sub-tile staged in shared
 // memory (column index + value as hi/lo floats or a double: 12 bytes).
 constexpr int kLevelCap = 3072;
-constexpr int kGather = 8;  // CSR entries per row whose gathers a level issues ahead of its arithmetic
 constexpr size_t kLevelSmem = (size_t)(kBThreads + 4) * 4 + (size_t)kLevelCap * 12 + 64;
 
 enum SysState { SYS_ACTIVE = 0, SYS_EXPORT = 1, SYS_FINISHED = 2 };
@@ -77,6 +76,8 @@ struct BSys {
     int dk, pad0;
     int doff[kDiaMax];
     float dcf[kDiaMax];
+    int dcen, dlap;  // index of offset 0; every off-centre value equals dco
+    float dco, pad1;
     double dinv_c, diag_c;
     int n, R, exact, T;
     int items, item0, rhs0, pad;
@@ -96,6 +97,8 @@ struct BReg {
     const void* diag;
     double dinv_c, diag_c;
     int n, R, exact, dk;
+    int dcen, dlap;
+    float dco;
 };
 
 __device__ __forceinline__ BReg breg(const BSys& y) {
@@ -114,6 +117,9 @@ __device__ __forceinline__ BReg breg(const BSys& y) {
     b.R = y.R;
     b.exact = y.exact;
     b.dk = y.dk;
+    b.dcen = y.dcen;
+    b.dlap = y.dlap;
+    b.dco = y.dco;
     return b;
 }
 
@@ -223,13 +229,50 @@ struct BK {
     // their gathers are contiguous.  RO: v was written by an earlier launch
     // (read-only path); otherwise through L2.  soff/scf: the diagonal form's
     // offsets and values in shared memory.
-    template <bool RO>
+    template <bool RO, bool LAP = true>
     static __device__ __forceinline__ Rv spmv_elem(const BReg& y, const int* soff, const float* scf, int i, int r,
                                                    const S* v) {
         const int R = y.R;
         Rv acc = A::zero();
         if (y.dk) {
             const uint32_t m = __ldg(y.dmask + i);
+            if constexpr (A::kind == 1 && LAP) {
+                if (y.dlap) {
+                    // Laplacian class: the present neighbours summed as
+                    // double-float values (TwoSum of the high parts, low parts
+                    // and errors in a second float), scaled once by their
+                    // common value, then the centre by one Dot2 step
+                    float sh = 0.f, se = 0.f;
+                    auto nb = [&](int t) {
+                        if (t == y.dcen || !((m >> t) & 1u)) return;
+                        const S* px = v + (size_t)(i + soff[t]) * R + r;
+                        const Rv x = RO ? A::ldg(px) : A::ldcg(px);
+                        float u, w;
+                        two_sum(sh, x.hi, u, w);
+                        sh = u;
+                        se = __fadd_rn(se, __fadd_rn(w, x.lo));
+                    };
+                    if (y.dk == 7) {
+#pragma unroll
+                        for (int t = 0; t < 7; t++) nb(t);
+                    } else {
+                        for (int t = 0; t < y.dk; t++) nb(t);
+                    }
+                    const S* pc = v + (size_t)i * R + r;
+                    const Rv xc = RO ? A::ldg(pc) : A::ldcg(pc);
+                    const float co = y.dco, p = __fmul_rn(co, sh);
+                    Dot2Acc d{p, __fmaf_rn(co, se, __fmaf_rn(co, sh, -p))};
+                    dot2_add(d, scf[y.dcen], xc);
+                    return dot2_result(d);
+                }
+                Dot2Acc d{0.f, 0.f};
+                for (int t = 0; t < y.dk; t++) {
+                    if (!((m >> t) & 1u)) continue;
+                    const S* px = v + (size_t)(i + soff[t]) * R + r;
+                    dot2_add(d, scf[t], RO ? A::ldg(px) : A::ldcg(px));
+                }
+                return dot2_result(d);
+            }
             for (int t = 0; t < y.dk; t++) {
                 if (!((m >> t) & 1u)) continue;
                 const S* px = v + (size_t)(i + soff[t]) * R + r;
@@ -302,20 +345,6 @@ __device__ __forceinline__ void cta_sum_slots(typename A::R val, int slot, int n
     const int slot = tr < rows_it ? r : kMaxR;                   \
     (void)slot
 
-// One Dot2 step a += v * x for a double-float matrix value v = (v.x, v.y):
-// the high product exactly (FMA TwoProduct) plus the cross terms in the
-// error float; v.y * x.lo is dropped, as in df_fma.
-__device__ __forceinline__ void dot2_add_df(Dot2Acc& a, float2 v, df64 x) {
-    const float p = __fmul_rn(v.x, x.hi);
-    float e = __fmaf_rn(v.x, x.hi, -p);
-    e = __fmaf_rn(v.x, x.lo, e);
-    e = __fmaf_rn(v.y, x.hi, e);
-    float u, w;
-    two_sum(a.s, p, u, w);
-    a.s = u;
-    a.e = __fadd_rn(a.e, __fadd_rn(w, e));
-}
-
 // Init phase: items it0, it0 + itstep, ... of every system.
 template <class A>
 __device__ void ph_init(const BArgs& a, int it0, int itstep) {
@@ -363,7 +392,10 @@ __device__ void ph_init(const BArgs& a, int it0, int itstep) {
 // Level j of every active system (RO: u_j was written by an earlier launch,
 // so the gathers may use the read-only path; inside one cooperative launch
 // they go through L2).
-template <class A, bool RO>
+// KIND: 0 every system; 1 CSR systems only; 2 diagonal-form systems only (the
+// per-phase mode launches the two separately, so each keeps its own register
+// budget).
+template <class A, bool RO, int KIND = 0>
 __device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
     using K = BK<A>;
     using Rv = typename A::R;
@@ -377,6 +409,7 @@ __device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
         const BSys& y = a.sys[k];
         const int state = __ldcg(&a.bctl[k].state);
         if (state == SYS_FINISHED || (state == SYS_EXPORT && (j > 0 || a.tuning))) continue;
+        if ((KIND == 1 && y.dk) || (KIND == 2 && !y.dk)) continue;  // the other kernel's system
         ITEM_MAP(y);
         const int li = it - y.item0;
         const int r0 = li * y.T, r1 = min(y.n, r0 + y.T);
@@ -401,20 +434,26 @@ __device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
         const bool want_m2 = 2 * j + 2 <= 2 * s - 1;
         const Rv dinv_cst = A::from_d(yb.dinv_c);
         Rv m1 = A::zero(), m2 = A::zero();
-        DotAcc d1{0.f, 0.f}, d2{0.f, 0.f};  // double-float: the moments as running Dot2 sums
+        DotAcc d1{0.f, 0.f}, d2{0.f, 0.f};  // diagonal form, double-float: running Dot2 sums
         auto epi = [&](int i, Rv av) {
             const size_t o = (size_t)i * R + r;
-            const Rv ui = RO ? A::ldg(uj + o) : A::ldcg(uj + o);
+            m1 = A::fma(RO ? A::ldg(uj + o) : A::ldcg(uj + o), av, m1);
             const Rv z = A::mul(yb.dinv ? A::ldg(reinterpret_cast<const S*>(yb.dinv) + i) : dinv_cst, av);
             A::st(un + o, z);
+            if (want_m2) m2 = A::fma(av, z, m2);
+        };
+        auto epi_dia = [&](int i, Rv av) {
             if constexpr (A::kind == 1) {
+                const size_t o = (size_t)i * R + r;
+                const Rv ui = RO ? A::ldg(uj + o) : A::ldcg(uj + o);
+                const Rv z = A::mul(dinv_cst, av);  // the diagonal form's D is constant
+                A::st(un + o, z);
                 dot_add(d1, ui, av);
-                dot_add(d2, av, z);
+                dot_add_sq(d2, av);  // av . D^-1 av = dinv_c (av . av), scaled below
                 dot_renorm(d1);
                 dot_renorm(d2);
             } else {
-                m1 = A::fma(ui, av, m1);
-                if (want_m2) m2 = A::fma(av, z, m2);
+                epi(i, av);
             }
         };
         if (!RO || yb.dk) {
@@ -426,9 +465,16 @@ __device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
                 }
                 __syncthreads();
             }
-            for (int i = r0 + tr; tr < rows_it && i < r1; i += rows_it)
-                epi(i, K::template spmv_elem<RO>(yb, s_doff, s_dcf, i, r, uj));
-        } else {
+            for (int i = r0 + tr; tr < rows_it && i < r1; i += rows_it) {
+                if constexpr (KIND == 1) {
+                    epi(i, K::template spmv_elem<RO, false>(yb, s_doff, s_dcf, i, r, uj));
+                } else {
+                    const Rv av = K::template spmv_elem<RO, true>(yb, s_doff, s_dcf, i, r, uj);
+                    if (yb.dk) epi_dia(i, av);
+                    else epi(i, av);
+                }
+            }
+        } else if constexpr (KIND != 2) {
             // CSR: stage each 256-row sub-tile's row pointers, column indices
             // and values in shared memory with coalesced loads; the R threads
             // of a row then read them from there
@@ -451,36 +497,6 @@ __device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
                     else s_vd[q] = __ldg(yb.val + base + q);
                 }
                 __syncthreads();
-                if constexpr (A::kind == 1) {
-                  if (s_rp[rows_t] - base <= kLevelCap) {
-                    // Whole sub-tile staged (the common case): the gathers of
-                    // a row's first kGather entries are issued before any
-                    // arithmetic, from shared-memory columns and values only;
-                    // each row is a Dot2 sum (values in double-float, the
-                    // lo * lo product dropped as in df_fma).
-                    const S* ur = uj + r;
-                    for (int rl = tr; tr < rows_it && rl < rows_t; rl += rows_it) {
-                        const int ks = s_rp[rl] - base, ke = s_rp[rl + 1] - base;
-                        Rv xa[kGather];
-#pragma unroll
-                        for (int t = 0; t < kGather; t++)
-                            if (ks + t < ke) {
-                                const S* px = ur + (size_t)s_col[ks + t] * R;
-                                xa[t] = RO ? A::ldg(px) : A::ldcg(px);
-                            }
-                        Dot2Acc aa{0.f, 0.f};
-#pragma unroll
-                        for (int t = 0; t < kGather; t++)
-                            if (ks + t < ke) dot2_add_df(aa, s_vf[ks + t], xa[t]);
-                        for (int q = ks + kGather; q < ke; q++) {  // longer rows
-                            const S* px = ur + (size_t)s_col[q] * R;
-                            dot2_add_df(aa, s_vf[q], RO ? A::ldg(px) : A::ldcg(px));
-                        }
-                        epi(t0 + rl, dot2_result(aa));
-                    }
-                    continue;
-                  }
-                }
                 for (int rl = tr; tr < rows_it && rl < rows_t; rl += rows_it) {
                     const int ks = s_rp[rl] - base, ke = s_rp[rl + 1] - base;
                     Rv acc = A::zero();
@@ -500,8 +516,10 @@ __device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
             }
         }
         if constexpr (A::kind == 1) {
-            m1 = dot_value(d1);
-            m2 = want_m2 ? dot_value(d2) : A::zero();
+            if (yb.dk) {
+                m1 = dot_value(d1);
+                m2 = want_m2 ? df_mul(dinv_cst, dot_value(d2)) : A::zero();
+            }
         }
         double out = 0.0;
         cta_sum_slots<A>(m1, slot, R, red, &out);
@@ -756,10 +774,10 @@ __global__ void __launch_bounds__(kBThreads) k_bp_init(BArgs a) {
     ph_init<A>(a, blockIdx.x, gridDim.x);
 }
 
-template <class A>
-__global__ void __launch_bounds__(kBThreads, 4) k_bp_level(BArgs a, int j) {
+template <class A, int KIND>
+__global__ void __launch_bounds__(kBThreads) k_bp_level(BArgs a, int j) {
     if (batch_done(a)) return;
-    ph_level<A, true>(a, j, blockIdx.x, gridDim.x);
+    ph_level<A, true, KIND>(a, j, blockIdx.x, gridDim.x);
 }
 
 template <class A>
@@ -793,7 +811,8 @@ struct sscg_batch {
     sscg_ctx* ctx;
     int nsys, s, arith, maxit, total_rhs, nitems, grid, graph_ok;
     int persistent;              // one cooperative launch instead of per-phase launches
-    int g_init, g_level, g_update;  // per-phase grids
+    int g_init, g_level, g_level_dia, g_update;  // per-phase grids (CSR and diagonal-form levels)
+    int has_csr, has_dia;                        // which level kernels an outer step launches
     cudaGraphExec_t step_exec;   // per-phase mode: one outer step
     double tol;
     std::vector<const sscg_mat*> mats;
@@ -953,7 +972,10 @@ int launch_init(sscg_batch* b, int tuning, int maxit, cudaStream_t st) {
 template <class A, int SB>
 int launch_step(sscg_batch* b, int tuning, int maxit, cudaStream_t st) {
     const BArgs a = make_args(b, tuning, maxit);
-    for (int j = 0; j < b->s; j++) k_bp_level<A><<<b->g_level, kBThreads, kLevelSmem, st>>>(a, j);
+    for (int j = 0; j < b->s; j++) {
+        if (b->has_csr) k_bp_level<A, 1><<<b->g_level, kBThreads, kLevelSmem, st>>>(a, j);
+        if (b->has_dia) k_bp_level<A, 2><<<b->g_level_dia, kBThreads, kLevelSmem, st>>>(a, j);
+    }
     k_bp_solve<A><<<std::min(b->nsys, kMaxGrid), kBThreads, 0, st>>>(a);
     k_bp_update<A, SB><<<b->g_update, kBThreads, 0, st>>>(a);
     SSCG_CUDA(b->ctx, cudaGetLastError());
@@ -991,14 +1013,15 @@ int phase_grids(sscg_batch* b) {
         return std::min(kMaxGrid, ctx->sm_count * std::min(per, 8));
     };
     b->g_init = grid_of(k_bp_init<A>);
-    cudaFuncSetAttribute(k_bp_level<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevelSmem);
-    {
+    auto level_grid = [&](auto kernel) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevelSmem);
         int per = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bp_level<A>, kBThreads, kLevelSmem) != cudaSuccess ||
-            per < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBThreads, kLevelSmem) != cudaSuccess || per < 1)
             per = 1;
-        b->g_level = std::min(kMaxGrid, ctx->sm_count * std::min(per, 8));
-    }
+        return std::min(kMaxGrid, ctx->sm_count * std::min(per, 8));
+    };
+    b->g_level = level_grid(k_bp_level<A, 1>);
+    b->g_level_dia = level_grid(k_bp_level<A, 2>);
     b->g_update = grid_of(k_bp_update<A, SB>);
     int per = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<A, SB>, kBThreads, 0);
@@ -1174,7 +1197,7 @@ int run_phases(sscg_batch* b) {
         }
         if (rc) break;
         launched += c;
-        b->last_launches += (int64_t)c * (b->s + 2);  // s levels, the solves, the update
+        b->last_launches += (int64_t)c * (b->s * (b->has_csr + b->has_dia) + 2);  // levels, solves, update
         const int slot = chunk & 1;
         if (cudaMemcpyAsync((void*)(ctx->pinned + slot), &b->d_g->finished, sizeof(int), cudaMemcpyDeviceToHost,
                             st) != cudaSuccess ||
@@ -1247,8 +1270,12 @@ int sscg_batch_create(sscg_ctx* ctx, int nsys, const sscg_mat* const* mats, cons
         const bool f64 = opts->arith == SSCG_ARITH_F64;
         if (m->dia) {
             // constant-coefficient diagonal form: masks, offsets, values; D is one constant
+            b->has_dia = 1;
             y.dmask = m->dia_mask;
             y.dk = m->dia_k;
+            y.dcen = m->dia_cen;
+            y.dlap = m->dia_lap;
+            y.dco = (float)m->dia_co;
             for (int t = 0; t < m->dia_k; t++) {
                 y.doff[t] = m->dia_off[t];
                 y.dcf[t] = (float)m->dia_c[t];
@@ -1258,6 +1285,7 @@ int sscg_batch_create(sscg_ctx* ctx, int nsys, const sscg_mat* const* mats, cons
             y.dinv_c = m->dia_dinv;
             y.diag_c = m->dia_d;
         } else {
+            b->has_csr = 1;
             y.dinv = f64 ? (const void*)m->dinv : (const void*)m->dinv_df;
             y.diag = f64 ? (const void*)m->diag : (const void*)m->diag_df;
         }
