@@ -78,6 +78,7 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-8)
     p.add_argument("--no-pcg", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-sweep", action="store_true", help="skip the s in {1,2,4,6,8} sweep")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--fused-mpk", action="store_true", help="several matrix-powers levels per launch (L2-resident)")
     p.add_argument("--workload", default="poisson", choices=["poisson", "batch", "mixed27", "cheb"],
@@ -366,6 +367,23 @@ def main():
                    pcg_kernel_gbs=round(pcg_bytes(bm, p0.outer_iters) / (pcg_ms * 1e-3) / 1e9, 1),
                    speedup_vs_pcg=round(pcg_ms / ms_per_step, 4))
 
+    # the block sizes of the workload's definition, s in {1, 2, 4, 6, 8}: one
+    # warm-up and two timed solves each (after the timed region)
+    sweep = {}
+    if not a.no_sweep:
+        for sv in (1, 2, 4, 6, 8):
+            if sv == a.s:
+                sweep[str(sv)] = dict(ms=round(ms_per_step, 3), outer=r0.outer_iters, rel_res_true=r0.rel_res_true,
+                                      status=r0.status)
+                continue
+            ssolver = sscg.Solver(A, s=sv, tol=a.tol, maxit=5000, arith=a.arith, fused_mpk=a.fused_mpk)
+            x.zero_()
+            ssolver.solve(b, x)
+            sms, sres = timed(lambda: ssolver.solve(b, x), 2)
+            sweep[str(sv)] = dict(ms=round(max_over_ranks(pg, sum(sms)) / len(sms), 3), outer=sres[-1].outer_iters,
+                                  rel_res_true=sres[-1].rel_res_true, status=sres[-1].status)
+            del ssolver
+
     # end to end through the public API with host buffers
     bh = torch.from_numpy(sysm["b"]).pin_memory()
     xh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -413,6 +431,8 @@ def main():
         }
         if pcg:
             line.update(pcg)
+        if sweep:
+            line["s_sweep"] = sweep
         print(json.dumps(line), flush=True)
     barrier(pg)
 
