@@ -246,6 +246,33 @@ def oracle_sample(sysm, s, budget_s, tol):
     return dict(steps=r.iters, seconds=dt, threads=oracle.num_threads())
 
 
+def hbm_peak():
+    """The measured copy bandwidth (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), \
+            "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def family_roofline(res, bytes_per_record, names):
+    """Roofline of a solve's dominant kernel family from the library's CUDA
+    events (profile=True): bytes_per_record[f] are the algorithmic bytes of one
+    timed record of family f, names[f] its kernels."""
+    fam = {}
+    for f in bytes_per_record:
+        t, c = res.profile[f"t_{f}_ms"], res.profile[f"n_{f}"]
+        if c:
+            fam[f] = (t, c)
+    dom = max(fam, key=lambda f: fam[f][0])
+    t, c = fam[dom]
+    achieved = bytes_per_record[dom] / (t / c * 1e-3) / 1e9
+    peak, src = hbm_peak()
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "kernel": names[dom], "peak_source": src,
+            "family_ms_per_solve": {f: round(v[0], 3) for f, v in fam.items()}}
+
+
 def workload_name(N, s, arith):
     n = N ** 3
     return (f"poisson7 {N}^3 (n={n:,}), CSR FP64 input, Jacobi, s={s} monomial, b=A x_true, x_true~U[-1,1) "
@@ -546,6 +573,27 @@ def run_batch(a, world, rank, local, pg):
         seq = {"seq_ms": round(seq_ms, 3), "seq_status": worst, "speedup_vs_sequential": round(seq_ms / solve_ms, 3)}
         del solvers, xs
 
+    cpu = None
+    if rank == 0:
+        # the oracle beside it: the mix's smallest system, each of its right-hand sides
+        # solved to the same tolerance by the FP64 CPU oracle's s-step PCG on the host cores
+        import oracle
+
+        k0 = min(range(len(spec)), key=lambda k: sizes[k][0])
+        Mo = oracle.as_matrix(dict(zip(("rowptr", "col", "val"), inputs.batch_csr(spec[k0]))))
+        t0 = time.perf_counter()
+        for r in range(R[k0]):
+            oracle.pcgs(Mo, B[k0][r].cpu().numpy(), a.s, tol=a.tol, maxit=5000)
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": round(R[k0] / t_cpu, 2), "unit": "rhs/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"system {k0} of the mix ({spec[k0]['kind']} {spec[k0]['N']}^3, {R[k0]} right-hand "
+                         f"sides, the smallest): {t_cpu:.2f} s"}
+        peak, src = hbm_peak()
+        eff = byts / (statistics.median(ms) * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(eff, 1), "peak": peak, "unit": "GB/s", "frac": round(eff / peak, 4),
+                "traffic": None, "kernel": "whole batched solve (k_bp_level, k_bp_solve, k_bp_update; "
+                                           "algorithmic bytes of every system's levels and updates)",
+                "peak_source": src}
     if rank == 0:
         classes = {}
         for k, (n, _, _) in enumerate(sizes):
@@ -575,6 +623,7 @@ def run_batch(a, world, rank, local, pg):
                      "mode": ("persistent cooperative launch" if a.persistent else
                               "per-phase launches over all systems, CUDA graph per outer step")},
             "gpu_launches": int(launches), "setup_s": round(t_gen, 1), "clocks": clk,
+            "roofline": roof, "cpu_baseline": cpu,
         }
         if seq:
             line.update(seq)
@@ -617,7 +666,7 @@ def run_mixed27(a, world, rank, local, pg):
     x = torch.zeros_like(b)
     out = {}
     for name, kw in (("mixed", dict(arith="mixed", replace_every=1)), ("df64", dict(arith="df64"))):
-        solver = sscg.Solver(A, s=a.s, tol=1e-10, maxit=5000, **kw)
+        solver = sscg.Solver(A, s=a.s, tol=1e-10, maxit=5000, profile=True, **kw)
         x.zero_()
         solver.solve(b, x)
         ms, res, nl = [], None, 0
@@ -632,6 +681,15 @@ def run_mixed27(a, world, rank, local, pg):
             ms.append(e0.elapsed_time(e1))
             nl += res.profile["kernel_launches"]
         xs = x.cpu().numpy()
+        if name == "mixed":
+            sv = a.s
+            # bytes per timed record (the mixed driver times the s levels, the Gram pass and
+            # the update + residual replacement of an outer step as one record each)
+            mixed_roof = family_roofline(
+                res, {"mpk": (20 * sv - 4) * n, "dir": (28 * sv + 8) * n, "update": (44 * sv + 48) * n},
+                {"mpk": "k_mx_level x s (diagonal-form SpMV of the FP32 basis, AU in double-float)",
+                 "dir": "k_gram (G, C, m and q of the direct-Gram blocks)",
+                 "update": "k_mx_update + k_mx_replace (P, AP, x; r = r0 - A(x - x0))"})
         out[name] = dict(ms=statistics.median(ms), outer=res.outer_iters, status=res.status, launches=nl,
                          rel_res_true=res.rel_res_true,
                          err_vs_oracle=float(np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x)),
@@ -648,6 +706,7 @@ def run_mixed27(a, world, rank, local, pg):
                 "mixed": {k: (round(v, 3) if k == "ms" else v) for k, v in m.items()},
                 "df64": {k: (round(v, 3) if k == "ms" else v) for k, v in out["df64"].items()},
                 "speedup_mixed_vs_df64": round(out["df64"]["ms"] / m["ms"], 3),
+                "roofline": mixed_roof,
                 "gpu_launches": int(m["launches"]),
                 "cpu_baseline": {"value": round(t_oracle * 1e3, 1), "unit": "ms", "cores": oracle.num_threads(),
                                  "kind": "oracle",
@@ -712,7 +771,7 @@ def run_cheb(a, world, rank, local, pg):
                 else:
                     A.set_bounds_model(net.h, None)
                 basis = "monomial" if name == "monomial" else "chebyshev"
-                solver = sscg.Solver(A, s=s, basis=basis, tol=1e-8, maxit=4000)
+                solver = sscg.Solver(A, s=s, basis=basis, tol=1e-8, maxit=4000, profile=True)
 
                 def go():
                     x.zero_()
@@ -721,6 +780,16 @@ def run_cheb(a, world, rank, local, pg):
                 r, ms = timed(go)
                 row[name] = {"ms": round(ms, 3), "status": r.status, "outer": r.outer_iters,
                              "rel_res_true": r.rel_res_true, "launches": r.profile["kernel_launches"]}
+                if name == "network" and sig == 3.0 and s == 8:
+                    nn, nz = A.n, len(c[1])
+                    Mb = 4 * (nn + 1) + 12 * nz  # CSR: int32 columns, double-float values
+                    cheb_roof = family_roofline(
+                        r, {"mpk": s * (Mb + 32 * nn), "dir": (24 * s + 8) * nn, "update": (48 * s + 48) * nn},
+                        {"mpk": "k_level_gen x s (CSR SpMV, AU stored, Chebyshev recurrence)",
+                         "dir": "k_gram (G, C, m of the direct-Gram blocks)",
+                         "update": "k_update_tma (P, AP, x, r, z)"})
+                    cheb_roof["workload"] = f"sigma=3 field {N}^3, Chebyshev basis s=8, network interval"
+                    cheb_csr = c
             A.set_bounds_model(net.h, None)
             (lo, hi), t_net = timed(lambda: net.bounds(A, blob))
             (llo, lhi), t_lz = timed(lambda: A.estimate_bounds(20))
@@ -729,6 +798,19 @@ def run_cheb(a, world, rank, local, pg):
             rows.append(row)
         A.close()
     if rank == 0:
+        # the oracle beside it: the two interval computations on the host cores for the
+        # sigma = 3 field (features + forward pass of the same network, 20 Lanczos steps)
+        import oracle
+
+        Mo = oracle.as_matrix(dict(rowptr=cheb_csr[0], col=cheb_csr[1], val=cheb_csr[2]))
+        st = net.state()
+        t0 = time.perf_counter()
+        f = oracle.features(Mo)
+        oracle.mlp_forward(st["d"], st["h"], st["o"], st["theta"], ((f - st["x_mean"]) / st["x_std"])[None, :])
+        t_net_cpu = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.lanczos_bounds(Mo, inputs.uniform(91, N ** 3), 20)
+        t_lz_cpu = time.perf_counter() - t0
         ok = [r for r in rows if r["network"]["status"] == 0 and r["lanczos"]["status"] == 0]
         gain = [r["lanczos"]["ms"] / r["network"]["ms"] for r in ok]
         line = {"metric": CHEB_METRIC, "value": round(statistics.median(gain), 3) if gain else None,
@@ -741,6 +823,12 @@ def run_cheb(a, world, rank, local, pg):
                                        f"Lanczos, {len(hist)} Adam epochs, {t_train:.1f} s",
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": int(sum(r["network"]["launches"] + r["lanczos"]["launches"] for r in rows)),
+                "roofline": cheb_roof,
+                "cpu_baseline": {"value": round(t_lz_cpu / t_net_cpu, 3),
+                                 "unit": "x (oracle 20-step Lanczos time / oracle features + network time)",
+                                 "cores": oracle.num_threads(), "kind": "oracle",
+                                 "sample": f"sigma=3 field {N}^3: oracle features + forward {t_net_cpu * 1e3:.1f} ms, "
+                                           f"oracle 20-step Lanczos {t_lz_cpu * 1e3:.1f} ms"},
                 "rows": rows}
         print(json.dumps(line), flush=True)
     barrier(pg)
