@@ -148,6 +148,20 @@ __device__ __forceinline__ float2 widen<float2, float>(float v) {
     return make_float2(v, 0.f);
 }
 
+// Asynchronous global -> shared element copies (cp.async), zero-filled past
+// src_bytes; completion tracked per thread by commit groups.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // TB: element type of the basis columns U (the new block's first s
 // columns, or `ublk` when given); AU (`au`, s columns), r and the old block
 // use A::S.  The
@@ -182,33 +196,61 @@ __global__ void __launch_bounds__(kThreads) k_gram(int n, int ldn, int s, const 
     }
     const size_t ld = (size_t)ldn;
     const int ntiles = (n + kGramTile - 1) / kGramTile;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int r0 = t * kGramTile;
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < g.ncols * kGramTile; idx += blockDim.x) {
-            int c = idx / kGramTile, i = idx % kGramTile, row = r0 + i;
-            S v;
-            if (row >= n) memset(&v, 0, sizeof(S));
-            else if (c < s) v = ublk ? widen<S, TB>(ublk[c * ld + row]) : blk_new[c * ld + row];
-            else if (c < 2 * s) v = au[(c - s) * ld + row];
-            else if (c == 2 * s) v = r[row];
-            else if (c <= 3 * s) v = blk_old[(s + (c - 2 * s - 1)) * ld + row];
-            else v = blk_old[(c - 3 * s - 1) * ld + row];
-            tile[c * LD + i] = v;
+    // Two tile buffers: the next tile's columns are copied global -> shared by
+    // cp.async (8 bytes an element; 4 for an FP32 basis element, whose low
+    // float stays zero) while the current one is summed.  Rows past n are
+    // zero-filled by the copies themselves.
+    const int tstride = g.ncols * LD;
+    if (ublk) {
+        for (int idx = threadIdx.x; idx < 2 * s * LD; idx += blockDim.x) {
+            const int bsel = idx / (s * LD), rem = idx % (s * LD);
+            reinterpret_cast<float*>(tile + bsel * tstride + rem)[1] = 0.f;
         }
+    }
+    auto stage = [&](int t, int b) {
+        const int r0 = t * kGramTile;
+        S* tl = tile + b * tstride;
+        for (int idx = threadIdx.x; idx < g.ncols * kGramTile; idx += blockDim.x) {
+            const int c = idx / kGramTile, i = idx % kGramTile, row = r0 + i;
+            const int ok = row < n;
+            const size_t rr = ok ? (size_t)row : 0;
+            if (c < s && ublk) {
+                cp_async4(tl + c * LD + i, ublk + c * ld + rr, ok ? 4 : 0);
+            } else {
+                const S* src;
+                if (c < s) src = blk_new + c * ld + rr;
+                else if (c < 2 * s) src = au + (c - s) * ld + rr;
+                else if (c == 2 * s) src = r + rr;
+                else if (c <= 3 * s) src = blk_old + (s + (c - 2 * s - 1)) * ld + rr;
+                else src = blk_old + (c - 3 * s - 1) * ld + rr;
+                cp_async8(tl + c * LD + i, src, ok ? 8 : 0);
+            }
+        }
+    };
+    int buf = 0;
+    if (blockIdx.x < ntiles) stage(blockIdx.x, 0);
+    cp_async_commit();
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (t + (int)gridDim.x < ntiles) stage(t + gridDim.x, buf ^ 1);
+        cp_async_commit();
+        cp_async_wait_prior();  // every group but the newest: tile t is in
         __syncthreads();
+        const S* tile_t = tile + buf * tstride;
         if (threadIdx.x < active) {
 #pragma unroll
             for (int q = 0; q < kMaxEPT; q++) {
                 if (e0 + q * kThreads >= g.E) break;
-                const S* ta = tile + ea[q] * LD;
-                const S* tb = tile + eb[q] * LD;
+                const S* ta = tile_t + ea[q] * LD;
+                const S* tb = tile_t + eb[q] * LD;
                 R a = acc[q];
                 for (int i = grp; i < kGramTile; i += groups) a = A::fma(A::ld(ta + i), A::ld(tb + i), a);
                 acc[q] = a;
             }
         }
+        __syncthreads();  // tile t is read: its buffer takes tile t + 2 gridDim.x next
+        buf ^= 1;
     }
+    cp_async_wait_all();
     // combine the row groups of each entry, then one partial per entry
     __syncthreads();
     double* red = reinterpret_cast<double*>(smem);  // kThreads doubles (tile is free now)

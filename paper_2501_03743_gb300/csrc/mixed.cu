@@ -304,7 +304,7 @@ int run_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     const size_t smem_df = DM != 0 ? 0 : pipe_bytes<VM, kStages>(cap) + 128;
     const size_t smem64 = stage_bytes<ArithF64, VAL_F64>(cap);
     const GramShape gs_full = gram_shape(s, 1, 1);
-    const size_t smem_gram = std::max({(size_t)gs_full.ncols * (kGramTile + 1) * sizeof(float2), sizeof(SmallScratch),
+    const size_t smem_gram = std::max({2 * (size_t)gs_full.ncols * (kGramTile + 1) * sizeof(float2), sizeof(SmallScratch),
                                        (size_t)kThreads * sizeof(double)});
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<ArithDF64, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem_init));

@@ -87,7 +87,7 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
     const size_t smem64 = stage_bytes<ArithF64, VAL_F64>(cap);
     const size_t smem_pipe = pipe_bytes<VM, kStages>(cap) + 128;
     const GramShape gs_full = gram_shape(s, 1);
-    const size_t smem_gram = std::max({(size_t)gs_full.ncols * (kGramTile + 1) * sizeof(S), sizeof(SmallScratch),
+    const size_t smem_gram = std::max({2 * (size_t)gs_full.ncols * (kGramTile + 1) * sizeof(S), sizeof(SmallScratch),
                                        (size_t)kThreads * sizeof(double)});
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<A, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const size_t smem_lv = DM != 0 ? 0 : smem_pipe;  // the diagonal form stages nothing
