@@ -272,13 +272,14 @@ struct BK {
                     dot2_add(d, scf[t], RO ? A::ldg(px) : A::ldcg(px));
                 }
                 return dot2_result(d);
-            }
-            for (int t = 0; t < y.dk; t++) {
-                if (!((m >> t) & 1u)) continue;
-                const S* px = v + (size_t)(i + soff[t]) * R + r;
-                const Rv x = RO ? A::ldg(px) : A::ldcg(px);
-                if constexpr (A::kind == 1) acc = df_fma_f(x, scf[t], acc);
-                else acc = ::fma((double)scf[t], x, acc);
+            } else {
+                for (int t = 0; t < y.dk; t++) {
+                    if (!((m >> t) & 1u)) continue;
+                    const S* px = v + (size_t)(i + soff[t]) * R + r;
+                    const Rv x = RO ? A::ldg(px) : A::ldcg(px);
+                    if constexpr (A::kind == 1) acc = df_fma_f(x, scf[t], acc);
+                    else acc = ::fma((double)scf[t], x, acc);
+                }
             }
             return acc;
         }
@@ -1125,7 +1126,6 @@ int autotune(sscg_batch* b) {
 // (s level launches, the solve launch, the update launch) for the per-phase
 // mode.  On a capture failure the plan launches directly.
 void build_graph(sscg_batch* b) {
-    sscg_ctx* ctx = b->ctx;
     // capture on a private stream: the context's stream may be the legacy
     // default stream, which cannot be captured; the graph is replayed on it
     cudaStream_t st = nullptr;

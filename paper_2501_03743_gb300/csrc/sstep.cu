@@ -132,22 +132,9 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
     return v;
 }
 
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-
-// Barrier 1 among the 256 consumer threads only (the producer warp is busy).
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 constexpr int kFuseStages = 2;
 constexpr int kFuseThreads = kThreads + 32;  // 8 consumer warps + 1 producer warp
@@ -373,8 +360,6 @@ struct Layout {
     double* xdev;
     size_t bytes;
 };
-
-int max_grid(const sscg_ctx* ctx) { return ctx->sm_count * 8; }
 
 Layout plan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t cap) {
     Layout L{};
