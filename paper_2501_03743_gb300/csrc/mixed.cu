@@ -133,22 +133,25 @@ __global__ void __launch_bounds__(kThreads) k_mx_update(int n, int ldn, int s, f
     const size_t ld = (size_t)ldn;
     df64 rr = df_make(0.f, 0.f);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        df64 po[SB], apo[SB];
-        if (!first) {
+        // every load of the row is issued (L2 path) before its arithmetic
+        df64 po[SB], apo[SB], uu[SB], au[SB];
 #pragma unroll
-            for (int l = 0; l < SB; l++)
-                if (l < s) {
-                    float2 a = p_old[l * ld + i], b = p_old[(s + l) * ld + i];
-                    po[l] = df_make(a.x, a.y);
-                    apo[l] = df_make(b.x, b.y);
+        for (int l = 0; l < SB; l++)
+            if (l < s) {
+                const float2 a = __ldcg(aublk + l * ld + i);
+                uu[l] = df_make(__ldcg(ublk + l * ld + i), 0.f);
+                au[l] = df_make(a.x, a.y);
+                if (!first) {
+                    const float2 b = __ldcg(p_old + l * ld + i), c = __ldcg(p_old + (s + l) * ld + i);
+                    po[l] = df_make(b.x, b.y);
+                    apo[l] = df_make(c.x, c.y);
                 }
-        }
+            }
         df64 xa = df_make(0.f, 0.f), ra = df_make(0.f, 0.f);
 #pragma unroll
         for (int jj = 0; jj < SB; jj++) {
             if (jj < s) {
-                float2 a = aublk[jj * ld + i];
-                df64 p = df_make(ublk[jj * ld + i], 0.f), ap = df_make(a.x, a.y);
+                df64 p = uu[jj], ap = au[jj];
                 if (!first) {
 #pragma unroll
                     for (int l = 0; l < SB; l++)
@@ -157,8 +160,8 @@ __global__ void __launch_bounds__(kThreads) k_mx_update(int n, int ldn, int s, f
                             ap = df_fma(apo[l], sb[l + jj * SB], ap);
                         }
                 }
-                p_new[jj * ld + i] = make_float2(p.hi, p.lo);
-                p_new[(s + jj) * ld + i] = make_float2(ap.hi, ap.lo);
+                __stcs(p_new + jj * ld + i, make_float2(p.hi, p.lo));  // read again only next step
+                __stcs(p_new + (s + jj) * ld + i, make_float2(ap.hi, ap.lo));
                 xa = df_fma(p, sa[jj], xa);
                 ra = df_fma(ap, sa[jj], ra);
             }

@@ -8,6 +8,8 @@
 // remainder straight from global memory.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -328,8 +330,9 @@ __device__ __forceinline__ void spmv_dia_lap(const MatView& M, const TX* __restr
             const TX* a = x + (i + M.doff[t]);
             const df64 v0 = DiaVec<TX>::ld(a), v1 = DiaVec<TX>::ld(a + 1);
             const bool b0 = (mm.x >> t) & 1u, b1 = (mm.y >> t) & 1u;
-            const float h0 = b0 ? v0.hi : 0.f, l0 = b0 ? v0.lo : 0.f;
-            const float h1 = b1 ? v1.hi : 0.f, l1 = b1 ? v1.lo : 0.f;
+            constexpr bool kLo = !std::is_same<TX, float>::value;  // FP32 elements have no low part
+            const float h0 = b0 ? v0.hi : 0.f, l0 = kLo && b0 ? v0.lo : 0.f;
+            const float h1 = b1 ? v1.hi : 0.f, l1 = kLo && b1 ? v1.lo : 0.f;
             if (t == 0) {  // the first term starts the sums
                 s0 = h0;
                 e0 = l0;
@@ -339,10 +342,10 @@ __device__ __forceinline__ void spmv_dia_lap(const MatView& M, const TX* __restr
                 float u, w;
                 two_sum(s0, h0, u, w);
                 s0 = u;
-                e0 = __fadd_rn(e0, __fadd_rn(w, l0));
+                e0 = __fadd_rn(e0, kLo ? __fadd_rn(w, l0) : w);
                 two_sum(s1, h1, u, w);
                 s1 = u;
-                e1 = __fadd_rn(e1, __fadd_rn(w, l1));
+                e1 = __fadd_rn(e1, kLo ? __fadd_rn(w, l1) : w);
             }
         }
         df64 c0, c1;
