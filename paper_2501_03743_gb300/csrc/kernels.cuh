@@ -339,6 +339,107 @@ __global__ void __launch_bounds__(kUpdRows) k_update_tma(int n, int ldn, int s, 
     }
 }
 
+// The same update (U, AU, P_old, AP_old, r, 1/diag in; P, AP, x, r and z out)
+// with each thread taking whole rows (grid-stride) and issuing every load of
+// a row through L2 before its arithmetic; P and AP are written with streaming
+// stores (read again only in the next step).  Used by the direct-Gram path
+// for s <= 8 (the row's 4s values stay in registers).
+template <class A, int SB>
+__global__ void __launch_bounds__(kThreads) k_update_ap(int n, int ldn, int s, typename A::S* __restrict__ blk_new,
+                                                        typename A::S* __restrict__ blk_old,
+                                                        typename A::S* __restrict__ x, typename A::S* __restrict__ r,
+                                                        const typename A::S* __restrict__ dinv,
+                                                        double* __restrict__ part, int first, int write_z,
+                                                        Ctrl* ctrl, double* __restrict__ hist) {
+    using R = typename A::R;
+    using S = typename A::S;
+    if (ctrl_done(ctrl)) return;
+    __shared__ R sb[SB * SB];
+    __shared__ R sa[SB];
+    __shared__ double red[2 * (kThreads / 32)];
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) sb[(e % s) + (e / s) * SB] = A::from_d(ctrl->beta[e]);
+    for (int e = threadIdx.x; e < s; e += blockDim.x) sa[e] = A::from_d(ctrl->alpha[e]);
+    __syncthreads();
+    const size_t ld = (size_t)ldn;
+    R rr = A::zero(), rz = A::zero();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        R u[SB], au[SB], po[SB], apo[SB];
+#pragma unroll
+        for (int l = 0; l < SB; l++)
+            if (l < s) {
+                u[l] = A::ldcg(blk_new + l * ld + i);
+                au[l] = A::ldcg(blk_new + (s + l) * ld + i);
+                if (!first) {
+                    po[l] = A::ldcg(blk_old + l * ld + i);
+                    apo[l] = A::ldcg(blk_old + (s + l) * ld + i);
+                }
+            }
+        const R r0 = A::ldcg(r + i), x0 = A::ldcg(x + i);
+        const R dv = dinv ? A::ldcg(dinv + i) : A::zero();
+        R xa = A::zero(), ra = A::zero();
+#pragma unroll
+        for (int jj = 0; jj < SB; jj++) {
+            if (jj < s) {
+                R p = u[jj], ap = au[jj];
+                if (!first) {
+#pragma unroll
+                    for (int l = 0; l < SB; l++)
+                        if (l < s) {
+                            const R b = sb[l + jj * SB];
+                            p = A::fma(po[l], b, p);
+                            ap = A::fma(apo[l], b, ap);
+                        }
+                }
+                A::st_stream(blk_new + jj * ld + i, p);
+                A::st_stream(blk_new + (s + jj) * ld + i, ap);
+                xa = A::fma(p, sa[jj], xa);
+                ra = A::fma(ap, sa[jj], ra);
+            }
+        }
+        const R xn = A::add(x0, xa);
+        const R rn = A::sub(r0, ra);
+        A::st(x + i, xn);
+        A::st(r + i, rn);
+        rr = A::fma(rn, rn, rr);
+        if (write_z) {
+            const R z = dinv ? A::mul(dv, rn) : rn;
+            A::st(blk_old + i, z);  // U_1 of the next step (P_old_1 of this row is already read)
+            rz = A::fma(rn, z, rz);
+        }
+    }
+    R v[2] = {rr, rz};
+    double out[2];
+    block_sum<A, 2>(v, red, out);
+    const int G = gridDim.x;
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = out[0];
+        part[G + blockIdx.x] = out[1];
+    }
+    if (!last_cta(&ctrl->ticket[2])) return;
+    __shared__ double sh[32];
+    double srr = cta_sum_partials(part, G, sh);
+    double srz = cta_sum_partials(part + G, G, sh);
+    if (threadIdx.x == 0) {
+        int step = ctrl->step + 1;
+        double rel = sqrt(srr) / ctrl->bnorm;
+        ctrl->step = step;
+        ctrl->relres = rel;
+        ctrl->mu[0] = srz;
+        hist[step] = rel;
+        ctrl->nhist = step + 1;
+        if (!isfinite(rel)) {
+            ctrl->status = 2;
+            ctrl->done = 1;
+        } else if (rel < ctrl->tol) {
+            ctrl->status = 0;
+            ctrl->done = 1;
+        } else if (step >= ctrl->maxit) {
+            ctrl->status = 1;
+            ctrl->done = 1;
+        }
+    }
+}
+
 // Launch geometry of k_update_tma: dynamic shared memory and a persistent
 // grid from the occupancy of its 128-thread CTAs.
 template <class A, int SB>

@@ -101,6 +101,7 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
     size_t smem_upd = 0;
     int Gu = 0;
     if (int e = update_tma_setup<A, SB>(ctx, n, s, &smem_upd, &Gu)) return e;
+    const int Ga = occupancy_grid(ctx, k_update_ap<A, SB>, 0, n);
     const int Ge = occupancy_grid(ctx, k_combine<A>, 0, n);
     const int Gt = occupancy_grid(ctx, k_true_res, smem64, n);
     const bool diag = mat->prec != SSCG_PREC_CHEB;
@@ -153,8 +154,12 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
                                                              bo, k > 0 ? 1 : 0, 0, L.part, k, L.ctrl);
             P.end(FAM_DIR, k);
             P.begin();
-            k_update_tma<A, SB><<<Gu, kUpdRows, smem_upd, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dvec, L.part,
-                                                                k == 0, diag ? 1 : 0, L.ctrl, L.hist);
+            if constexpr (SB <= 8)
+                k_update_ap<A, SB><<<Ga, kThreads, 0, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dvec, L.part, k == 0,
+                                                             diag ? 1 : 0, L.ctrl, L.hist);
+            else
+                k_update_tma<A, SB><<<Gu, kUpdRows, smem_upd, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dvec, L.part,
+                                                                    k == 0, diag ? 1 : 0, L.ctrl, L.hist);
             if (!diag) P.launches += cheb.apply(M, dvec, r, bo, tmp, ld, Ge, Gl, smem_pipe, st, L.ctrl);
             P.end(FAM_UPDATE, k);
         }
