@@ -787,7 +787,7 @@ def run_cheb(a, world, rank, local, pg):
                         r, {"mpk": s * (Mb + 32 * nn), "dir": (24 * s + 8) * nn, "update": (48 * s + 48) * nn},
                         {"mpk": "k_level_gen x s (CSR SpMV, AU stored, Chebyshev recurrence)",
                          "dir": "k_gram (G, C, m of the direct-Gram blocks)",
-                         "update": "k_update_tma (P, AP, x, r, z)"})
+                         "update": "k_update_ap (P, AP, x, r, z; s <= 8)"})
                     cheb_roof["workload"] = f"sigma=3 field {N}^3, Chebyshev basis s=8, network interval"
                     cheb_csr = c
             A.set_bounds_model(net.h, None)
