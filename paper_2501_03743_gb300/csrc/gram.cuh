@@ -138,16 +138,6 @@ __device__ __forceinline__ void gram_entry(const GramShape& g, int e, int& a, in
 
 constexpr int kGramTile = 128;  // rows staged per tile
 
-// Widening of a staged element to the arithmetic's storage type.
-template <class S, class TB>
-__device__ __forceinline__ S widen(TB v) {
-    return v;
-}
-template <>
-__device__ __forceinline__ float2 widen<float2, float>(float v) {
-    return make_float2(v, 0.f);
-}
-
 // Asynchronous global -> shared element copies (cp.async), zero-filled past
 // src_bytes; completion tracked per thread by commit groups.
 __device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
@@ -207,24 +197,27 @@ __global__ void __launch_bounds__(kThreads) k_gram(int n, int ldn, int s, const 
             reinterpret_cast<float*>(tile + bsel * tstride + rem)[1] = 0.f;
         }
     }
+    // column bases, once per CTA; a thread then copies one fixed row of a tile
+    // (i = threadIdx.x mod 128) for every second column (blockDim.x = 256)
+    __shared__ const void* s_src[4 * kMaxS + 2];
+    for (int c = threadIdx.x; c < g.ncols; c += blockDim.x) {
+        const void* p;
+        if (c < s) p = ublk ? static_cast<const void*>(ublk + c * ld) : static_cast<const void*>(blk_new + c * ld);
+        else if (c < 2 * s) p = au + (c - s) * ld;
+        else if (c == 2 * s) p = r;
+        else if (c <= 3 * s) p = blk_old + (s + (c - 2 * s - 1)) * ld;
+        else p = blk_old + (c - 3 * s - 1) * ld;
+        s_src[c] = p;
+    }
+    __syncthreads();
     auto stage = [&](int t, int b) {
-        const int r0 = t * kGramTile;
-        S* tl = tile + b * tstride;
-        for (int idx = threadIdx.x; idx < g.ncols * kGramTile; idx += blockDim.x) {
-            const int c = idx / kGramTile, i = idx % kGramTile, row = r0 + i;
-            const int ok = row < n;
-            const size_t rr = ok ? (size_t)row : 0;
-            if (c < s && ublk) {
-                cp_async4(tl + c * LD + i, ublk + c * ld + rr, ok ? 4 : 0);
-            } else {
-                const S* src;
-                if (c < s) src = blk_new + c * ld + rr;
-                else if (c < 2 * s) src = au + (c - s) * ld + rr;
-                else if (c == 2 * s) src = r + rr;
-                else if (c <= 3 * s) src = blk_old + (s + (c - 2 * s - 1)) * ld + rr;
-                else src = blk_old + (c - 3 * s - 1) * ld + rr;
-                cp_async8(tl + c * LD + i, src, ok ? 8 : 0);
-            }
+        const int i = threadIdx.x % kGramTile, row = t * kGramTile + i;
+        const int ok = row < n;
+        const size_t rr = ok ? (size_t)row : 0;
+        S* dst = tile + b * tstride + i;
+        for (int c = threadIdx.x / kGramTile; c < g.ncols; c += blockDim.x / kGramTile) {
+            if (ublk && c < s) cp_async4(dst + c * LD, static_cast<const TB*>(s_src[c]) + rr, ok ? 4 : 0);
+            else cp_async8(dst + c * LD, static_cast<const S*>(s_src[c]) + rr, ok ? 8 : 0);
         }
     };
     int buf = 0;
