@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kUpdRows) k_update_tma(int n, int ldn, int s, 
 // stores (read again only in the next step).  Used by the direct-Gram path
 // for s <= 8 (the row's 4s values stay in registers).
 template <class A, int SB>
-__global__ void __launch_bounds__(kThreads) k_update_ap(int n, int ldn, int s, typename A::S* __restrict__ blk_new,
+__global__ void __launch_bounds__(kThreads, 2) k_update_ap(int n, int ldn, int s, typename A::S* __restrict__ blk_new,
                                                         typename A::S* __restrict__ blk_old,
                                                         typename A::S* __restrict__ x, typename A::S* __restrict__ r,
                                                         const typename A::S* __restrict__ dinv,
