@@ -321,33 +321,43 @@ __device__ __forceinline__ void spmv_dia_lap(const MatView& M, const TX* __restr
     const float cc = (float)M.dc[C], co = M.dco;
     const int n = M.n;
     const int stride = 2 * gridDim.x * blockDim.x;
+    // offsets other than the centre and its two neighbours in the sorted order
+    // (the +/-1 of a grid): in a warp whose rows all hold them, their terms are
+    // summed without the mask select (rows at the grid's far faces are rare;
+    // the +/-1 terms stay masked)
+    constexpr uint32_t kFar = ((K >= 32 ? 0xffffffffu : ((1u << K) - 1u))) & ~(7u << (C - 1));
     for (int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x); i < n; i += stride) {
         const uint2 mm = __ldg(reinterpret_cast<const uint2*>(M.dmask + i));
         float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f;
+        auto sums = [&](auto far_all) {
 #pragma unroll
-        for (int t = 0; t < K; t++) {
-            if (t == C) continue;
-            const TX* a = x + (i + M.doff[t]);
-            const df64 v0 = DiaVec<TX>::ld(a), v1 = DiaVec<TX>::ld(a + 1);
-            const bool b0 = (mm.x >> t) & 1u, b1 = (mm.y >> t) & 1u;
-            constexpr bool kLo = !std::is_same<TX, float>::value;  // FP32 elements have no low part
-            const float h0 = b0 ? v0.hi : 0.f, l0 = kLo && b0 ? v0.lo : 0.f;
-            const float h1 = b1 ? v1.hi : 0.f, l1 = kLo && b1 ? v1.lo : 0.f;
-            if (t == 0) {  // the first term starts the sums
-                s0 = h0;
-                e0 = l0;
-                s1 = h1;
-                e1 = l1;
-            } else {
-                float u, w;
-                two_sum(s0, h0, u, w);
-                s0 = u;
-                e0 = __fadd_rn(e0, kLo ? __fadd_rn(w, l0) : w);
-                two_sum(s1, h1, u, w);
-                s1 = u;
-                e1 = __fadd_rn(e1, kLo ? __fadd_rn(w, l1) : w);
+            for (int t = 0; t < K; t++) {
+                if (t == C) continue;
+                const TX* a = x + (i + M.doff[t]);
+                const df64 v0 = DiaVec<TX>::ld(a), v1 = DiaVec<TX>::ld(a + 1);
+                const bool all = decltype(far_all)::value && ((kFar >> t) & 1u);
+                const bool b0 = all || ((mm.x >> t) & 1u), b1 = all || ((mm.y >> t) & 1u);
+                constexpr bool kLo = !std::is_same<TX, float>::value;  // FP32 elements have no low part
+                const float h0 = b0 ? v0.hi : 0.f, l0 = kLo && b0 ? v0.lo : 0.f;
+                const float h1 = b1 ? v1.hi : 0.f, l1 = kLo && b1 ? v1.lo : 0.f;
+                if (t == 0) {  // the first term starts the sums
+                    s0 = h0;
+                    e0 = l0;
+                    s1 = h1;
+                    e1 = l1;
+                } else {
+                    float u, w;
+                    two_sum(s0, h0, u, w);
+                    s0 = u;
+                    e0 = __fadd_rn(e0, kLo ? __fadd_rn(w, l0) : w);
+                    two_sum(s1, h1, u, w);
+                    s1 = u;
+                    e1 = __fadd_rn(e1, kLo ? __fadd_rn(w, l1) : w);
+                }
             }
-        }
+        };
+        if (__all_sync(__activemask(), ((mm.x & mm.y) & kFar) == kFar)) sums(std::true_type{});
+        else sums(std::false_type{});
         df64 c0, c1;
         DiaVec<TX>::ld_pair(x + i, c0, c1);
         // co * (s + e): its high part exactly as p + fma residue, e scaled into the error float
