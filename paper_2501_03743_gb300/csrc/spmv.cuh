@@ -36,6 +36,7 @@ struct MatView {
     int dcen;   // index of offset 0
     int dlap;   // every off-centre coefficient equals dco
     float dco;  // that coefficient
+    int deven;  // every offset beyond the centre's two sorted neighbours is even
 };
 
 // The kernels' view of a matrix: its CSR arrays and, when it has one, its
@@ -58,6 +59,9 @@ inline MatView mat_view(const sscg_mat* m) {
     v.dcen = m->dia_cen;
     v.dlap = m->dia_lap;
     v.dco = (float)m->dia_co;
+    v.deven = 1;
+    for (int t = 0; t < v.dk; t++)
+        if ((t < m->dia_cen - 1 || t > m->dia_cen + 1) && (v.doff[t] & 1)) v.deven = 0;
     return v;
 }
 
@@ -329,13 +333,20 @@ __device__ __forceinline__ void spmv_dia_lap(const MatView& M, const TX* __restr
     for (int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x); i < n; i += stride) {
         const uint2 mm = __ldg(reinterpret_cast<const uint2*>(M.dmask + i));
         float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f;
-        auto sums = [&](auto far_all) {
+        auto sums = [&](auto far_all, auto even) {
 #pragma unroll
             for (int t = 0; t < K; t++) {
                 if (t == C) continue;
                 const TX* a = x + (i + M.doff[t]);
-                const df64 v0 = DiaVec<TX>::ld(a), v1 = DiaVec<TX>::ld(a + 1);
-                const bool all = decltype(far_all)::value && ((kFar >> t) & 1u);
+                const bool far = (kFar >> t) & 1u;
+                df64 v0, v1;
+                if (decltype(even)::value && far) {
+                    DiaVec<TX>::ld_pair(a, v0, v1);  // i and the offset even: one aligned pair load
+                } else {
+                    v0 = DiaVec<TX>::ld(a);
+                    v1 = DiaVec<TX>::ld(a + 1);
+                }
+                const bool all = decltype(far_all)::value && far;
                 const bool b0 = all || ((mm.x >> t) & 1u), b1 = all || ((mm.y >> t) & 1u);
                 constexpr bool kLo = !std::is_same<TX, float>::value;  // FP32 elements have no low part
                 const float h0 = b0 ? v0.hi : 0.f, l0 = kLo && b0 ? v0.lo : 0.f;
@@ -356,8 +367,12 @@ __device__ __forceinline__ void spmv_dia_lap(const MatView& M, const TX* __restr
                 }
             }
         };
-        if (__all_sync(__activemask(), ((mm.x & mm.y) & kFar) == kFar)) sums(std::true_type{});
-        else sums(std::false_type{});
+        if (__all_sync(__activemask(), ((mm.x & mm.y) & kFar) == kFar)) {
+            if (M.deven) sums(std::true_type{}, std::true_type{});
+            else sums(std::true_type{}, std::false_type{});
+        } else {
+            sums(std::false_type{}, std::false_type{});
+        }
         df64 c0, c1;
         DiaVec<TX>::ld_pair(x + i, c0, c1);
         // co * (s + e): its high part exactly as p + fma residue, e scaled into the error float
