@@ -1,0 +1,55 @@
+"""Host logic of bench.py (no GPU): the byte models behind the roofline and
+the yardstick, the measured-traffic lookup and the dominant-family roofline."""
+import os
+import sys
+from types import SimpleNamespace
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_byte_model_zq_update_and_diagonal_level():
+    n, nnz, s = 1000, 6400, 4
+    V = 8 * n
+    bm = bench.byte_model(n, nnz, 4, s, "df64", fused=False, dia=True)
+    # z / Q update with a constant diagonal: U_1..U_{s+1}, P_old, Q_old, x in; P, Q, x, z out
+    assert bm["update"] == (5 * s + 4) * V
+    # a diagonal-form level: the masks, u_j gathered, u_{j+1} written
+    assert bm["level_avg"] == 4 * n + 2 * V
+    csr = bench.byte_model(n, nnz, 4, s, "df64", fused=False, dia=False)
+    M = 4 * (n + 1) + nnz * 8
+    assert csr["level_avg"] == M + 3 * V and csr["update"] == (5 * s + 5) * V
+
+
+def test_yardstick_is_fixed_algorithm3_bytes():
+    n, nnz, s = 4096, 27000, 4
+    y = bench.yardstick(n, nnz, s)
+    V, M = 8 * n, 4 * (n + 1) + 12 * nnz
+    # Algorithm 3 on CSR FP64: every level reads A and u_j, writes A u_j (and u_{j+1} but the last)
+    assert y["level"] == [M + 2 * V + 2 * V] * (s - 1) + [M + 2 * V]
+    assert y["update"] == (6 * s + 6) * V
+    # independent of how the library stores the matrix
+    assert bench.yardstick(n, nnz, s) == bench.byte_model(n, nnz, 8, s, "f64", fused=True, dia=False)
+
+
+def test_traffic_only_for_the_captured_configuration():
+    a = SimpleNamespace(s=4, arith="df64", fused_mpk=False)
+    t = bench.traffic(a, "update", 4_096_000, True)
+    assert t == round(732.694e6)
+    assert bench.traffic(SimpleNamespace(s=8, arith="df64", fused_mpk=False), "update", 4_096_000, True) is None
+    assert bench.traffic(a, "update", 4_096_000, False) is None
+    assert bench.traffic(a, "dir", 4_096_000, True) is None
+
+
+def test_family_roofline_picks_the_dominant_family(monkeypatch):
+    monkeypatch.setattr(bench, "hbm_peak", lambda: (8000.0, "test peak"))
+    res = SimpleNamespace(profile={"t_mpk_ms": 10.0, "n_mpk": 100, "t_dir_ms": 30.0, "n_dir": 10,
+                                   "t_update_ms": 20.0, "n_update": 10})
+    r = bench.family_roofline(res, {"mpk": 1e6, "dir": 3e9, "update": 2e9},
+                              {"mpk": "levels", "dir": "gram", "update": "update"})
+    assert r["kernel"] == "gram"
+    # 3 GB per record, 10 records in 30 ms: 1000 GB/s
+    assert r["achieved"] == pytest.approx(1000.0) and r["frac"] == pytest.approx(0.125)
+    assert r["bound"] == "hbm" and r["traffic"] is None and r["peak"] == 8000.0
