@@ -46,3 +46,18 @@ def test_aniso7_couplings():
     assert A[i, i - N * N] == A[i, i + N * N] == -4.0
     assert np.count_nonzero(A[i]) == 7
     assert np.linalg.eigvalsh(A).min() > 0.0
+
+
+def test_aniso7_closed_form_spectrum():
+    """The anisotropic stencil is a Kronecker sum of three 1-D Dirichlet
+    operators: eigenvalues 14 - 2 cos(a) - 4 cos(b) - 8 cos(c) over the sine
+    modes a, b, c = pi k / (N + 1)."""
+    import scipy.sparse as sp
+
+    N = 4
+    rowptr, col, val = inputs.aniso7(N)
+    A = sp.csr_matrix((val, col, rowptr), shape=(N ** 3, N ** 3)).toarray()
+    th = np.pi * np.arange(1, N + 1) / (N + 1)
+    c = np.cos(th)
+    lam = 14.0 - 2.0 * c[:, None, None] - 4.0 * c[None, :, None] - 8.0 * c[None, None, :]
+    assert np.allclose(np.sort(lam.ravel()), np.linalg.eigvalsh(A), atol=1e-12)
