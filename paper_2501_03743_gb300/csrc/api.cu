@@ -274,7 +274,7 @@ int sscg_create(sscg_ctx** out, void* stream) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, c->device);
     if (e == cudaSuccess && !(major == 10 && minor == 3)) {
         free(c);
-        return SSCG_ERR_CUDA;  // this build carries sm_103a code only
+        return SSCG_ERR_CUDA;  // the library holds sm_103a code only
     }
     void* pinned = nullptr;
     if (e == cudaSuccess) e = cudaHostAlloc(&pinned, 64, cudaHostAllocDefault);
