@@ -8,19 +8,24 @@ recursive rel. residual 1e-8.  One step = one complete solve (init, every
 outer step, export of x, true residual) through the C ABI.
 
 Reported:
-  value      whole-job effective bandwidth of the s-step solves: the bytes
-             Algorithm 3 moves on the system as given (CSR with FP64 values,
-             FP64 vectors, A U and A P stored: the yardstick model below) over
-             the solve's device time, summed over ranks.  The yardstick does
-             not change with the library's storage choices, so a faster solve
-             always reads higher; plain PCG, the CPU oracle and the reference
-             arm are measured against the same yardstick (Algorithm 1 for PCG).
+  value      whole-job bandwidth of the s-step solves: the bytes the solve's
+             kernels move (the per-kernel byte model below) over the solve's
+             device time, summed over ranks; it cannot exceed the copy
+             bandwidth.  value_yardstick_gbs divides the bytes Algorithm 3 moves
+             on the system as given (CSR with FP64 values, FP64 vectors, A U and
+             A P stored: the yardstick below) by the same time.
+  dtype      the arithmetic of the solve: f64 (default) or df64 (pairs of FP32)
   e2e        the same metric through the public API with host buffers
              (b, x0 copied in and x copied out inside the timed region)
   roofline   the dominant kernel family, timed by the library's CUDA events
-             on its own stream over the timed steps, against the bytes its
-             kernels actually move (the per-kernel byte model below)
-  pcg_*      plain PCG (Algorithm 1) on the same kernels, timed beside it
+             on its own stream over the timed steps.  In FP64 the kernels are
+             bound by the FP64 units (about 2 operations per clock per SM on a
+             GB300, 1/60 of the FP32 rate): "alu", FP64 operations per launch
+             (fp64_ops_model) over the launch's duration against 2 per clock
+             per SM at the maximum SM clock; in df64 "hbm", the bytes the
+             kernels move against the measured copy bandwidth
+  pcg_*      plain PCG (Algorithm 1) on the same kernels and arithmetic
+  df64_*     (FP64 runs) the same solve and PCG in double-float
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same solve
 
 Yardstick (bytes per solve, V = 8 n, M = 12 nnz + 4 (n+1)): init M + 5V,
@@ -74,17 +79,19 @@ def parse():
     p.add_argument("--impl", default="sscg", choices=["sscg", "reference"])
     p.add_argument("--N", type=int, default=256)
     p.add_argument("--s", type=int, default=4)
-    p.add_argument("--arith", default="df64", choices=["f64", "df64"])
+    p.add_argument("--arith", default="f64", choices=["f64", "df64"])
+    p.add_argument("--no-df64", action="store_true", help="skip the double-float solve and PCG beside the FP64 line")
     p.add_argument("--tol", type=float, default=1e-8)
     p.add_argument("--no-pcg", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-sweep", action="store_true", help="skip the s in {1,2,4,6,8} sweep")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--fused-mpk", action="store_true", help="several matrix-powers levels per launch (L2-resident)")
-    p.add_argument("--workload", default="poisson", choices=["poisson", "batch", "mixed27", "cheb"],
+    p.add_argument("--workload", default="poisson", choices=["poisson", "batch", "mixed27", "cheb", "peaks"],
                    help="poisson: one 7-point solve (the headline); batch: the batched serving mix; "
                         "mixed27: 27-point 192^3 in mixed precision to 1e-10; cheb: Chebyshev basis with "
-                        "network vs Lanczos intervals on variable-coefficient 128^3 fields")
+                        "network vs Lanczos intervals on variable-coefficient 128^3 fields; peaks: the "
+                        "arithmetic throughput probes (FP64 FMA/add/multiply, FP64 mma, FP32 FMA, integer)")
     p.add_argument("--batch-systems", type=int, default=64)
     p.add_argument("--no-tune", action="store_true", help="batch: fixed tiles instead of the autotuner")
     p.add_argument("--no-seq", action="store_true", help="batch: skip the one-at-a-time comparison")
@@ -279,6 +286,27 @@ def workload_name(N, s, arith):
             f"seed=rank, x0=0, tol 1e-8; arithmetic {arith}")
 
 
+def fp64_ops_model(s, K=7):
+    """FP64 operations per row of the FP64 kernels on a Laplacian-class stencil
+    with K offsets in the diagonal form under a constant Jacobi scale (one
+    DFMA, DADD or DMUL per thread is one operation): level j: K - 2 additions
+    for the neighbour sum, one FMA for u_{j+1}, one for each moment (the
+    second moment is skipped on the last level); block update: s^2 FMAs each
+    for P and Q, s each for x and z, one for sum z^2 (first step: no P, Q
+    FMAs); PCG: SpMV K - 2 + 1, p . Ap 1; update x, r, ||r||^2; direction
+    u = D^-1 r and p = u + beta p."""
+    lvl = [(K - 2) + 2 + (1 if 2 * j + 2 <= 2 * s - 1 else 0) for j in range(s)]
+    return dict(level=lvl, level_avg=sum(lvl) / s, update=2 * s * s + 2 * s + 1, update_first=2 * s + 1,
+                pcg_spmv=K, pcg_update=3, pcg_dir=2)
+
+
+def alu_peak(sm_count, mhz=2070.0):
+    """The FP64 ALU roof in operations per second: 2 FP64 operations per clock
+    per SM (the nominal 1.25 TFLOP/s of a GB300 at its 2070 MHz maximum SM
+    clock is 1.25e12 / 2 / 152 / 2.07e9 = 1.99 FMAs per clock per SM)."""
+    return fp64_alu_peak(sm_count, mhz)
+
+
 def main():
     a = parse()
     world, rank, local, pg = dist_setup(a.gpus)
@@ -292,6 +320,8 @@ def main():
         return run_mixed27(a, world, rank, local, pg)
     if a.workload == "cheb":
         return run_cheb(a, world, rank, local, pg)
+    if a.workload == "peaks":
+        return run_peaks(a, world, rank, local, pg)
 
     import torch
 
@@ -308,9 +338,14 @@ def main():
     ctx = sscg.Context()
     A = sscg.Matrix(ctx, sysm["rowptr"], sysm["col"], sysm["val"])
     props = A.props()
-    vbytes = 8 if a.arith == "f64" else (4 if props["values_exact_fp32"] else 8)
-    dia = props["format"] == 1 and not a.fused_mpk
-    bm = byte_model(n, nnz, vbytes, a.s, a.arith, fused=a.fused_mpk, dia=dia)
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+
+    def model(arith):
+        vbytes = 8 if arith == "f64" else (4 if props["values_exact_fp32"] else 8)
+        dia = props["format"] == 1 and not a.fused_mpk
+        return byte_model(n, nnz, vbytes, a.s, arith, fused=a.fused_mpk, dia=dia), dia
+
+    bm, dia = model(a.arith)
     ym = yardstick(n, nnz, a.s)
     b = torch.from_numpy(sysm["b"]).cuda()
     x = torch.zeros_like(b)
@@ -349,38 +384,54 @@ def main():
     r0 = res[-1]
     total_ms = max_over_ranks(pg, sum(ms))
     ms_per_step = total_ms / a.steps
-    bytes_solve = sstep_bytes(ym, r0.outer_iters)
+    yard_solve = sstep_bytes(ym, r0.outer_iters)
     kernel_bytes_solve = sstep_bytes(bm, r0.outer_iters)
-    value = sum_over_ranks(pg, bytes_solve * a.steps) / (total_ms * 1e-3) / 1e9
+    # value: the bytes the solve's kernels move (their algorithmic byte model) per second
+    value = sum_over_ranks(pg, kernel_bytes_solve * a.steps) / (total_ms * 1e-3) / 1e9
+    value_yard = sum_over_ranks(pg, yard_solve * a.steps) / (total_ms * 1e-3) / 1e9
 
-    # dominant kernel family over the timed steps
+    # kernel families over the timed steps (the library's CUDA events on its stream)
+    ops = fp64_ops_model(a.s)
     fam = {}
-    for key, cnt, per in (("mpk", "n_mpk", bm["level_avg"]), ("update", "n_update", bm["update"])):
+    for key, cnt, per, fops in (("mpk", "n_mpk", bm["level_avg"], ops["level_avg"]),
+                                ("update", "n_update", bm["update"], ops["update"])):
         t = sum(r.profile[f"t_{key}_ms"] for r in res)
         c = sum(r.profile[cnt] for r in res)
-        fam[key] = dict(ms=t, launches=c, bytes_per_launch=per)
+        fam[key] = dict(ms=t, launches=c, bytes_per_launch=per, ops_per_launch=fops * n)
     dom = max(fam, key=lambda k: fam[k]["ms"])
     d = fam[dom]
     avg_s = d["ms"] / max(d["launches"], 1) * 1e-3
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
-    except (OSError, KeyError, ValueError):
-        peak, peak_src = 6800.0, "fallback"
-    achieved = d["bytes_per_launch"] / avg_s / 1e9
+    hbm, hbm_src = hbm_peak()
     kernel_names = {"mpk": ("k_level (matrix-powers level: diagonal-form SpMV + Jacobi + moments)" if dia else
                             "k_level (matrix-powers level: CSR SpMV + Jacobi + moments)"),
                     "update": ("k_update_tma (block update P, AP, x, r + next z)" if a.fused_mpk else
                                "k_update_q (block update P, Q = D^-1 A P, x, z)")}
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic(a, dom, n, dia), "kernel": kernel_names[dom],
-                "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "family_ms_per_solve": {k: round(v["ms"] / a.steps, 3) for k, v in fam.items()},
-                "family_gbs": {k: round(v["bytes_per_launch"] / (v["ms"] / max(v["launches"], 1) * 1e-3) / 1e9, 1)
-                               for k, v in fam.items()}}
+    gbs = {k: round(v["bytes_per_launch"] / (v["ms"] / max(v["launches"], 1) * 1e-3) / 1e9, 1) for k, v in fam.items()}
+    if a.arith == "f64" and dia and not a.fused_mpk:
+        peak = alu_peak(sm_count)
+        gops = {k: round(v["ops_per_launch"] / (v["ms"] / max(v["launches"], 1) * 1e-3) / 1e9, 1)
+                for k, v in fam.items()}
+        achieved = d["ops_per_launch"] / avg_s / 1e9
+        roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak / 1e9, 1), "unit": "Gop/s",
+                    "frac": round(achieved * 1e9 / peak, 4), "traffic": traffic(a, dom, n, dia),
+                    "kernel": kernel_names[dom],
+                    "peak_source": f"FP64 operations (DFMA/DADD/DMUL per thread) at 2 per clock per SM x {sm_count} "
+                                   "SMs x 2070 MHz, from the nominal 1.25 TFLOP/s and maximum SM clock; "
+                                   "the probe of include/sscg_probe.h measures 529 Gop/s",
+                    "ops_per_row": {"level": round(ops["level_avg"], 2), "update": ops["update"]},
+                    "family_ms_per_solve": {k: round(v["ms"] / a.steps, 3) for k, v in fam.items()},
+                    "family_gops": gops, "family_frac": {k: round(g * 1e9 / peak, 4) for k, g in gops.items()},
+                    "family_gbs": gbs, "family_hbm_frac": {k: round(g / hbm, 4) for k, g in gbs.items()},
+                    "hbm_peak": hbm}
+    else:
+        achieved = d["bytes_per_launch"] / avg_s / 1e9
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(achieved / hbm, 4), "traffic": traffic(a, dom, n, dia), "kernel": kernel_names[dom],
+                    "peak_source": f"measured copy bandwidth ({hbm_src})",
+                    "family_ms_per_solve": {k: round(v["ms"] / a.steps, 3) for k, v in fam.items()},
+                    "family_gbs": gbs}
 
-    # plain PCG beside it
+    # plain PCG beside it, in the same arithmetic
     pcg = None
     if not a.no_pcg:
         psolver = sscg.Solver(A, method="pcg", tol=a.tol, maxit=20000, arith=a.arith, profile=True)
@@ -390,9 +441,38 @@ def main():
         p0 = pres[-1]
         pcg_ms = max_over_ranks(pg, sum(pms)) / len(pms)
         pcg = dict(pcg_solve_ms=round(pcg_ms, 3), pcg_iters=p0.outer_iters, pcg_rel_res_true=p0.rel_res_true,
-                   pcg_gbs=round(pcg_bytes(ym, p0.outer_iters) / (pcg_ms * 1e-3) / 1e9, 1),
-                   pcg_kernel_gbs=round(pcg_bytes(bm, p0.outer_iters) / (pcg_ms * 1e-3) / 1e9, 1),
+                   pcg_gbs=round(pcg_bytes(bm, p0.outer_iters) / (pcg_ms * 1e-3) / 1e9, 1),
+                   pcg_yardstick_gbs=round(pcg_bytes(ym, p0.outer_iters) / (pcg_ms * 1e-3) / 1e9, 1),
                    speedup_vs_pcg=round(pcg_ms / ms_per_step, 4))
+        if a.arith == "f64" and dia:
+            pf = {}
+            for key, cnt, fo in (("mpk", "n_mpk", ops["pcg_spmv"]), ("update", "n_update", ops["pcg_update"]),
+                                 ("dir", "n_dir", ops["pcg_dir"])):
+                t = sum(r.profile[f"t_{key}_ms"] for r in pres)
+                c = sum(r.profile[cnt] for r in pres)
+                if c:
+                    pf[key] = round(fo * n / (t / c * 1e-3) / 1e9, 1)
+            pcg["pcg_family_gops"] = pf
+
+    # the same solve and PCG in double-float (pairs of FP32, about 48 bits, FP32 exponent range)
+    df = None
+    if a.arith == "f64" and not a.no_df64:
+        dsolver = sscg.Solver(A, s=a.s, tol=a.tol, maxit=5000, arith="df64")
+        x.zero_()
+        dsolver.solve(b, x)
+        dms, dres = timed(lambda: dsolver.solve(b, x), 2)
+        dp = sscg.Solver(A, method="pcg", tol=a.tol, maxit=20000, arith="df64")
+        x.zero_()
+        dp.solve(b, x)
+        dpms, dpres = timed(lambda: dp.solve(b, x), 2)
+        d_ms = max_over_ranks(pg, sum(dms)) / len(dms)
+        dp_ms = max_over_ranks(pg, sum(dpms)) / len(dpms)
+        df = {"df64_solve_ms": round(d_ms, 3), "df64_outer_iters": dres[-1].outer_iters,
+              "df64_rel_res_true": dres[-1].rel_res_true, "df64_pcg_solve_ms": round(dp_ms, 3),
+              "df64_speedup_vs_pcg": round(dp_ms / d_ms, 4),
+              "df64_note": "double-float: pairs of FP32 (about 48 significant bits, FP32 exponent range) on the "
+                           "FP32 units; narrower than FP64, reported for comparison only"}
+        del dsolver, dp
 
     # the block sizes of the workload's definition, s in {1, 2, 4, 6, 8}: one
     # warm-up and two timed solves each (after the timed region)
@@ -401,14 +481,15 @@ def main():
         for sv in (1, 2, 4, 6, 8):
             if sv == a.s:
                 sweep[str(sv)] = dict(ms=round(ms_per_step, 3), outer=r0.outer_iters, rel_res_true=r0.rel_res_true,
-                                      status=r0.status)
+                                      status=r0.status, true_res_below_tol=bool(r0.rel_res_true <= a.tol))
                 continue
             ssolver = sscg.Solver(A, s=sv, tol=a.tol, maxit=5000, arith=a.arith, fused_mpk=a.fused_mpk)
             x.zero_()
             ssolver.solve(b, x)
             sms, sres = timed(lambda: ssolver.solve(b, x), 2)
             sweep[str(sv)] = dict(ms=round(max_over_ranks(pg, sum(sms)) / len(sms), 3), outer=sres[-1].outer_iters,
-                                  rel_res_true=sres[-1].rel_res_true, status=sres[-1].status)
+                                  rel_res_true=sres[-1].rel_res_true, status=sres[-1].status,
+                                  true_res_below_tol=bool(sres[-1].rel_res_true <= a.tol))
             del ssolver
 
     # end to end through the public API with host buffers
@@ -426,7 +507,7 @@ def main():
         hr = hsolver.solve(bh, xh)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(pg, sum(e2e_t) / len(e2e_t))
-    e2e = {"value": round(sum_over_ranks(pg, sstep_bytes(ym, hr.outer_iters)) / e2e_s / 1e9, 1), "unit": "GB/s",
+    e2e = {"value": round(sum_over_ranks(pg, sstep_bytes(bm, hr.outer_iters)) / e2e_s / 1e9, 1), "unit": "GB/s",
            "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": round(e2e_s * 1e3, 3)}
 
     cpu = None
@@ -436,7 +517,8 @@ def main():
         cpu = {"value": round(per * o["steps"] / o["seconds"] / 1e9, 3), "unit": "GB/s", "cores": o["threads"],
                "kind": "oracle",
                "sample": f"{o['steps']} outer steps of the same s={a.s} solve (tol 0), FP64 C oracle, "
-                         f"{o['seconds']:.1f} s; bytes by the same yardstick, outer steps only"}
+                         f"{o['seconds']:.1f} s; bytes: the oracle's own (CSR with FP64 values, FP64 vectors, "
+                         "A U and A P stored), outer steps only"}
 
     if rank == 0:
         line = {
@@ -449,15 +531,20 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 ({kernel_bytes_solve / max(r0.outer_iters, 1) / 1e9:.2f} GB "
                              "moved per outer step, working set > 4 GB); no flush needed"},
+            "value_definition": "bytes the solve's kernels move (their algorithmic byte model, V = 8 n) per second "
+                                "of device time; cannot exceed the copy bandwidth",
+            "value_yardstick_gbs": round(value_yard, 1),
             "solve_ms": round(ms_per_step, 3), "outer_iters": r0.outer_iters, "equiv_iters": r0.equiv_iters,
             "status": r0.status, "rel_res_recursive": r0.rel_res_recursive, "rel_res_true": r0.rel_res_true,
-            "bytes_per_solve": bytes_solve, "kernel_bytes_per_solve": kernel_bytes_solve,
+            "yardstick_bytes_per_solve": yard_solve, "kernel_bytes_per_solve": kernel_bytes_solve,
             "wall_s_timed": round(t_wall, 3),
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(sum(r.profile["kernel_launches"] for r in res)),
             "clocks": clk, "cpu_baseline": cpu,
         }
         if pcg:
             line.update(pcg)
+        if df:
+            line.update(df)
         if sweep:
             line["s_sweep"] = sweep
         print(json.dumps(line), flush=True)
@@ -520,7 +607,7 @@ def run_batch(a, world, rank, local, pg):
     B = [ctx.uniform(R[k] * mats[k].n, 7000 + k).view(R[k], mats[k].n) for k in range(len(spec))]
     X = [torch.zeros_like(b) for b in B]
     t0 = time.perf_counter()
-    plan = sscg.BatchSolver(mats, R, s=a.s, tol=a.tol, maxit=5000, arith="df64", tune=not a.no_tune,
+    plan = sscg.BatchSolver(mats, R, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, tune=not a.no_tune,
                             persistent=a.persistent)
     t_plan = time.perf_counter() - t0
     props = plan.props()
@@ -553,7 +640,7 @@ def run_batch(a, world, rank, local, pg):
 
     seq = None
     if not a.no_seq:
-        solvers = [sscg.Solver(m, s=a.s, tol=a.tol, maxit=5000, arith="df64") for m in mats]
+        solvers = [sscg.Solver(m, s=a.s, tol=a.tol, maxit=5000, arith=a.arith) for m in mats]
         xs = [torch.zeros(m.n, dtype=torch.float64, device="cuda") for m in mats]
         # warm every solver once, then time all right-hand sides one by one
         for k in range(len(mats)):
@@ -830,6 +917,78 @@ def run_cheb(a, world, rank, local, pg):
                                  "sample": f"sigma=3 field {N}^3: oracle features + forward {t_net_cpu * 1e3:.1f} ms, "
                                            f"oracle 20-step Lanczos {t_lz_cpu * 1e3:.1f} ms"},
                 "rows": rows}
+        print(json.dumps(line), flush=True)
+    barrier(pg)
+
+
+PEAKS_METRIC = "arithmetic throughput probes: operations per second over the device"
+
+
+def probe_calibrated(ctx, kind, target_ms=100.0, iters_b=0):
+    """Run a probe once short, then with the iteration count that takes about
+    target_ms; best of three at that count."""
+    ops, ms = ctx.probe_rate(kind, 256, iters_b if iters_b else 0)
+    it = max(256, int(256 * target_ms / max(ms, 1e-3)))
+    best = None
+    for _ in range(3):
+        r = ctx.probe_rate(kind, it, iters_b)
+        best = r if best is None or r[0] > best[0] else best
+    return best[0], best[1], it
+
+
+def fp64_alu_peak(sm_count, sm_mhz):
+    """FP64 operations per second at sm_mhz: the nominal 1.25 TFLOP/s of a
+    GB300 at its 2070 MHz maximum SM clock is 2 FP64 FMAs per clock per SM
+    (1.25e12 / 2 / 152 / 2.07e9 = 1.99)."""
+    return 2.0 * sm_count * sm_mhz * 1e6
+
+
+def run_peaks(a, world, rank, local, pg):
+    """Each probe of include/sscg_probe.h for about 100 ms over a full-device
+    grid (best of three), with the SM clock sampled meanwhile; the mixed probe
+    runs DFMA and DMMA warps together with equal solo times to show whether
+    the FP64 tensor instruction adds throughput to the FP64 FMA pipe."""
+    import torch
+
+    if rank == 0:
+        from paper_2501_03743_gb300 import build
+
+        build.build()
+    barrier(pg)
+    torch.cuda.set_device(local)
+    from paper_2501_03743_gb300 import sscg
+
+    ctx = sscg.Context()
+    sm = torch.cuda.get_device_properties(local).multi_processor_count
+    clocks = Clocks(local)
+    clocks.start()
+    rates = {}
+    for kind in ("dfma", "dadd", "dmul", "dmma", "ffma", "ialu", "imad"):
+        ops, ms, it = probe_calibrated(ctx, kind)
+        rates[kind] = {"ops_per_s": ops, "ms": round(ms, 3), "iters": it}
+    # equal solo times: the DMMA warps' iteration count scaled from the solo rates
+    itf = rates["dfma"]["iters"]
+    t_f = rates["dfma"]["ms"]
+    itm = max(1, int(rates["dmma"]["iters"] * t_f / rates["dmma"]["ms"]))
+    best = None
+    for _ in range(3):
+        r = ctx.probe_rate("dfma_dmma", itf, itm)
+        best = r if best is None or r[0] > best[0] else best
+    rates["dfma_dmma"] = {"ops_per_s": best[0], "ms": round(best[1], 3), "iters": [itf, itm],
+                          "time_vs_solo": round(best[1] / t_f, 3)}
+    clk = clocks.stop()
+    if rank == 0:
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        per = {k: round(v["ops_per_s"] / (sm * mhz * 1e6), 3) for k, v in rates.items()}
+        line = {"metric": PEAKS_METRIC, "value": round(rates["dfma"]["ops_per_s"] / 1e9, 1),
+                "unit": "G FP64 FMA/s", "n_gpus": world, "steps": 3, "warmup": 1, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"full-device grid ({sm} SMs), independent dependency chains per thread, "
+                                       "about 100 ms per probe, best of 3"},
+                "rates_gops": {k: round(v["ops_per_s"] / 1e9, 2) for k, v in rates.items()},
+                "per_sm_per_clock": per, "sm_count": sm, "detail": rates,
+                "fp64_nominal_derived_gops_at_max_clock": round(fp64_alu_peak(sm, 2070.0) / 1e9, 1),
+                "clocks": clk}
         print(json.dumps(line), flush=True)
     barrier(pg)
 

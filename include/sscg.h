@@ -58,13 +58,16 @@ typedef enum {
     SSCG_PREC_CHEB = 2    /* B^-1 = p(D^-1 A) D^-1, Chebyshev polynomial over [lmin, lmax] */
 } sscg_prec;
 
-/* Arithmetic of the hot path.  F64 uses the FP64 units.  DF64 carries every
- * basis, block and vector element as an unevaluated sum of two FP32 numbers
- * (about 48 significant bits, FP32 exponent range) and computes with the FP32
- * units, whose GB300 throughput is about 57 times the FP64 rate.  MIXED stores
- * the basis blocks and matrix values in FP32 and keeps the Gram sums, the
- * s x s solves, x and r in DF64, with the true residual recomputed every
- * `replace_every` outer steps.  The s x s solves are always FP64. */
+/* Arithmetic of the hot path.  F64 (the default, the paper's precision) uses
+ * the FP64 units.  DF64 carries every basis, block and vector element as an
+ * unevaluated sum of two FP32 numbers (about 48 significant bits, FP32
+ * exponent range: right-hand sides and matrix values must lie well inside it)
+ * and computes with the FP32 units, whose GB300 throughput is about 60 times
+ * the FP64 rate; with the monomial basis it takes s <= 6 (larger s amplify its
+ * rounding past 1e-7 of the FP64 solution).  MIXED stores the basis blocks and
+ * matrix values in FP32 and accumulates the Gram sums, x and r in FP64, with
+ * the true residual recomputed in FP64 every `replace_every` outer steps.  The
+ * s x s solves are always FP64. */
 typedef enum { SSCG_ARITH_F64 = 0, SSCG_ARITH_DF64 = 1, SSCG_ARITH_MIXED = 2 } sscg_arith;
 
 /* Flags of sscg_opts.flags and sscg_mat_create_csr. */
@@ -186,7 +189,8 @@ int sscg_solve_workspace_bytes(const sscg_mat* mat, const sscg_opts* opts, size_
  * directly for the Chebyshev basis).  b: n FP64; x: n FP64, x0 on entry and
  * the solution on exit (device pointers unless SSCG_HOST_VECTORS).
  * info may be NULL.  Returns SSCG_OK, SSCG_NOT_CONVERGED, SSCG_BREAKDOWN,
- * SSCG_TIMEOUT or a negative error.  On b = 0, x = 0 and SSCG_OK. */
+ * SSCG_TIMEOUT or a negative error (SSCG_ERR_INVALID also for DF64 with the
+ * monomial basis and s > 6).  On b = 0, x = 0 and SSCG_OK. */
 int sscg_solve(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x,
                const sscg_opts* opts, sscg_info* info, void* workspace, size_t workspace_bytes);
 
@@ -223,6 +227,9 @@ int sscg_spmv(sscg_ctx* ctx, const sscg_mat* mat, const double* x, double* y);
  *   contents; the solve initialises everything it reads.  Calls whose work
  *   overlaps on the GPU (other streams or host threads) race on the array:
  *   serialise them.
+ * - A device reset (cudaDeviceReset) reloads the library's device code and
+ *   may move the array: the cached address is then stale.  Do not call
+ *   sscg_solve_static on a device after resetting it in the same process.
  */
 #define SSCG_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
 int sscg_solve_static(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x,
@@ -346,7 +353,8 @@ int sscg_set_bounds_model(sscg_mat* mat, int h, const double* model);
  * The paper has no batched form; this is the library's serving path.
  *
  * The plan binds the matrices (not copied: they must outlive the plan), the
- * options (s <= SSCG_BATCH_MAX_S, monomial basis, f64 or df64 arithmetic,
+ * options (s <= SSCG_BATCH_MAX_S, monomial basis, f64 or df64 arithmetic
+ * (df64: s <= 6),
  * tol, maxit, flags) and the caller's workspace.  Rows are processed in items
  * of T rows per system; T depends on the system's size class (n < 2^16,
  * < 2^19, < 2^21, larger).  With `tune` set, sscg_batch_create times two
@@ -388,6 +396,18 @@ int sscg_batch_solve(sscg_batch* plan, const double* const* B, double* const* X,
  * persistent mode), and the last solve's device time in ms (CUDA events
  * around it).  Any pointer may be NULL. */
 int sscg_batch_props(const sscg_batch* plan, int* tile_rows, int* grid, int* graph, float* last_ms);
+/* Fault injection for tests of the bounded waits (the paper has no
+ * counterpart).  Arms the next sscg_batch_solve of a plan made with
+ * SSCG_BATCH_PERSISTENT: CTA `cta` of its cooperative launch skips its
+ * arrival at the first grid-wide barrier, and every barrier wait of that
+ * solve gives up after `wait_ms` milliseconds (1..10000) instead of 2 s.  The
+ * other CTAs' waits then expire, every CTA returns (the skipping one after a
+ * bounded wait of its own), and the solve returns SSCG_TIMEOUT with X
+ * undefined.  Nothing faults or hangs: the context and the plan stay usable,
+ * and the knob is disarmed after that one solve.  cta = -1 disarms.
+ * Errors: SSCG_ERR_INVALID (not a persistent plan, cta outside the
+ * cooperative grid, wait_ms outside 1..10000). */
+int sscg_batch_inject_barrier_fault(sscg_batch* plan, int cta, int wait_ms);
 /* Kernels the last sscg_batch_solve ran, nodes of replayed CUDA graphs
  * included (per outer step: s levels, the solves, the update; plus the
  * initial launch); 1 in the persistent mode.  0 before the first solve.

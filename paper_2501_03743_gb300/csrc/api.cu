@@ -24,6 +24,7 @@ struct Analysis {
     unsigned long long dmax_bits;
     unsigned dia_bad;  // entries violating the constant-coefficient diagonal form
     unsigned pad;
+    unsigned long long out_of_f32;  // nonzero values outside FP32's normal range (|v| > FLT_MAX or < FLT_MIN)
 };
 
 // Per row: check column range and finiteness, split values into FP32
@@ -35,14 +36,14 @@ __global__ void __launch_bounds__(kThreads) k_analyze(int n, const int32_t* __re
                                                       double* __restrict__ dinv, float2* __restrict__ dinv_df,
                                                       float2* __restrict__ diag_df, float* __restrict__ dinv_f,
                                                       Analysis* out) {
-    __shared__ unsigned long long s_bad, s_nf, s_ne, s_np, s_bw, s_mn, s_mx;
+    __shared__ unsigned long long s_bad, s_nf, s_ne, s_np, s_bw, s_mn, s_mx, s_or;
     if (threadIdx.x == 0) {
-        s_bad = s_nf = s_ne = s_np = s_bw = 0ull;
+        s_bad = s_nf = s_ne = s_np = s_bw = s_or = 0ull;
         s_mn = ~0ull;
         s_mx = 0ull;
     }
     __syncthreads();
-    unsigned long long bad = 0, nf = 0, ne = 0, np = 0, bw = 0, mn = ~0ull, mx = 0ull;
+    unsigned long long bad = 0, nf = 0, ne = 0, np = 0, bw = 0, mn = ~0ull, mx = 0ull, orr = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double d = 0.0;
         for (int k = rowptr[i]; k < rowptr[i + 1]; k++) {
@@ -50,6 +51,8 @@ __global__ void __launch_bounds__(kThreads) k_analyze(int n, const int32_t* __re
             double v = val[k];
             if (c < 0 || c >= n) bad++;
             if (!isfinite(v)) nf++;
+            const double av = fabs(v);
+            if (av != 0.0 && (av > 3.4028234663852886e38 || av < 1.1754943508222875e-38)) orr++;
             float hi = __double2float_rn(v);
             float lo = __double2float_rn(v - (double)hi);
             vhi[k] = hi;
@@ -83,6 +86,7 @@ __global__ void __launch_bounds__(kThreads) k_analyze(int n, const int32_t* __re
     if (bad) atomicAdd(&s_bad, bad);
     if (nf) atomicAdd(&s_nf, nf);
     if (ne) atomicAdd(&s_ne, ne);
+    if (orr) atomicAdd(&s_or, orr);
     if (np) atomicAdd(&s_np, np);
     atomicMax(&s_bw, bw);
     atomicMin(&s_mn, mn);
@@ -92,6 +96,7 @@ __global__ void __launch_bounds__(kThreads) k_analyze(int n, const int32_t* __re
         if (s_bad) atomicAdd(&out->bad_col, s_bad);
         if (s_nf) atomicAdd(&out->nonfinite, s_nf);
         if (s_ne) atomicAdd(&out->not_exact, s_ne);
+        if (s_or) atomicAdd(&out->out_of_f32, s_or);
         if (s_np) atomicAdd(&out->nonpos_diag, s_np);
         atomicMax(&out->bandwidth, s_bw);
         atomicMin(&out->dmin_bits, s_mn);
@@ -379,6 +384,7 @@ int sscg_mat_create_csr(sscg_ctx* ctx, int64_t n, int64_t nnz, const int32_t* ro
     m->diag_df = L.diag_df;
     m->bandwidth = (int64_t)a.bandwidth;
     m->exact_fp32 = a.not_exact == 0;
+    m->out_of_f32 = a.out_of_f32 != 0;
     m->max_row_nnz = max_row;
     m->max_tile_nnz = max_tile;
     double dmn, dmx;
@@ -481,6 +487,12 @@ int sscg_solve(sscg_ctx* ctx, const sscg_mat* m, const double* b, double* x, con
         return set_err(ctx, SSCG_ERR_INVALID, "arith %d not supported", o->arith);
     if (o->arith == SSCG_ARITH_MIXED && m->prec == SSCG_PREC_CHEB)
         return set_err(ctx, SSCG_ERR_INVALID, "the mixed-precision mode takes a diagonal preconditioner");
+    if (o->arith != SSCG_ARITH_F64 && m->out_of_f32)
+        return set_err(ctx, SSCG_ERR_INVALID, "matrix values lie outside FP32's normal range, which double-float "
+                                              "and mixed arithmetic carry; use f64");
+    if (o->arith == SSCG_ARITH_DF64 && o->basis == SSCG_BASIS_MONOMIAL && o->s > kMaxSDf64Monomial)
+        return set_err(ctx, SSCG_ERR_INVALID, "double-float arithmetic takes the monomial basis up to s = %d; use f64",
+                       kMaxSDf64Monomial);
     if (o->arith != SSCG_ARITH_MIXED && !use_gram(m, o)) return solve_sstep(ctx, m, b, x, o, info, ws, ws_bytes);
     double lo = o->basis_lmin, hi = o->basis_lmax;
     if (auto_bounds(o)) {
@@ -524,6 +536,9 @@ int sscg_pcg_workspace_bytes(const sscg_mat* m, const sscg_opts* o, size_t* byte
 int sscg_pcg_solve(sscg_ctx* ctx, const sscg_mat* m, const double* b, double* x, const sscg_opts* o, sscg_info* info,
                    void* ws, size_t ws_bytes) {
     if (!ctx) return SSCG_ERR_INVALID;
+    if (m && o && o->arith != SSCG_ARITH_F64 && m->out_of_f32)
+        return set_err(ctx, SSCG_ERR_INVALID, "matrix values lie outside FP32's normal range, which double-float "
+                                              "arithmetic carries; use f64");
     return solve_pcg(ctx, m, b, x, o, info, ws, ws_bytes);
 }
 

@@ -150,6 +150,8 @@ struct BArgs {
     GCtl* g;
     BCtl* bctl;
     Ctrl* rc;  // one per right-hand side
+    int skip_cta;             // fault injection: this CTA skips its first barrier arrival (-1: none)
+    unsigned long long wait_ns;  // limit of every barrier wait
 };
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
@@ -163,11 +165,25 @@ __device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
 }
 
 // Grid-wide barrier (all CTAs are co-resident: cooperative launch).  Returns
-// false when the kernel must stop (a wait expired here or elsewhere).
-__device__ bool grid_sync(GCtl* g) {
+// false when the kernel must stop (a wait expired here or elsewhere).  Every
+// wait gives up after wait_ns.  With skip_cta set (fault injection for tests
+// of the bounded waits), that CTA does not arrive: the others' waits expire
+// and set SSCG_TIMEOUT, while it waits (bounded as well) for that error and
+// returns; the barrier's counters are reset by the next solve.
+__device__ bool grid_sync(GCtl* g, int skip_cta, unsigned long long wait_ns) {
     __shared__ int s_ok;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && (int)blockIdx.x == skip_cta) {
+        const uint64_t t0 = globaltimer();
+        while (!*(volatile int*)&g->err) {
+            if (globaltimer() - t0 > 2 * wait_ns + 100000000ull) {
+                atomicCAS(&g->err, 0, SSCG_TIMEOUT);
+                break;
+            }
+            __nanosleep(1000);
+        }
+        s_ok = 0;
+    } else if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned gen = ld_acquire_gpu(&g->bar.gen);
         __threadfence();
@@ -183,7 +199,7 @@ __device__ bool grid_sync(GCtl* g) {
                     ok = 0;
                     break;
                 }
-                if (globaltimer() - t0 > kBarrierTimeoutNs) {
+                if (globaltimer() - t0 > wait_ns) {
                     atomicCAS(&g->err, 0, SSCG_TIMEOUT);
                     ok = 0;
                     break;
@@ -751,17 +767,17 @@ template <class A, int SB>
 __global__ void __launch_bounds__(kBThreads, 3) k_batch(BArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) a.g->t0 = globaltimer();
     ph_init<A>(a, blockIdx.x, gridDim.x);
-    if (!grid_sync(a.g)) return;
+    if (!grid_sync(a.g, a.skip_cta, a.wait_ns)) return;
     for (;;) {
         for (int j = 0; j < a.s; j++) {
             ph_level<A, false>(a, j, blockIdx.x, gridDim.x);
-            if (!grid_sync(a.g)) return;
+            if (!grid_sync(a.g, a.skip_cta, a.wait_ns)) return;
         }
         ph_solve<A>(a, blockIdx.x, gridDim.x);
-        if (!grid_sync(a.g)) return;
+        if (!grid_sync(a.g, a.skip_cta, a.wait_ns)) return;
         if (*(volatile int*)&a.g->finished >= a.nsys) break;
         ph_update<A, SB>(a, blockIdx.x, gridDim.x);
-        if (!grid_sync(a.g)) return;
+        if (!grid_sync(a.g, a.skip_cta, a.wait_ns)) return;
     }
 }
 
@@ -834,6 +850,8 @@ struct sscg_batch {
     cudaGraphExec_t exec;
     float last_ms;
     int64_t last_launches;       // kernels the last solve ran (graph nodes included)
+    int fault_cta = -1;          // armed barrier fault for the next solve (sscg_batch_inject_barrier_fault)
+    unsigned long long fault_wait_ns = 0;
 };
 
 namespace {
@@ -894,9 +912,14 @@ int check_batch(sscg_ctx* ctx, int nsys, const sscg_mat* const* mats, const int*
     if (o->basis != SSCG_BASIS_MONOMIAL) return set_err(ctx, SSCG_ERR_INVALID, "batched solves use the monomial basis");
     if (o->arith != SSCG_ARITH_F64 && o->arith != SSCG_ARITH_DF64)
         return set_err(ctx, SSCG_ERR_INVALID, "batched solves run in f64 or df64 arithmetic");
+    if (o->arith == SSCG_ARITH_DF64 && o->s > kMaxSDf64Monomial)
+        return set_err(ctx, SSCG_ERR_INVALID, "double-float arithmetic takes the monomial basis up to s = %d; use f64",
+                       kMaxSDf64Monomial);
     if (o->maxit < 0 || !(o->tol >= 0.0)) return set_err(ctx, SSCG_ERR_INVALID, "bad maxit or tol");
     for (int k = 0; k < nsys; k++) {
         if (!mats[k]) return set_err(ctx, SSCG_ERR_INVALID, "system %d: null matrix", k);
+        if (o->arith != SSCG_ARITH_F64 && mats[k]->out_of_f32)
+            return set_err(ctx, SSCG_ERR_INVALID, "system %d: values outside FP32's normal range; use f64", k);
         if (nrhs[k] < 1 || nrhs[k] > kMaxR)
             return set_err(ctx, SSCG_ERR_INVALID, "system %d: %d right-hand sides (1..%d)", k, nrhs[k], kMaxR);
         if (mats[k]->prec != SSCG_PREC_JACOBI)
@@ -941,6 +964,8 @@ BArgs make_args(const sscg_batch* b, int tuning, int maxit) {
     a.g = b->d_g;
     a.bctl = b->d_bctl;
     a.rc = b->d_rc;
+    a.skip_cta = b->fault_cta;
+    a.wait_ns = b->fault_cta >= 0 ? b->fault_wait_ns : kBarrierTimeoutNs;
     return a;
 }
 
@@ -1353,14 +1378,17 @@ int sscg_batch_solve(sscg_batch* b, const double* const* B, double* const* X, ss
     SSCG_CUDA(ctx, cudaEventCreate(&e1));
     SSCG_CUDA(ctx, cudaEventRecord(e0, st));
     b->last_launches = 1;  // the persistent mode: one cooperative kernel
+    const bool fault = b->fault_cta >= 0;  // an armed fault runs outside the captured graph
     if (!b->persistent) {
         if (int rc = run_phases(b)) return rc;
-    } else if (b->graph_ok) {
+    } else if (b->graph_ok && !fault) {
         SSCG_CUDA(ctx, cudaGraphLaunch(b->exec, st));
     } else {
         if (int rc = reset_state(b)) return rc;
         SSCG_CUDA(ctx, cudaMemcpyAsync(b->d_io, b->h_io, sizeof(double*) * 2 * b->nsys, cudaMemcpyHostToDevice, st));
-        if (int rc = launch_any(b, L_PERSISTENT, 0, b->maxit)) return rc;
+        const int lrc = launch_any(b, L_PERSISTENT, 0, b->maxit);
+        b->fault_cta = -1;  // disarmed after one solve
+        if (lrc) return lrc;
         SSCG_CUDA(ctx, cudaMemcpyAsync(b->h_rc, b->d_rc, sizeof(Ctrl) * b->total_rhs, cudaMemcpyDeviceToHost, st));
         SSCG_CUDA(ctx, cudaMemcpyAsync(b->h_bctl, b->d_bctl, sizeof(BCtl) * b->nsys, cudaMemcpyDeviceToHost, st));
         SSCG_CUDA(ctx, cudaMemcpyAsync(b->h_g, b->d_g, sizeof(GCtl), cudaMemcpyDeviceToHost, st));
@@ -1411,6 +1439,20 @@ int sscg_batch_solve(sscg_batch* b, const double* const* B, double* const* X, ss
         if (st_k > worst) worst = st_k;
     }
     return worst;
+}
+
+int sscg_batch_inject_barrier_fault(sscg_batch* b, int cta, int wait_ms) {
+    if (!b) return SSCG_ERR_INVALID;
+    if (cta == -1) {
+        b->fault_cta = -1;
+        return SSCG_OK;
+    }
+    if (!b->persistent) return set_err(b->ctx, SSCG_ERR_INVALID, "barrier faults need a persistent plan");
+    if (cta < 0 || cta >= b->grid) return set_err(b->ctx, SSCG_ERR_INVALID, "CTA %d outside the grid of %d", cta, b->grid);
+    if (wait_ms < 1 || wait_ms > 10000) return set_err(b->ctx, SSCG_ERR_INVALID, "wait_ms must lie in 1..10000");
+    b->fault_cta = cta;
+    b->fault_wait_ns = (unsigned long long)wait_ms * 1000000ull;
+    return SSCG_OK;
 }
 
 int sscg_batch_props(const sscg_batch* b, int* tile_rows, int* grid, int* graph, float* last_ms) {

@@ -361,6 +361,35 @@ __device__ __forceinline__ double cta_sum_partials(const double* p, int count, d
     return r;
 }
 
+// Maximum of v over the CTA, valid in thread 0 (blockDim.x a multiple of 32;
+// `sh` holds blockDim.x / 32 doubles).  Ends with a CTA barrier.
+__device__ __forceinline__ double block_max(double v, double* sh) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, m));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x / 32); w++) r = fmax(r, sh[w]);
+    __syncthreads();
+    return r;
+}
+
+// Maximum of `count` nonnegative values, by one CTA; valid in thread 0.
+__device__ __forceinline__ double cta_max_partials(const double* p, int count, double* sh) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) t = fmax(t, __ldcg(p + i));
+    __syncthreads();
+    return block_max(t, sh);
+}
+
+// Right-hand sides a double-float or mixed solve accepts: max |b_i| in
+// [2^-30, 2^30].  Their vectors, squared norms and moments live in FP32's
+// exponent range (about 1e-38 ... 3e38); a right-hand side far outside O(1)
+// would underflow or overflow them before the solve reached its tolerance.
+constexpr double kDfRhsMin = 0x1p-30, kDfRhsMax = 0x1p30;
+
 // Deterministic sums of `count` partial arrays (array e holds G values at
 // p + e*G) by one CTA, warps taking arrays round-robin; store(e, value) runs
 // in lane 0 of the owning warp.  Ends with a CTA barrier.

@@ -36,6 +36,7 @@ struct sscg_mat {
     // properties
     int64_t bandwidth;
     int exact_fp32;
+    int out_of_f32;  // some nonzero value lies outside FP32's normal range: df64 / mixed solves refuse
     int max_row_nnz;
     int max_tile_nnz;  // largest nnz count of a 256-row tile
     double dmin, dmax;
@@ -233,6 +234,13 @@ int splitmix_uniform(sscg_ctx* ctx, int64_t n, uint64_t seed, double* out);
 int mixed_workspace(const sscg_mat* mat, const sscg_opts* opts, size_t* bytes);
 int solve_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* opts,
                 sscg_info* info, void* ws, size_t ws_bytes, double blo, double bhi);
+
+// Largest block size of a double-float solve in the monomial basis.  The
+// monomial basis amplifies rounding with s (its Hankel moment matrix loses
+// conditioning geometrically); with double-float's unit roundoff (2^-48,
+// 32 times FP64's) the solution at s >= 7 drifts beyond 1e-7 of the FP64
+// result on a 19^3 Poisson system (1.1e-7 at s = 8), so those solves take f64.
+constexpr int kMaxSDf64Monomial = 6;
 
 // Steps of the Lanczos estimate a Chebyshev-basis solve runs when the caller
 // gives no basis interval, and the widening applied to its Ritz values.

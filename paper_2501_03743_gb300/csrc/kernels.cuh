@@ -13,8 +13,11 @@ namespace {
 
 __device__ __forceinline__ int ctrl_done(const Ctrl* c) { return __ldcg(&c->done); }
 
-// r = b - A x0 (x0 and b FP64), x_w = x0, z = B^-1 r -> u0; ||b||^2, ||r||^2,
-// mu_0 = r . z; the last CTA initialises the control block.
+// r = b - A x0 (x0 and b FP64), x_w = x0, z = B^-1 r -> u0; ||b||^2 and
+// max |b_i| (in FP64 whatever the arithmetic), ||r||^2, mu_0 = r . z; the
+// last CTA initialises the control block.  A double-float solve whose
+// right-hand side lies outside [kDfRhsMin, kDfRhsMax] stops with
+// SSCG_ERR_INVALID before its first step.  `part` holds 4 G doubles.
 template <class A, int VM>
 __global__ void __launch_bounds__(kThreads) k_init(MatView M, const typename A::S* __restrict__ dinv,
                                                    const double* __restrict__ b, const double* __restrict__ x0,
@@ -26,17 +29,20 @@ __global__ void __launch_bounds__(kThreads) k_init(MatView M, const typename A::
     __shared__ int s_rp[kTileRows + 1];
     __shared__ double red[3 * (kThreads / 32)];
     const int ntiles = (M.n + kTileRows - 1) / kTileRows;
-    R bb = A::zero(), rr = A::zero(), rz = A::zero();
+    R rr = A::zero(), rz = A::zero();
+    double bb = 0.0, bmax = 0.0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         R y;
         int row;
         bool live = tile_spmv<A, VM>(M, tile, [&](int c) { return A::from_d(__ldg(x0 + c)); }, y, row, smem, s_rp);
         if (live) {
-            R bi = A::from_d(b[row]);
+            const double bd = b[row];
+            R bi = A::from_d(bd);
             R ri = A::sub(bi, y);
             if (xw) A::st(xw + row, A::zero());  // DF64 iterate holds x - x0
             A::st(r + row, ri);
-            bb = A::fma(bi, bi, bb);
+            bb = fma(bd, bd, bb);
+            bmax = fmax(bmax, fabs(bd));
             rr = A::fma(ri, ri, rr);
             if (u0) {  // null: the preconditioner is applied by separate kernels
                 R zi = dinv ? A::mul(A::ld(dinv + row), ri) : ri;
@@ -45,24 +51,32 @@ __global__ void __launch_bounds__(kThreads) k_init(MatView M, const typename A::
             }
         }
     }
-    R v[3] = {bb, rr, rz};
-    double out[3];
-    block_sum<A, 3>(v, red, out);
+    R v[2] = {rr, rz};
+    double out[2];
+    block_sum<A, 2>(v, red, out);
+    double vb[1] = {bb}, outb[1];
+    block_sum<ArithF64, 1>(vb, red, outb);
+    const double bm = block_max(isfinite(bmax) ? bmax : 0.0, red);
     const int G = gridDim.x;
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = out[0];
-        part[G + blockIdx.x] = out[1];
-        part[2 * G + blockIdx.x] = out[2];
+        part[blockIdx.x] = outb[0];
+        part[G + blockIdx.x] = out[0];
+        part[2 * G + blockIdx.x] = out[1];
+        part[3 * G + blockIdx.x] = bm;
     }
     if (!last_cta(&ctrl->ticket[0])) return;
     __shared__ double sh[32];
     double sbb = cta_sum_partials(part, G, sh);
     double srr = cta_sum_partials(part + G, G, sh);
     double srz = cta_sum_partials(part + 2 * G, G, sh);
+    const double smax = cta_max_partials(part + 3 * G, G, sh);
     if (threadIdx.x == 0) {
         ctrl->bnorm = sqrt(sbb);
         ctrl->mu[0] = srz;
-        if (sbb == 0.0) {
+        if (A::kind != 0 && isfinite(sbb) && sbb != 0.0 && (smax < kDfRhsMin || smax > kDfRhsMax)) {
+            ctrl->status = SSCG_ERR_INVALID;
+            ctrl->done = 1;
+        } else if (sbb == 0.0) {
             ctrl->zero_rhs = 1;
             ctrl->relres = 0.0;
             hist[0] = 0.0;
@@ -88,101 +102,9 @@ __global__ void __launch_bounds__(kThreads) k_init(MatView M, const typename A::
     }
 }
 
-// Block updates of Algorithm 3 for one outer step (see file comment).
-// blk_new holds U | AU on entry and P | AP on exit; blk_old holds
-// P_old | AP_old and receives z = B^-1 r_new in its first column.
-template <class A, int SB>
-__global__ void __launch_bounds__(kThreads, SB <= 4 ? 3 : 2) k_update(int n, int ldn, int s, typename A::S* __restrict__ blk_new,
-                                                     typename A::S* __restrict__ blk_old,
-                                                     typename A::S* __restrict__ x, typename A::S* __restrict__ r,
-                                                     const typename A::S* __restrict__ dinv,
-                                                     double* __restrict__ part, int first, int write_z,
-                                                     Ctrl* ctrl, double* __restrict__ hist) {
-    using R = typename A::R;
-    if (ctrl_done(ctrl)) return;
-    __shared__ R sb[SB * SB];
-    __shared__ R sa[SB];
-    __shared__ double red[2 * (kThreads / 32)];
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) sb[(e % s) + (e / s) * SB] = A::from_d(ctrl->beta[e]);
-    for (int e = threadIdx.x; e < s; e += blockDim.x) sa[e] = A::from_d(ctrl->alpha[e]);
-    __syncthreads();
-    R rr = A::zero(), rz = A::zero();
-    const size_t ld = (size_t)ldn;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        R po[SB], apo[SB];
-        if (!first) {
-#pragma unroll
-            for (int l = 0; l < SB; l++)
-                if (l < s) {
-                    po[l] = A::ld(blk_old + l * ld + i);
-                    apo[l] = A::ld(blk_old + (s + l) * ld + i);
-                }
-        }
-        R xa = A::zero(), ra = A::zero();
-#pragma unroll
-        for (int jj = 0; jj < SB; jj++) {
-            if (jj < s) {
-                R p = A::ld(blk_new + jj * ld + i);
-                R ap = A::ld(blk_new + (s + jj) * ld + i);
-                if (!first) {
-#pragma unroll
-                    for (int l = 0; l < SB; l++)
-                        if (l < s) {
-                            p = A::fma(po[l], sb[l + jj * SB], p);
-                            ap = A::fma(apo[l], sb[l + jj * SB], ap);
-                        }
-                }
-                A::st(blk_new + jj * ld + i, p);
-                A::st(blk_new + (s + jj) * ld + i, ap);
-                xa = A::fma(p, sa[jj], xa);
-                ra = A::fma(ap, sa[jj], ra);
-            }
-        }
-        R xn = A::add(A::ld(x + i), xa);
-        R rn = A::sub(A::ld(r + i), ra);
-        A::st(x + i, xn);
-        A::st(r + i, rn);
-        rr = A::fma(rn, rn, rr);
-        if (write_z) {  // u_1 of the next step, B^-1 r with B diagonal
-            R z = dinv ? A::mul(A::ld(dinv + i), rn) : rn;
-            A::st(blk_old + i, z);
-            rz = A::fma(rn, z, rz);
-        }
-    }
-    R v[2] = {rr, rz};
-    double out[2];
-    block_sum<A, 2>(v, red, out);
-    const int G = gridDim.x;
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = out[0];
-        part[G + blockIdx.x] = out[1];
-    }
-    if (!last_cta(&ctrl->ticket[2])) return;
-    __shared__ double sh[32];
-    double srr = cta_sum_partials(part, G, sh);
-    double srz = cta_sum_partials(part + G, G, sh);
-    if (threadIdx.x == 0) {
-        int step = ctrl->step + 1;
-        double rel = sqrt(srr) / ctrl->bnorm;
-        ctrl->step = step;
-        ctrl->relres = rel;
-        ctrl->mu[0] = srz;
-        hist[step] = rel;
-        ctrl->nhist = step + 1;
-        if (!isfinite(rel)) {
-            ctrl->status = 2;
-            ctrl->done = 1;
-        } else if (rel < ctrl->tol) {
-            ctrl->status = 0;
-            ctrl->done = 1;
-        } else if (step >= ctrl->maxit) {
-            ctrl->status = 1;
-            ctrl->done = 1;
-        }
-    }
-}
-
-// The same block updates fed by bulk copies: a CTA of kUpdRows threads
+// Block updates of Algorithm 3 (P = U + P_old beta, AP = AU + AP_old beta,
+// x += P alpha, r -= AP alpha, z = B^-1 r and ||r||^2, mu_0 = r . z for the
+// next step) fed by bulk copies: a CTA of kUpdRows threads
 // takes tiles of kUpdRows rows; thread 0 copies each tile's slice of every
 // input column (U, AU, P_old, AP_old, r and 1/diag) into one of two shared
 // memory stages with cp.async.bulk, completing on the stage's mbarrier, so
@@ -486,8 +408,12 @@ __global__ void __launch_bounds__(kThreads) k_update_q(int n, int ldn, int s, ty
     __shared__ R sb[SB * SB];
     __shared__ R sa[SB];
     __shared__ double red[2 * (kThreads / 32)];
+    __shared__ R sna[SB];
     for (int e = threadIdx.x; e < s * s; e += blockDim.x) sb[(e % s) + (e / s) * SB] = A::from_d(ctrl->beta[e]);
-    for (int e = threadIdx.x; e < s; e += blockDim.x) sa[e] = A::from_d(ctrl->alpha[e]);
+    for (int e = threadIdx.x; e < s; e += blockDim.x) {
+        sa[e] = A::from_d(ctrl->alpha[e]);
+        sna[e] = A::from_d(-ctrl->alpha[e]);
+    }
     const R dcst = A::from_d(diag_c);
     __syncthreads();
     const size_t ld = (size_t)ldn;
@@ -505,9 +431,8 @@ __global__ void __launch_bounds__(kThreads) k_update_q(int n, int ldn, int s, ty
                     qo[l] = A::ldcg(blk_old + (s + 1 + l) * ld + i);
                 }
         }
-        const R x0 = A::ldcg(x + i);
-        const R d = diag ? A::ldcg(diag + i) : dcst;
-        R xa = A::zero(), za = A::zero();
+        // x and z accumulate onto their old values: x += P alpha, z += Q (-alpha)
+        R xn = A::ldcg(x + i), zn = u[0];
 #pragma unroll
         for (int jj = 0; jj < SB; jj++) {
             if (jj < s) {
@@ -524,17 +449,23 @@ __global__ void __launch_bounds__(kThreads) k_update_q(int n, int ldn, int s, ty
                     A::st_stream(blk_new + jj * ld + i, p);
                 }
                 A::st_stream(blk_new + (s + 1 + jj) * ld + i, q);
-                xa = A::fma(p, sa[jj], xa);
-                za = A::fma(q, sa[jj], za);
+                xn = A::fma(p, sa[jj], xn);
+                zn = A::fma(q, sna[jj], zn);
             }
         }
-        const R xn = A::add(x0, xa);
-        const R zn = A::sub(u[0], za);
         A::st(x + i, xn);
         A::st(blk_old + i, zn);  // U_1 of the next step (P_old_1 already read)
-        const R rn = (diag || diag_c != 0.0) ? A::mul(d, zn) : zn;
-        rr = A::fma(rn, rn, rr);
-        rz = A::fma(rn, zn, rz);
+        if (diag) {
+            const R rn = A::mul(A::ldcg(diag + i), zn);
+            rr = A::fma(rn, rn, rr);
+            rz = A::fma(rn, zn, rz);
+        } else {
+            rz = A::fma(zn, zn, rz);  // sum z^2; scaled by the constant diagonal below
+        }
+    }
+    if (!diag) {  // r = d z: ||r||^2 = d^2 sum z^2, mu_0 = d sum z^2 (d = 1 without a preconditioner)
+        if (diag_c != 0.0) rz = A::mul(dcst, rz);
+        rr = diag_c != 0.0 ? A::mul(dcst, rz) : rz;
     }
     R v[2] = {rr, rz};
     double out[2];

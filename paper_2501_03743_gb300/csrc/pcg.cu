@@ -37,18 +37,21 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(MatView M, const typename
     __shared__ int s_rp[kTileRows + 1];
     __shared__ double red[3 * (kThreads / 32)];
     const int ntiles = (M.n + kTileRows - 1) / kTileRows;
-    R bb = A::zero(), rr = A::zero(), ru = A::zero();
+    R rr = A::zero(), ru = A::zero();
+    double bb = 0.0, bmax = 0.0;  // ||b||^2 and max |b_i| in FP64 whatever the arithmetic
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         R y = A::zero();
         int row = tile * kTileRows + threadIdx.x;
         bool live = row < M.n;
         if (x0) live = tile_spmv<A, VM>(M, tile, [&](int c) { return A::from_d(__ldg(x0 + c)); }, y, row, smem, s_rp);
         if (live) {
-            R bi = A::from_d(b[row]);
+            const double bd = b[row];
+            R bi = A::from_d(bd);
             R ri = A::sub(bi, y);
             if (xw) A::st(xw + row, A::zero());  // DF64 iterate holds x - x0
             A::st(r + row, ri);
-            bb = A::fma(bi, bi, bb);
+            bb = fma(bd, bd, bb);
+            bmax = fmax(bmax, fabs(bd));
             rr = A::fma(ri, ri, rr);
             if (diag) {
                 R ui = dinv ? A::mul(A::ld(dinv + row), ri) : ri;
@@ -57,25 +60,33 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(MatView M, const typename
             }
         }
     }
-    R v[3] = {bb, rr, ru};
-    double out[3];
-    block_sum<A, 3>(v, red, out);
+    R v[2] = {rr, ru};
+    double out[2];
+    block_sum<A, 2>(v, red, out);
+    double vb[1] = {bb}, outb[1];
+    block_sum<ArithF64, 1>(vb, red, outb);
+    const double bm = block_max(isfinite(bmax) ? bmax : 0.0, red);
     const int G = gridDim.x;
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = out[0];
-        part[G + blockIdx.x] = out[1];
-        part[2 * G + blockIdx.x] = out[2];
+        part[blockIdx.x] = outb[0];
+        part[G + blockIdx.x] = out[0];
+        part[2 * G + blockIdx.x] = out[1];
+        part[3 * G + blockIdx.x] = bm;
     }
     if (!last_cta(&ctrl->ticket[0])) return;
     __shared__ double sh[32];
     double sbb = cta_sum_partials(part, G, sh);
     double srr = cta_sum_partials(part + G, G, sh);
     double sru = cta_sum_partials(part + 2 * G, G, sh);
+    const double smax = cta_max_partials(part + 3 * G, G, sh);
     if (threadIdx.x == 0) {
         ctrl->bnorm = sqrt(sbb);
         ctrl->rho = sru;
         ctrl->nhist = 1;
-        if (sbb == 0.0) {
+        if (A::kind != 0 && isfinite(sbb) && sbb != 0.0 && (smax < kDfRhsMin || smax > kDfRhsMax)) {
+            ctrl->status = SSCG_ERR_INVALID;
+            ctrl->done = 1;
+        } else if (sbb == 0.0) {
             ctrl->zero_rhs = 1;
             ctrl->relres = 0.0;
             hist[0] = 0.0;
@@ -115,7 +126,22 @@ __global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1) k_pcg_spmv(MatView 
         pq = A::fma(A::ldg(p + row), y, pq);
     };
     bool ok = true;
-    if constexpr (DM != 0 && A::kind == 1) {
+    if constexpr (DM >= 7 && A::kind == 0) {
+        // FP64 diagonal form, Laplacian class: q = c_centre p + c_off S, one
+        // FMA beyond the neighbour sum when c_off = -1 (the Poisson stencils)
+        const double cc = M.dc[DM / 2], co = (double)M.dco;
+        double a = 0.0;
+        auto run = [&](auto qf) {
+            spmv_dia_lap_f64<DM>(M, p, [&](int i, double S, double pc) {
+                const double y = qf(S, pc);
+                q[i] = y;
+                a = fma(pc, y, a);
+            });
+        };
+        if (co == -1.0) run([&](double S, double pc) { return fma(cc, pc, -S); });
+        else run([&](double S, double pc) { return fma(co, S, cc * pc); });
+        pq = a;
+    } else if constexpr (DM != 0 && A::kind == 1) {
         DotAcc d{0.f, 0.f};
         spmv_dia_df<DM>(M, p, [&](int i, df64 y0, df64 x0, df64 y1, df64 x1, bool has1) {
             if (has1) st_pair(q + i, y0, y1);
@@ -159,21 +185,20 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, int diag, typena
     using R = typename A::R;
     if (done_of(ctrl)) return;
     __shared__ double red[2 * (kThreads / 32)];
-    const R alpha = A::from_d(ctrl->pcg_alpha);
+    const R alpha = A::from_d(ctrl->pcg_alpha), nalpha = A::from_d(-ctrl->pcg_alpha);
     const R dc = A::from_d(dinv_c);
     R rr = A::zero(), ru = A::zero();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         R pi = A::ld(p + i);
         R xi = A::fma(alpha, pi, A::ld(x + i));
-        R ri = A::sub(A::ld(r + i), A::mul(alpha, A::ld(q + i)));
+        R ri = A::fma(nalpha, A::ld(q + i), A::ld(r + i));
         A::st(x + i, xi);
         A::st(r + i, ri);
         rr = A::fma(ri, ri, rr);
-        if (diag) {
-            R ui = dinv ? A::mul(A::ld(dinv + i), ri) : (dinv_c != 0.0 ? A::mul(dc, ri) : ri);
-            ru = A::fma(ri, ui, ru);
-        }
+        if (diag && dinv) ru = A::fma(ri, A::mul(A::ld(dinv + i), ri), ru);
     }
+    // u = B^-1 r with B^-1 the constant dinv_c (or the identity): u . r = dinv_c ||r||^2
+    if (diag && !dinv) ru = dinv_c != 0.0 ? A::mul(dc, rr) : rr;
     R v[2] = {rr, ru};
     double out[2];
     block_sum<A, 2>(v, red, out);
@@ -512,8 +537,13 @@ int dispatch_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x,
     // Chebyshev preconditioner's steps stage CSR tiles)
     const bool dia = mat->dia && mat->prec != SSCG_PREC_CHEB;
     if (arith == SSCG_ARITH_F64) {
-        if (dia) return run_pcg<ArithF64, VAL_F64, 1>(ctx, mat, b, x, maxit, L, scale ? mat->dinv : nullptr, h, P, coef);
-        return run_pcg<ArithF64, VAL_F64, 0>(ctx, mat, b, x, maxit, L, scale ? mat->dinv : nullptr, h, P, coef);
+        const double* d = scale ? mat->dinv : nullptr;
+        // every PCG layout carves margins around p, the only vector the SpMV gathers
+        const int dm = dia ? dia_mode(mat, true) : 0;
+        if (dm == 7) return run_pcg<ArithF64, VAL_F64, 7>(ctx, mat, b, x, maxit, L, d, h, P, coef);
+        if (dm == 27) return run_pcg<ArithF64, VAL_F64, 27>(ctx, mat, b, x, maxit, L, d, h, P, coef);
+        if (dm != 0) return run_pcg<ArithF64, VAL_F64, 1>(ctx, mat, b, x, maxit, L, d, h, P, coef);
+        return run_pcg<ArithF64, VAL_F64, 0>(ctx, mat, b, x, maxit, L, d, h, P, coef);
     }
     const float2* d = scale ? mat->dinv_df : nullptr;
     // every PCG layout carves margins around p, the only vector the SpMV gathers
@@ -591,6 +621,11 @@ int solve_pcg(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     if (h.status == SSCG_ERR_NONFINITE) {
         delete prof;
         return set_err(ctx, SSCG_ERR_NONFINITE, "non-finite right-hand side or x0");
+    }
+    if (h.status == SSCG_ERR_INVALID) {
+        delete prof;
+        return set_err(ctx, SSCG_ERR_INVALID, "right-hand side with max |b_i| outside [2^-30, 2^30], where double-float "
+                                              "vectors and norms stay in FP32's exponent range; scale b or use f64");
     }
     if (info) fill_profile(info, *prof, h.step);
     delete prof;

@@ -1,0 +1,192 @@
+// Arithmetic throughput probes (include/sscg_probe.h): one kernel per
+// instruction kind, every thread running kChains independent dependency
+// chains so that latency is hidden, over a full-device grid, timed with CUDA
+// events.  Results are kept alive through a comparison against a value the
+// chains never reach, so no store happens and the compiler cannot drop the
+// work.
+#include "../../include/sscg_probe.h"
+#include "internal.h"
+
+namespace {
+
+constexpr int kChains = 8;    // independent chains per thread (FP64, FP32, integer kinds)
+constexpr int kMmaAcc = 8;    // independent 8x8 accumulators per warp (DMMA kind)
+constexpr int kProbeThreads = 256;
+
+__device__ double g_probe_sink;  // written only if a chain hits an impossible value
+
+__device__ __forceinline__ void dmma_m8n8k4(double& d0, double& d1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                 : "+d"(d0), "+d"(d1)
+                 : "d"(a), "d"(b));
+}
+
+__device__ __forceinline__ double dfma_chains(long long iters, double seed, double m, double c) {
+    double a[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; k++) a[k] = seed + k;
+    for (long long it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < kChains; k++) a[k] = fma(a[k], m, c);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < kChains; k++) t += a[k];
+    return t;
+}
+
+__device__ __forceinline__ double dmma_chains(long long iters, double seed) {
+    double acc[kMmaAcc][2];
+#pragma unroll
+    for (int k = 0; k < kMmaAcc; k++) acc[k][0] = acc[k][1] = seed;
+    const double a = 1e-3 + 1e-6 * (threadIdx.x & 31), b = 1e-3 - 1e-6 * (threadIdx.x & 31);
+    for (long long it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < kMmaAcc; k++) dmma_m8n8k4(acc[k][0], acc[k][1], a, b);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < kMmaAcc; k++) t += acc[k][0] + acc[k][1];
+    return t;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kProbeThreads) k_probe(long long iters_a, long long iters_b, double seed) {
+    double t = 0.0;
+    if constexpr (KIND == SSCG_PROBE_DFMA) {
+        t = dfma_chains(iters_a, seed, 1.0 - 0x1p-30, 1e-7);
+    } else if constexpr (KIND == SSCG_PROBE_DADD) {
+        double a[kChains];
+#pragma unroll
+        for (int k = 0; k < kChains; k++) a[k] = seed + k;
+        const double c = 1e-9 * seed;
+        for (long long it = 0; it < iters_a; it++) {
+#pragma unroll
+            for (int k = 0; k < kChains; k++) a[k] = a[k] + c;
+        }
+#pragma unroll
+        for (int k = 0; k < kChains; k++) t += a[k];
+    } else if constexpr (KIND == SSCG_PROBE_DMUL) {
+        double a[kChains];
+#pragma unroll
+        for (int k = 0; k < kChains; k++) a[k] = seed + k;
+        const double m = 1.0 - 0x1p-30 * seed;
+        for (long long it = 0; it < iters_a; it++) {
+#pragma unroll
+            for (int k = 0; k < kChains; k++) a[k] = a[k] * m;
+        }
+#pragma unroll
+        for (int k = 0; k < kChains; k++) t += a[k];
+    } else if constexpr (KIND == SSCG_PROBE_DMMA) {
+        t = dmma_chains(iters_a, seed);
+    } else if constexpr (KIND == SSCG_PROBE_DFMA_DMMA) {
+        // warp-uniform split: even warps on the FP64 FMA pipe, odd warps on the tensor instruction
+        if (((threadIdx.x >> 5) & 1) == 0) t = dfma_chains(iters_a, seed, 1.0 - 0x1p-30, 1e-7);
+        else t = dmma_chains(iters_b, seed);
+    } else if constexpr (KIND == SSCG_PROBE_FFMA) {
+        float a[kChains];
+#pragma unroll
+        for (int k = 0; k < kChains; k++) a[k] = (float)seed + k;
+        const float m = 1.0f - 0x1p-20f, c = 1e-6f;
+#pragma unroll 4
+        for (long long it = 0; it < iters_a; it++) {
+#pragma unroll
+            for (int k = 0; k < kChains; k++) a[k] = fmaf(a[k], m, c);
+        }
+#pragma unroll
+        for (int k = 0; k < kChains; k++) t += a[k];
+    } else if constexpr (KIND == SSCG_PROBE_IALU) {
+        unsigned x[kChains];
+        const unsigned y = 0x9E3779B9u ^ (unsigned)seed, z = 0x7F4A7C15u + threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < kChains; k++) x[k] = threadIdx.x * 2654435761u + k;
+        // each step mixes a neighbouring chain in, so the chains cannot be run one after another
+#pragma unroll 4
+        for (long long it = 0; it < iters_a; it++) {
+            unsigned nx[kChains];
+#pragma unroll
+            for (int k = 0; k < kChains; k++) nx[k] = (x[k] ^ x[(k + 1) % kChains] ^ y) + z;
+#pragma unroll
+            for (int k = 0; k < kChains; k++) x[k] = nx[k];
+        }
+        unsigned u = 0;
+#pragma unroll
+        for (int k = 0; k < kChains; k++) u ^= x[k];
+        t = (double)u - 1.0;  // -1 only if every chain ends at 0
+    } else {
+        unsigned x[kChains];
+        const unsigned m = 2654435761u ^ (unsigned)seed;
+#pragma unroll
+        for (int k = 0; k < kChains; k++) x[k] = threadIdx.x + k;
+#pragma unroll 4
+        for (long long it = 0; it < iters_a; it++) {
+            unsigned nx[kChains];
+#pragma unroll
+            for (int k = 0; k < kChains; k++) nx[k] = x[k] * m + x[(k + 1) % kChains];
+#pragma unroll
+            for (int k = 0; k < kChains; k++) x[k] = nx[k];
+        }
+        unsigned u = 0;
+#pragma unroll
+        for (int k = 0; k < kChains; k++) u ^= x[k];
+        t = (double)u - 1.0;  // -1 only if every chain ends at 0
+    }
+    if (t == -1.0) g_probe_sink = t;  // never true: keeps the chains live
+}
+
+template <int KIND>
+int run_probe(sscg_ctx* ctx, long long ia, long long ib, double* ops, double* ms) {
+    int per_sm = 0;
+    SSCG_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe<KIND>, kProbeThreads, 0));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+    const long long grid = (long long)ctx->sm_count * per_sm;
+    cudaEvent_t e0, e1;
+    SSCG_CUDA(ctx, cudaEventCreate(&e0));
+    SSCG_CUDA(ctx, cudaEventCreate(&e1));
+    SSCG_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+    k_probe<KIND><<<(unsigned)grid, kProbeThreads, 0, ctx->stream>>>(ia, ib, 1.0 + 1e-3 * KIND);
+    cudaError_t le = cudaGetLastError();
+    SSCG_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+    SSCG_CUDA(ctx, cudaEventSynchronize(e1));
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (le != cudaSuccess) return sscg::set_err(ctx, SSCG_ERR_CUDA, "probe launch: %s", cudaGetErrorString(le));
+    const double threads = (double)grid * kProbeThreads, warps = threads / 32.0;
+    double n = 0.0;
+    switch (KIND) {
+        case SSCG_PROBE_DMMA: n = warps * (double)ia * kMmaAcc * 256.0; break;
+        case SSCG_PROBE_DFMA_DMMA:
+            n = threads / 2 * (double)ia * kChains + warps / 2 * (double)ib * kMmaAcc * 256.0;
+            break;
+        case SSCG_PROBE_IALU: n = threads * (double)ia * kChains * 2.0; break;
+        default: n = threads * (double)ia * kChains;
+    }
+    *ms = t;
+    *ops = t > 0.f ? n / (t * 1e-3) : 0.0;
+    return SSCG_OK;
+}
+
+}  // namespace
+
+extern "C" int sscg_probe_rate(sscg_ctx* ctx, int kind, int64_t iters_a, int64_t iters_b, double* ops_per_s,
+                               double* ms) {
+    if (!ctx) return SSCG_ERR_INVALID;
+    if (!ops_per_s || !ms) return sscg::set_err(ctx, SSCG_ERR_INVALID, "null output");
+    const int64_t lim = (int64_t)1 << 40;
+    if (iters_a <= 0 || iters_a > lim || (kind == SSCG_PROBE_DFMA_DMMA && (iters_b <= 0 || iters_b > lim)))
+        return sscg::set_err(ctx, SSCG_ERR_INVALID, "iteration counts must lie in 1..2^40");
+    switch (kind) {
+        case SSCG_PROBE_DFMA: return run_probe<SSCG_PROBE_DFMA>(ctx, iters_a, iters_b, ops_per_s, ms);
+        case SSCG_PROBE_DADD: return run_probe<SSCG_PROBE_DADD>(ctx, iters_a, iters_b, ops_per_s, ms);
+        case SSCG_PROBE_DMUL: return run_probe<SSCG_PROBE_DMUL>(ctx, iters_a, iters_b, ops_per_s, ms);
+        case SSCG_PROBE_DMMA: return run_probe<SSCG_PROBE_DMMA>(ctx, iters_a, iters_b, ops_per_s, ms);
+        case SSCG_PROBE_DFMA_DMMA: return run_probe<SSCG_PROBE_DFMA_DMMA>(ctx, iters_a, iters_b, ops_per_s, ms);
+        case SSCG_PROBE_FFMA: return run_probe<SSCG_PROBE_FFMA>(ctx, iters_a, iters_b, ops_per_s, ms);
+        case SSCG_PROBE_IALU: return run_probe<SSCG_PROBE_IALU>(ctx, iters_a, iters_b, ops_per_s, ms);
+        case SSCG_PROBE_IMAD: return run_probe<SSCG_PROBE_IMAD>(ctx, iters_a, iters_b, ops_per_s, ms);
+        default: return sscg::set_err(ctx, SSCG_ERR_INVALID, "unknown probe kind %d", kind);
+    }
+}

@@ -441,6 +441,38 @@ __device__ __forceinline__ void spmv_dia_df(const MatView& M, const TX* __restri
 }
 
 // ---------------------------------------------------------------------------
+// Diagonal form in FP64, Laplacian class, over a margined vector.
+//
+// On a GB300 the FP64 units retire about 2 operations per clock per SM, 1/60
+// of the FP32 and 1/40 of the integer rate, so an FP64 stencil row is bound by
+// its FP64 operations, not its bytes.  This form spends the fewest: the
+// off-centre neighbours are summed (K - 2 additions; a term whose mask bit is
+// clear is replaced by zero with an integer select before it enters) and the
+// caller combines the sum S with the centre value in one FMA, e.g.
+// D^-1 A x = x + (c_off / d) S for the Jacobi-scaled level.  x must be
+// readable at every index in [-g, n + g) for g >= max |offset| (the solvers
+// carve such margins).  epi(i, S, x_i) runs once per row, rows grid-stride.
+template <int K, class EPI>
+__device__ __forceinline__ void spmv_dia_lap_f64(const MatView& M, const double* __restrict__ x, EPI epi) {
+    constexpr int C = K / 2;  // symmetric pattern: offset 0 sits in the middle
+    const int n = M.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t m = __ldg(M.dmask + i);
+        double v[K];
+#pragma unroll
+        for (int t = 0; t < K; t++) v[t] = __ldg(x + (i + M.doff[t]));
+        double S = 0.0;
+#pragma unroll
+        for (int t = 0; t < K; t++) {
+            if (t == C) continue;
+            const double w = ((m >> t) & 1u) ? v[t] : 0.0;
+            S = (t == 0) ? w : S + w;  // the first term starts the sum
+        }
+        epi(i, S, v[C]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // TMA-pipelined row tiles.
 //
 // Each CTA walks its tiles (blockIdx.x, +gridDim.x, ...) through NS shared

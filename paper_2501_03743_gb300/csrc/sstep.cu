@@ -1,21 +1,27 @@
-// Preconditioned s-step CG (Algorithm 3) on one GPU.
+// Preconditioned s-step CG (Algorithm 3) on one GPU, monomial basis, B
+// diagonal (Jacobi) or the identity.
 //
-// Per outer step i the device runs
-//   s x k_level  : one level of the preconditioned matrix-powers kernel
-//                  (Algorithm 4): AU_j = A u_j and u_{j+1} = B^-1 A u_j, with
-//                  the moments of Algorithm 5 accumulated in the epilogue as
-//                  mu_{2j+1} = u_j . A u_j and mu_{2j+2} = (A u_j) . B^-1 (A u_j).
-//                  The last level's last CTA reduces the moments and solves
-//                  the s x s systems of Algorithm 6 on chip.
-//   1 x k_update : the block updates of Algorithm 3 (P = U + P_old beta,
-//                  AP = AU + AP_old beta, x += P alpha, r -= AP alpha) in one
-//                  pass, fused with z = B^-1 r for the next step, ||r||^2 and
-//                  mu_0 = r . z; its last CTA tests convergence.
-// The two n x 2s blocks of Algorithm 3 (P1, P2) alternate between "new"
-// and "old" with the step parity; P and AP overwrite U and AU in place.
+// The device carries z = B^-1 r and Q = B^-1 A P instead of r and A P (the
+// recurrences of Algorithm 3 multiplied by B^-1), so the matrix-powers
+// levels never store A U: B^-1 A U_{1..s} = U_{2..s+1}.  Per outer step i:
+//   s x k_level    : one level of the preconditioned matrix-powers kernel
+//                    (Algorithm 4): u_{j+1} = B^-1 A u_j, with the moments of
+//                    Algorithm 5 accumulated in the epilogue as
+//                    mu_{2j+1} = u_j . A u_j and mu_{2j+2} = (A u_j) . B^-1 (A u_j).
+//                    The last level's last CTA reduces the moments and solves
+//                    the s x s systems of Algorithm 6 on chip.
+//   1 x k_update_q : the block updates P = U + P_old beta, Q = U_{2..s+1} +
+//                    Q_old beta, x += P alpha, z -= Q alpha in one pass, with
+//                    ||r||^2 and mu_0 = r . z of the new residual; its last CTA
+//                    tests convergence.
+// A block holds 2s+1 columns (U_1..U_{s+1} | Q); the two blocks (the P1, P2 of
+// Algorithm 3) alternate between "new" and "old" with the step parity.  With
+// SSCG_FUSED_MPK the levels run in the fused kernel below instead and the
+// update keeps r and A P (k_update_tma).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -59,7 +65,37 @@ __global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1) k_level(MatView M, 
         }
     };
     bool ok = true;
-    if constexpr (DM != 0 && A::kind == 1) {
+    if constexpr (DM >= 7 && A::kind == 0) {
+        // Diagonal form, Laplacian class, FP64 (spmv_dia_lap_f64): with the
+        // neighbour sum S, u_{j+1} = u + (c_off / d) S under Jacobi (B^-1 the
+        // constant 1/d) and c_centre u + c_off S without a preconditioner;
+        // mu_{2j+1} = u . A u = d sum u u_{j+1} and mu_{2j+2} = d sum u_{j+1}^2
+        // (d = 1 without a preconditioner): three FP64 operations a row beyond
+        // the sum, the moments' scale applied once per thread.
+        const double cc = M.dc[DM / 2], co = (double)M.dco;
+        const bool jac = dinv_c != 0.0;
+        const double cz = co * dinv_c, ds = jac ? cc : 1.0;
+        double a1 = 0.0, a2 = 0.0;
+        auto run = [&](auto zf, auto m2on) {
+            spmv_dia_lap_f64<DM>(M, u_in, [&](int i, double S, double xc) {
+                const double z = zf(S, xc);
+                u_next[i] = z;
+                a1 = fma(xc, z, a1);
+                if (decltype(m2on)::value) a2 = fma(z, z, a2);
+            });
+        };
+        if (jac) {
+            auto zf = [&](double S, double xc) { return fma(S, cz, xc); };
+            if (want_m2) run(zf, std::true_type{});
+            else run(zf, std::false_type{});
+        } else {
+            auto zf = [&](double S, double xc) { return fma(co, S, cc * xc); };
+            if (want_m2) run(zf, std::true_type{});
+            else run(zf, std::false_type{});
+        }
+        m1 = ds * a1;
+        m2 = ds * a2;
+    } else if constexpr (DM != 0 && A::kind == 1) {
         // Diagonal form (double-float): B^-1 is the constant dinv_c (Jacobi) or
         // the identity (dinv_c = 0), the level always writes u_{j+1} and never
         // AU_j.  Rows come in pairs; the moments are running Dot2 sums,
@@ -583,7 +619,11 @@ int solve_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, 
     if (o->arith == SSCG_ARITH_F64) {
         const double* dinv = jac ? mat->dinv : nullptr;
         const double* diag = jac ? mat->diag : nullptr;
-        if (dia) rc = run_sstep_sb<ArithF64, VAL_F64, 1>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        // plan() carves margins around both blocks whenever the matrix has the diagonal form
+        const int dm = dia ? dia_mode(mat, true) : 0;
+        if (dm == 7) rc = run_sstep_sb<ArithF64, VAL_F64, 7>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        else if (dm == 27) rc = run_sstep_sb<ArithF64, VAL_F64, 27>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
+        else if (dm != 0) rc = run_sstep_sb<ArithF64, VAL_F64, 1>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
         else rc = run_sstep_sb<ArithF64, VAL_F64, 0>(ctx, mat, bd, xd, o, L, dinv, diag, &h, *prof);
     } else {
         const float2* dinv = jac ? mat->dinv_df : nullptr;
@@ -607,6 +647,11 @@ int solve_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, 
     if (h.status == SSCG_ERR_NONFINITE) {
         delete prof;
         return set_err(ctx, SSCG_ERR_NONFINITE, "non-finite right-hand side or x0");
+    }
+    if (h.status == SSCG_ERR_INVALID) {
+        delete prof;
+        return set_err(ctx, SSCG_ERR_INVALID, "right-hand side with max |b_i| outside [2^-30, 2^30], where double-float "
+                                              "vectors and norms stay in FP32's exponent range; scale b or use f64");
     }
     if (info) fill_profile(info, *prof, h.step);
     delete prof;

@@ -273,6 +273,11 @@ int solve_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, c
         delete prof;
         return set_err(ctx, SSCG_ERR_NONFINITE, "non-finite right-hand side or x0");
     }
+    if (h.status == SSCG_ERR_INVALID) {
+        delete prof;
+        return set_err(ctx, SSCG_ERR_INVALID, "right-hand side with max |b_i| outside [2^-30, 2^30], where double-float "
+                                              "vectors and norms stay in FP32's exponent range; scale b or use f64");
+    }
     if (info) fill_profile(info, *prof, h.step);
     delete prof;
     if (info) {

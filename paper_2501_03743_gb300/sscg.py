@@ -36,7 +36,10 @@ EXPORTS = (
     "sscg_mlp_workspace_bytes", "sscg_mlp_forward", "sscg_mlp_loss_grad", "sscg_mlp_adam_step", "sscg_mlp_train",
     "sscg_bounds_mlp", "sscg_set_bounds_model", "sscg_batch_workspace_bytes", "sscg_batch_create",
     "sscg_batch_destroy", "sscg_batch_solve", "sscg_batch_props", "sscg_batch_launches",
+    "sscg_probe_rate", "sscg_batch_inject_barrier_fault",
 )
+# Probe kinds of include/sscg_probe.h.
+PROBE = {"dfma": 0, "dadd": 1, "dmul": 2, "dmma": 3, "dfma_dmma": 4, "ffma": 5, "ialu": 6, "imad": 7}
 BATCH_MAX_RHS = 8
 BATCH_PERSISTENT = 0x10
 BATCH_MAX_S = 8
@@ -125,6 +128,8 @@ def load(path: str | None = None):
     L.sscg_batch_solve.argtypes = [vp, vp, vp, vp, vp, vp]
     L.sscg_batch_props.argtypes = [vp, vp, P(i32), P(i32), P(C.c_float)]
     L.sscg_batch_launches.argtypes = [vp, P(C.c_int64)]
+    L.sscg_probe_rate.argtypes = [vp, i32, i64, i64, P(dbl), P(dbl)]
+    L.sscg_batch_inject_barrier_fault.argtypes = [vp, i32, i32]
     _lib = L
     return L
 
@@ -171,6 +176,14 @@ class Context:
         out = torch.empty(n, dtype=torch.float64, device="cuda")
         self.check(self.lib.sscg_uniform(self.h, n, seed, C.c_void_p(out.data_ptr())))
         return out
+
+    def probe_rate(self, kind, iters_a, iters_b=0):
+        """Throughput probe of include/sscg_probe.h: (operations per second
+        over the device, kernel milliseconds)."""
+        ops, ms = C.c_double(), C.c_double()
+        self.check(self.lib.sscg_probe_rate(self.h, PROBE[kind], int(iters_a), int(iters_b), C.byref(ops),
+                                            C.byref(ms)))
+        return ops.value, ms.value
 
     def check(self, rc, allow_positive=False):
         if rc < 0 or (rc > 0 and not allow_positive):
@@ -295,7 +308,7 @@ DIRECT_GRAM = 0x4
 FUSED_MPK = 0x8
 
 
-def make_opts(s=4, basis="monomial", tol=1e-8, maxit=1000, arith="df64", basis_bounds=(0.0, 0.0),
+def make_opts(s=4, basis="monomial", tol=1e-8, maxit=1000, arith="f64", basis_bounds=(0.0, 0.0),
               replace_every=0, host_vectors=False, profile=False, direct_gram=False, fused_mpk=False) -> Opts:
     flags = (HOST_VECTORS if host_vectors else 0) | (PROFILE if profile else 0) | (DIRECT_GRAM if direct_gram else 0)
     flags |= FUSED_MPK if fused_mpk else 0
@@ -358,7 +371,7 @@ class BatchSolver:
     """Plan for solving many systems (each with 1..8 right-hand sides) in one
     persistent launch; see sscg_batch_create."""
 
-    def __init__(self, mats, nrhs, s=4, tol=1e-8, maxit=1000, arith="df64", tune=False, persistent=False):
+    def __init__(self, mats, nrhs, s=4, tol=1e-8, maxit=1000, arith="f64", tune=False, persistent=False):
         torch = _torch()
         self.mats = list(mats)
         self.nrhs = [int(r) for r in nrhs]
@@ -391,6 +404,12 @@ class BatchSolver:
         self.ctx.check(self.ctx.lib.sscg_batch_launches(self.h, C.byref(nl)))
         return dict(tile_rows=list(tiles), grid=grid.value, graph=bool(graph.value), last_ms=ms.value,
                     launches=nl.value)
+
+    def inject_barrier_fault(self, cta, wait_ms):
+        """Arm the next solve of a persistent plan: CTA `cta` skips its first
+        grid-barrier arrival and barrier waits give up after wait_ms (the
+        solve then returns TIMEOUT); cta=-1 disarms."""
+        self.ctx.check(self.ctx.lib.sscg_batch_inject_barrier_fault(self.h, int(cta), int(wait_ms)))
 
     def solve(self, B, X) -> BatchResult:
         """B[k], X[k]: FP64 device tensors of shape (nrhs[k], n_k) (each

@@ -53,3 +53,32 @@ def test_family_roofline_picks_the_dominant_family(monkeypatch):
     # 3 GB per record, 10 records in 30 ms: 1000 GB/s
     assert r["achieved"] == pytest.approx(1000.0) and r["frac"] == pytest.approx(0.125)
     assert r["bound"] == "hbm" and r["traffic"] is None and r["peak"] == 8000.0
+
+
+def test_value_is_kernel_bytes_over_time_and_stays_below_the_copy_bandwidth():
+    """value = the bytes the solve's kernels move per second; at the 256^3
+    s = 4 solve measured on the GB300 (130 outer steps in 122.2 ms, the
+    double-float run) it sits below the measured copy bandwidth, while the
+    Algorithm 3 yardstick over the same time would read 1.9x above it."""
+    n, nnz, s, outer, ms, hbm = 256 ** 3, 117_047_296, 4, 130, 122.155, 6786.6
+    bm = bench.byte_model(n, nnz, 4, s, "df64", fused=False, dia=True)
+    value = bench.sstep_bytes(bm, outer) / (ms * 1e-3) / 1e9
+    assert value <= 1.2 * hbm and value == pytest.approx(4872, rel=1e-3)
+    yard = bench.sstep_bytes(bench.yardstick(n, nnz, s), outer) / (ms * 1e-3) / 1e9
+    assert yard > hbm
+
+
+def test_fp64_operation_model():
+    ops = bench.fp64_ops_model(4, K=7)
+    # level: 5 additions (6 neighbours), u_{j+1}, two moments (one on the last level)
+    assert ops["level"] == [8, 8, 8, 7]
+    # update: s^2 for P and Q each, s for x and z each, one for sum z^2
+    assert ops["update"] == 2 * 16 + 2 * 4 + 1 and ops["update_first"] == 9
+    assert (ops["pcg_spmv"], ops["pcg_update"], ops["pcg_dir"]) == (7, 3, 2)
+    assert bench.fp64_ops_model(2, K=27)["level"] == [28, 27]
+
+
+def test_fp64_alu_peak_is_two_per_clock_per_sm():
+    # 2 x 152 SMs x 2070 MHz = 629.3 G operations/s, the nominal 1.25 TFLOP/s (FMA = 2 FLOPs)
+    assert bench.alu_peak(152) == pytest.approx(629.28e9)
+    assert 2 * bench.alu_peak(152) == pytest.approx(1.25e12, rel=0.01)

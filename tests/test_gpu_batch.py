@@ -224,3 +224,40 @@ def test_batch_invalid_arguments(ctx):
     rc = ctx.lib.sscg_batch_create(ctx.h, 1, mh, nr, C.byref(ok), 0, C.c_void_p(ws.data_ptr()), nb.value - 256,
                                    C.byref(h))
     assert rc == sscg.ERR_SPACE
+
+
+def test_bounded_barrier_wait_runs_out(ctx):
+    """Failure detection without a GPU fault: one CTA of the persistent
+    solve's cooperative launch skips its first grid-barrier arrival, so every
+    other CTA's bounded wait (200 ms here) runs out.  The solve must come
+    back with SSCG_TIMEOUT well inside a second, and the same plan's next
+    solve must succeed and agree with a clean solve."""
+    import time
+
+    spec = [("poisson7", 12, 0, 2), ("varcoef7", 10, 3, 1)]
+    mats, csrs, B, X = make_batch(ctx, spec, rhs_seed=31)
+    plan = sscg.BatchSolver(mats, [m[3] for m in spec], s=4, tol=1e-9, maxit=300, persistent=True)
+    grid = plan.props()["grid"]
+    for x in X:
+        x.zero_()
+    ref = plan.solve(B, X)
+    assert ref.status == sscg.OK
+    x_ref = [x.clone() for x in X]
+    for cta in (0, grid - 1):
+        plan.inject_barrier_fault(cta, 200)
+        for x in X:
+            x.zero_()
+        t0 = time.perf_counter()
+        bad = plan.solve(B, X)
+        assert bad.status == sscg.TIMEOUT
+        assert time.perf_counter() - t0 < 5.0
+        for x in X:
+            x.zero_()
+        again = plan.solve(B, X)  # disarmed: the plan and the context are still usable
+        assert again.status == sscg.OK
+        for x, xr in zip(X, x_ref):
+            assert torch.equal(x, xr)
+    with pytest.raises(sscg.SscgError):
+        plan.inject_barrier_fault(grid, 200)
+    with pytest.raises(sscg.SscgError):
+        sscg.BatchSolver(mats, [m[3] for m in spec], s=4, tol=1e-9, maxit=300).inject_barrier_fault(0, 200)
