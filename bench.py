@@ -25,6 +25,7 @@ Reported:
              per SM at the maximum SM clock; in df64 "hbm", the bytes the
              kernels move against the measured copy bandwidth
   pcg_*      plain PCG (Algorithm 1) on the same kernels and arithmetic
+  pfcg_*     PFCG-NN (Algorithm 2, one reduction per iteration), likewise
   df64_*     (FP64 runs) the same solve and PCG in double-float
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same solve
 
@@ -102,14 +103,17 @@ def parse():
 # ------------------------------------------------------------ byte model
 
 # DRAM bytes (read + write) per row and launch that ncu --set full measured
-# for this workload's kernels (7-point stencil in the diagonal form, df64,
-# s = 4, sequential levels) at n = 4,096,000 (profiles/
-# k_level_dia_k_update_q_poisson7_160_df64_s4.txt): a level (mean of two
-# captured launches; at that size L2 still holds most of the level's writes
-# when it ends) and the block update.  The roofline's "traffic" scales them
-# to the workload's n; it is null for any other configuration.
-NCU_TRAFFIC_PER_ROW = {"mpk": 54.0e6 / 4.096e6, "update": 732.694e6 / 4.096e6}
-NCU_TRAFFIC_CONFIG = dict(s=4, arith="df64", fused_mpk=False, dia=True)
+# for this workload's kernels (7-point stencil in the diagonal form, s = 4,
+# sequential levels) at n = 4,096,000: a level (mean of the captured
+# launches; at that size L2 still holds most of the level's writes when it
+# ends) and the block update, per arithmetic (profiles/
+# k_level_k_update_q_poisson7_160_f64_s4.txt, k_level_dia_k_update_q_poisson7_160_df64_s4.txt).
+# The roofline's "traffic" scales them to the workload's n; it is null for any
+# other configuration.
+NCU_TRAFFIC_PER_ROW = {
+    "f64": {"mpk": 54.2e6 / 4.096e6, "update": 734.1e6 / 4.096e6},
+    "df64": {"mpk": 54.0e6 / 4.096e6, "update": 732.694e6 / 4.096e6},
+}
 
 
 def byte_model(n, nnz, vbytes, s, arith, fused=False, dia=False):
@@ -132,10 +136,10 @@ def byte_model(n, nnz, vbytes, s, arith, fused=False, dia=False):
 
 def traffic(a, family, n, dia):
     """Measured DRAM bytes per launch of `family`, scaled to n rows, or None."""
-    cfg = dict(s=a.s, arith=a.arith, fused_mpk=bool(a.fused_mpk), dia=bool(dia))
-    if cfg != NCU_TRAFFIC_CONFIG or family not in NCU_TRAFFIC_PER_ROW:
+    per = NCU_TRAFFIC_PER_ROW.get(a.arith)
+    if per is None or a.s != 4 or a.fused_mpk or not dia or family not in per:
         return None
-    return round(NCU_TRAFFIC_PER_ROW[family] * n)
+    return round(per[family] * n)
 
 
 def yardstick(n, nnz, s):
@@ -278,6 +282,25 @@ def family_roofline(res, bytes_per_record, names):
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": None, "kernel": names[dom], "peak_source": src,
             "family_ms_per_solve": {f: round(v[0], 3) for f, v in fam.items()}}
+
+
+def family_alu_roofline(res, ops_per_record, names, sm_count):
+    """FP64 ALU roofline of a solve's dominant kernel family from the library's
+    CUDA events: ops_per_record[f] FP64 operations per timed record of f."""
+    fam = {}
+    for f in ops_per_record:
+        t, c = res.profile[f"t_{f}_ms"], res.profile[f"n_{f}"]
+        if c:
+            fam[f] = (t, c)
+    dom = max(fam, key=lambda f: fam[f][0])
+    t, c = fam[dom]
+    peak = alu_peak(sm_count)
+    achieved = ops_per_record[dom] / (t / c * 1e-3)
+    return {"bound": "alu", "achieved": round(achieved / 1e9, 1), "peak": round(peak / 1e9, 1), "unit": "Gop/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "kernel": names[dom],
+            "peak_source": "FP64 operations at 2 per clock per SM x SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
+            "family_ms_per_solve": {f: round(v[0], 3) for f, v in fam.items()},
+            "family_frac": {f: round(ops_per_record[f] / (v[0] / v[1] * 1e-3) / peak, 4) for f, v in fam.items()}}
 
 
 def workload_name(N, s, arith):
@@ -453,6 +476,15 @@ def main():
                 if c:
                     pf[key] = round(fo * n / (t / c * 1e-3) / 1e9, 1)
             pcg["pcg_family_gops"] = pf
+        # PFCG-NN (Algorithm 2), the paper's comparison solver, on the same kernels and arithmetic
+        fsolver = sscg.Solver(A, method="pfcg", tol=a.tol, maxit=20000, arith=a.arith)
+        x.zero_()
+        fsolver.solve(b, x)
+        fms, fres = timed(lambda: fsolver.solve(b, x), max(1, min(a.steps, 3)))
+        pfcg_ms = max_over_ranks(pg, sum(fms)) / len(fms)
+        pcg.update(pfcg_solve_ms=round(pfcg_ms, 3), pfcg_iters=fres[-1].outer_iters,
+                   pfcg_rel_res_true=fres[-1].rel_res_true, speedup_vs_pfcg=round(pfcg_ms / ms_per_step, 4))
+        del fsolver
 
     # the same solve and PCG in double-float (pairs of FP32, about 48 bits, FP32 exponent range)
     df = None
@@ -689,7 +721,7 @@ def run_batch(a, world, rank, local, pg):
         line = {
             "metric": BATCH_METRIC, "value": round(value, 2), "unit": "rhs/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": round(solve_ms, 3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "df64", "data": "synthetic",
+            "vs_baseline": None, "dtype": a.arith, "data": "synthetic",
             "config": {"workload": f"serving mix: {len(spec)} systems (7-/27-point stencils, variable-coefficient "
                                    f"fields sigma in {{0.5,1,2,3}}) on 32^3..160^3 grids, 1..8 seeded RHS each "
                                    f"({total_rhs} RHS, {sum(n for n, _, _ in sizes):,} rows), s={a.s} monomial, "
@@ -723,8 +755,8 @@ MIXED_METRIC = "mixed-precision s-step PCG: 27-point 192^3 to rel. residual 1e-1
 
 def run_mixed27(a, world, rank, local, pg):
     """27-point stencil on 192^3 (a.N overrides), mixed precision (FP32 values
-    and basis, double-float Gram, P, AP, x, r, true-residual replacement every
-    outer step) to 1e-10, beside the double-float path to the same tolerance.
+    and basis, FP64 Gram sums, P, AP, x, r, FP64 true-residual replacement
+    every outer step) to 1e-10, beside the FP64 path to the same tolerance.
     The cpu_baseline leg solves the same system with the FP64 CPU oracle's PCG
     (timed on the host cores); its solution is also what the GPU solutions'
     error is measured against."""
@@ -752,7 +784,7 @@ def run_mixed27(a, world, rank, local, pg):
     b = torch.from_numpy(sysm["b"]).cuda()
     x = torch.zeros_like(b)
     out = {}
-    for name, kw in (("mixed", dict(arith="mixed", replace_every=1)), ("df64", dict(arith="df64"))):
+    for name, kw in (("mixed", dict(arith="mixed", replace_every=1)), ("f64", dict(arith="f64"))):
         solver = sscg.Solver(A, s=a.s, tol=1e-10, maxit=5000, profile=True, **kw)
         x.zero_()
         solver.solve(b, x)
@@ -772,11 +804,17 @@ def run_mixed27(a, world, rank, local, pg):
             sv = a.s
             # bytes per timed record (the mixed driver times the s levels, the Gram pass and
             # the update + residual replacement of an outer step as one record each)
-            mixed_roof = family_roofline(
-                res, {"mpk": (20 * sv - 4) * n, "dir": (28 * sv + 8) * n, "update": (44 * sv + 48) * n},
-                {"mpk": "k_mx_level x s (diagonal-form SpMV of the FP32 basis, AU in double-float)",
-                 "dir": "k_gram (G, C, m and q of the direct-Gram blocks)",
-                 "update": "k_mx_update + k_mx_replace (P, AP, x; r = r0 - A(x - x0))"})
+            # FP64 operations per timed record (the s levels, the Gram pass, the update with the
+            # replacement): levels 3 a row each (A U widened to FP64); Gram s(s+1)/2 + s + s^2 + s
+            # FMAs and s widenings; update 2 s^2 + s FMAs and s widenings, replacement 25
+            # additions, 3 FMAs and the FP32 rounding of B^-1 r
+            fam_ops = {"mpk": 3 * sv * n, "dir": (sv * (sv + 1) // 2 + 3 * sv + sv * sv) * n,
+                       "update": (2 * sv * sv + 2 * sv + 30) * n}
+            names = {"mpk": "k_mx_level x s (diagonal-form SpMV of the FP32 basis, AU widened to FP64)",
+                     "dir": "k_gram (G, C, m and q of the direct-Gram blocks, FP64 sums)",
+                     "update": "k_mx_update + k_mx_replace (P, AP, x; r = r0 - A(x - x0) in FP64)"}
+            mixed_roof = family_alu_roofline(res, fam_ops, names, torch.cuda.get_device_properties(local)
+                                             .multi_processor_count)
         out[name] = dict(ms=statistics.median(ms), outer=res.outer_iters, status=res.status, launches=nl,
                          rel_res_true=res.rel_res_true,
                          err_vs_oracle=float(np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x)),
@@ -785,14 +823,14 @@ def run_mixed27(a, world, rank, local, pg):
     if rank == 0:
         line = {"metric": MIXED_METRIC, "value": round(m["ms"], 3), "unit": "ms", "n_gpus": world,
                 "steps": a.steps, "warmup": 1, "ms_per_step": round(m["ms"], 3), "higher_is_better": False,
-                "scaling": "weak", "vs_baseline": None, "dtype": "mixed (fp32 basis, df64 accumulation)",
+                "scaling": "weak", "vs_baseline": None, "dtype": "mixed (fp32 basis and values, fp64 accumulation)",
                 "data": "synthetic",
                 "config": {"workload": f"poisson27 {N}^3 (n={n:,}, nnz={nnz:,}), Jacobi, s={a.s} monomial, "
                                        "b=A x_true, x0=0, tol 1e-10, true-residual replacement every outer step",
                            "parallelism": f"replicas x{world}"},
                 "mixed": {k: (round(v, 3) if k == "ms" else v) for k, v in m.items()},
-                "df64": {k: (round(v, 3) if k == "ms" else v) for k, v in out["df64"].items()},
-                "speedup_mixed_vs_df64": round(out["df64"]["ms"] / m["ms"], 3),
+                "f64": {k: (round(v, 3) if k == "ms" else v) for k, v in out["f64"].items()},
+                "speedup_mixed_vs_f64": round(out["f64"]["ms"] / m["ms"], 3),
                 "roofline": mixed_roof,
                 "gpu_launches": int(m["launches"]),
                 "cpu_baseline": {"value": round(t_oracle * 1e3, 1), "unit": "ms", "cores": oracle.num_threads(),
@@ -868,13 +906,17 @@ def run_cheb(a, world, rank, local, pg):
                 row[name] = {"ms": round(ms, 3), "status": r.status, "outer": r.outer_iters,
                              "rel_res_true": r.rel_res_true, "launches": r.profile["kernel_launches"]}
                 if name == "network" and sig == 3.0 and s == 8:
-                    nn, nz = A.n, len(c[1])
-                    Mb = 4 * (nn + 1) + 12 * nz  # CSR: int32 columns, double-float values
-                    cheb_roof = family_roofline(
-                        r, {"mpk": s * (Mb + 32 * nn), "dir": (24 * s + 8) * nn, "update": (48 * s + 48) * nn},
+                    nn = A.n
+                    # FP64 operations per timed record: s levels of a 7-point CSR row (7 FMAs, the
+                    # Jacobi scale, the Chebyshev recurrence's 3); the Gram pass's s(s+1)/2 + s + s^2
+                    # FMAs; the update's 2 s^2 + 2 s FMAs for P, AP, x, r and 3 for z and the norms
+                    cheb_roof = family_alu_roofline(
+                        r, {"mpk": 11 * s * nn, "dir": (s * (s + 1) // 2 + s + s * s) * nn,
+                            "update": (2 * s * s + 2 * s + 3) * nn},
                         {"mpk": "k_level_gen x s (CSR SpMV, AU stored, Chebyshev recurrence)",
                          "dir": "k_gram (G, C, m of the direct-Gram blocks)",
-                         "update": "k_update_ap (P, AP, x, r, z; s <= 8)"})
+                         "update": "k_update_ap (P, AP, x, r, z; s <= 8)"},
+                        torch.cuda.get_device_properties(local).multi_processor_count)
                     cheb_roof["workload"] = f"sigma=3 field {N}^3, Chebyshev basis s=8, network interval"
                     cheb_csr = c
             A.set_bounds_model(net.h, None)
@@ -903,7 +945,7 @@ def run_cheb(a, world, rank, local, pg):
         line = {"metric": CHEB_METRIC, "value": round(statistics.median(gain), 3) if gain else None,
                 "unit": "x (Lanczos-interval time / network-interval time, median)", "n_gpus": world,
                 "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "df64", "data": "synthetic",
+                "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"varcoef7 {N}^3, k = exp(sigma g), sigma in {{0.5,1,2,3}}, Jacobi, "
                                        "Chebyshev basis s in {8,12}, tol 1e-8",
                            "training": f"{len(samples)} seeded systems at 8^3..128^3, labels from device "

@@ -200,6 +200,19 @@ int sscg_pcg_workspace_bytes(const sscg_mat* mat, const sscg_opts* opts, size_t*
 int sscg_pcg_solve(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x,
                    const sscg_opts* opts, sscg_info* info, void* workspace, size_t workspace_bytes);
 
+/* PFCG-NN (Algorithm 2): Notay's flexible preconditioned CG, the paper's
+ * comparison solver.  Per iteration: one SpMV, one preconditioner apply, the
+ * three coupled dot products alpha = u.r, beta = u.w, gamma = u.s in one
+ * global reduction (with ||r||^2, so the stop test needs no second one) and
+ * the two coupled axpy pairs p, s and x, r.  B: Jacobi or none (otherwise
+ * SSCG_ERR_INVALID).  opts->s and basis are ignored; maxit counts iterations;
+ * f64 or df64 arithmetic.  Vectors, workspace rules and returns as for
+ * sscg_pcg_solve; SSCG_BREAKDOWN when rho_k = beta_k - gamma_k^2/rho_{k-1}
+ * is not positive. */
+int sscg_pfcg_workspace_bytes(const sscg_mat* mat, const sscg_opts* opts, size_t* bytes);
+int sscg_pfcg_solve(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x,
+                    const sscg_opts* opts, sscg_info* info, void* workspace, size_t workspace_bytes);
+
 /* y = A x (device FP64 vectors of length n), the library's CSR SpMV. */
 int sscg_spmv(sscg_ctx* ctx, const sscg_mat* mat, const double* x, double* y);
 

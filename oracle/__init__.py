@@ -24,7 +24,7 @@ _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
 PREC = {"none": 0, "jacobi": 1, "cheb": 2}
-BASIS = {"monomial": 0, "chebyshev": 1}
+BASIS = {"monomial": 0, "chebyshev": 1, "newton": 2}
 OK, NOT_CONVERGED, BREAKDOWN, ERR_INVALID = 0, 1, 2, -1
 
 
@@ -78,6 +78,7 @@ def lib():
         L.orc_pcgs.argtypes = [P(_Csr), P(_Prec), vp, vp, i32, dbl, i32, P(_Res), P(_Trace)]
         L.orc_pcgs_gram.argtypes = [P(_Csr), P(_Prec), vp, vp, i32, i32, dbl, dbl, dbl, i32, P(_Res), P(_Trace)]
         L.orc_pfcg.argtypes = [P(_Csr), P(_Prec), vp, vp, dbl, i32, P(_Res)]
+        L.orc_newton_shifts.argtypes = [i32, dbl, dbl, vp, P(dbl)]
         L.orc_chol_solve.argtypes = [i32, vp, i32, vp, vp]
         L.orc_tridiag_eig_extremes.argtypes = [i32, vp, vp, P(dbl), P(dbl)]
         L.orc_lanczos_bounds.argtypes = [P(_Csr), P(_Prec), vp, i32, P(dbl), P(dbl)]
@@ -248,6 +249,16 @@ def pcgs_gram(A, b, s, basis="monomial", bounds=(0.0, 0.0), x0=None, prec="jacob
     lib().orc_pcgs_gram(C.byref(A.c), C.byref(p), _ptr(b), _ptr(x), s, BASIS[basis], float(bounds[0]),
                         float(bounds[1]), tol, maxit, C.byref(res), C.byref(t) if t is not None else None)
     return Result(x, res.status, res.iters, res.relres, h[:res.hist_len].copy(), _untrace(t, bufs))
+
+
+def newton_shifts(s, lo, hi):
+    """(theta[0..s-2], sigma) of the Newton basis over [lo, hi] (orc_newton_shifts)."""
+    theta = np.zeros(max(s - 1, 1))
+    sig = C.c_double()
+    st = lib().orc_newton_shifts(int(s), float(lo), float(hi), _ptr(theta), C.byref(sig))
+    if st != OK:
+        raise ValueError("bad Newton-shift arguments")
+    return theta[: s - 1].copy(), sig.value
 
 
 def chol_solve(Adense, B):

@@ -467,10 +467,46 @@ done:
  *              u_{j+1} = 2 (B^-1 A u_j - c u_j)/delta - u_{j-1},
  * with c, delta the centre and half-width of [blo, bhi], bounds of the
  * spectrum of B^-1 A (the scaled Chebyshev basis named in Section IV). */
+int orc_newton_shifts(int s, double lo, double hi, double* theta, double* sigma) {
+    if (s < 1 || !(hi > lo)) return ORC_ERR_INVALID;
+    const int m = s - 1;
+    const double c = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+    const double pi = 3.14159265358979323846;
+    double* t = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    int* used = (int*)calloc((size_t)(m > 0 ? m : 1), sizeof(int));
+    for (int k = 0; k < m; k++) t[k] = c + delta * cos((2.0 * k + 1.0) * pi / (2.0 * m));
+    for (int q = 0; q < m; q++) {
+        int best = -1;
+        double bv = -1.0;
+        for (int k = 0; k < m; k++) {
+            if (used[k]) continue;
+            double v;
+            if (q == 0) {
+                v = fabs(t[k]);
+            } else {
+                v = 1.0;
+                for (int i = 0; i < q; i++) v *= fabs(t[k] - theta[i]);
+            }
+            if (v > bv) {
+                bv = v;
+                best = k;
+            }
+        }
+        used[best] = 1;
+        theta[q] = t[best];
+    }
+    *sigma = 0.25 * (hi - lo);
+    free(t);
+    free(used);
+    return ORC_OK;
+}
+
 static int basis_block(const orc_csr* A, const orc_prec* B, const double* r, int s, int basis,
                        double blo, double bhi, double* U, double* AU, double* w) {
     int64_t n = A->n;
     double c = 0.5 * (bhi + blo), delta = 0.5 * (bhi - blo);
+    double theta[32], sigma = 1.0;
+    if (basis == ORC_BASIS_NEWTON && orc_newton_shifts(s, blo, bhi, theta, &sigma) != ORC_OK) return ORC_ERR_INVALID;
     if (orc_prec_apply(A, B, r, COL(U, n, 0)) != ORC_OK) return ORC_ERR_INVALID;
     for (int j = 0; j < s; j++) {
         orc_spmv(A, COL(U, n, j), COL(AU, n, j));
@@ -480,6 +516,8 @@ static int basis_block(const orc_csr* A, const orc_prec* B, const double* r, int
         const double* uj = COL(U, n, j);
         if (basis == ORC_BASIS_MONOMIAL) {
             memcpy(un, w, (size_t)n * sizeof(double));
+        } else if (basis == ORC_BASIS_NEWTON) {  /* u_{j+1} = (B^-1 A u_j - theta_j u_j) / sigma */
+            for (int64_t i = 0; i < n; i++) un[i] = (w[i] - theta[j] * uj[i]) / sigma;
         } else if (j == 0) {
             for (int64_t i = 0; i < n; i++) un[i] = (w[i] - c * uj[i]) / delta;
         } else {

@@ -24,7 +24,7 @@ extern "C" {
 #endif
 
 enum { ORC_PREC_NONE = 0, ORC_PREC_JACOBI = 1, ORC_PREC_CHEB = 2 };
-enum { ORC_BASIS_MONOMIAL = 0, ORC_BASIS_CHEBYSHEV = 1 };
+enum { ORC_BASIS_MONOMIAL = 0, ORC_BASIS_CHEBYSHEV = 1, ORC_BASIS_NEWTON = 2 };
 enum { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_BREAKDOWN = 2, ORC_ERR_INVALID = -1 };
 
 typedef struct {
@@ -82,9 +82,22 @@ int orc_pcg(const orc_csr* A, const orc_prec* B, const double* b, double* x,
 int orc_pcgs(const orc_csr* A, const orc_prec* B, const double* b, double* x,
              int s, double tol, int maxit, orc_result* res, orc_trace* tr);
 
+/* basis: ORC_BASIS_MONOMIAL, ORC_BASIS_CHEBYSHEV (three-term recurrence over
+ * [blo, bhi]) or ORC_BASIS_NEWTON (orc_newton_shifts over [blo, bhi]). */
 int orc_pcgs_gram(const orc_csr* A, const orc_prec* B, const double* b, double* x,
                   int s, int basis, double blo, double bhi, double tol, int maxit,
                   orc_result* res, orc_trace* tr);
+
+/* Shifts of the Newton basis over the interval [lo, hi] of B^-1 A (Section IV
+ * names the Newton basis; the shifts are this project's reading): the s - 1
+ * zeros of the Chebyshev polynomial T_{s-1} mapped to [lo, hi],
+ * t_k = c + delta cos((2k + 1) pi / (2 (s - 1))), put in Leja order (first
+ * the point of largest modulus, then each next point maximising the product
+ * of its distances to the points already chosen; ties to the lower index),
+ * and the scale sigma = (hi - lo) / 4, the logarithmic capacity of the
+ * interval.  The basis is u_1 = B^-1 r, u_{j+1} = (B^-1 A u_j - theta_j u_j)
+ * / sigma.  Returns ORC_ERR_INVALID for s < 1 or an empty interval. */
+int orc_newton_shifts(int s, double lo, double hi, double* theta, double* sigma);
 
 int orc_pfcg(const orc_csr* A, const orc_prec* B, const double* b, double* x,
              double tol, int maxit, orc_result* res);

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -154,8 +155,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // TB: element type of the basis columns U (the new block's first s
 // columns, or `ublk` when given); AU (`au`, s columns), r and the old block
-// use A::S.  The
-// mixed-precision mode passes FP32 U with double-float AU, r and P_old.
+// use A::S.  The mixed-precision mode passes FP32 U with FP64 AU, r and
+// P_old (A = ArithF64: the FP32 elements are widened in shared memory).
 template <class A, int SB, class TB = typename A::S>
 __global__ void __launch_bounds__(kThreads) k_gram(int n, int ldn, int s, const typename A::S* __restrict__ blk_new,
                                                    const TB* __restrict__ ublk, const typename A::S* __restrict__ au,
@@ -228,6 +229,18 @@ __global__ void __launch_bounds__(kThreads) k_gram(int n, int ldn, int s, const 
         cp_async_commit();
         cp_async_wait_prior();  // every group but the newest: tile t is in
         __syncthreads();
+        if constexpr (A::kind == 0 && std::is_same<TB, float>::value) {
+            // FP64 sums of an FP32 basis: each thread widens the U elements it
+            // staged (the low 4 bytes of their slots) to FP64 in place
+            if (ublk) {
+                const int i = threadIdx.x % kGramTile;
+                for (int c = threadIdx.x / kGramTile; c < s; c += blockDim.x / kGramTile) {
+                    S* d = tile + buf * tstride + c * LD + i;
+                    *d = (double)reinterpret_cast<const float*>(d)[0];
+                }
+                __syncthreads();
+            }
+        }
         const S* tile_t = tile + buf * tstride;
         if (threadIdx.x < active) {
 #pragma unroll

@@ -1,17 +1,17 @@
 // Mixed-precision s-step solve (Section IV, item (ii): higher precision for
 // the moment-related computations).  The Krylov basis U that the
-// matrix-powers kernel builds each outer step is stored in FP32; A U is formed
-// from it in double-float (every product of two FP32 numbers is exact) and
-// stored in double-float, so the block the method works with satisfies
-// AU = A U to double-float accuracy whatever rounding U carries.  The Gram
-// sums, the direction blocks P, AP (the method's memory across steps), x and
-// r are double-float; the s x s solves are FP64.  Every `replace_every` outer steps the
+// matrix-powers kernel builds each outer step is stored in FP32 and
+// multiplied with the FP32 matrix values; A U is formed from it with every
+// product exact (products of two FP32 numbers) and the row sums in
+// double-float, then stored in FP64.  The Gram sums are accumulated in FP64,
+// the direction blocks P, AP (the method's memory across steps), x and r are
+// FP64, and the s x s solves are FP64.  Every `replace_every` outer steps the
 // residual is replaced by the true residual (Section IV, item (i)),
-// r = r0 - A (x - x0) with r0 = b - A x0, computed in double-float with the
-// matrix values to full precision, and convergence is tested on it.
-// Blocks are formed by the direct-Gram path (any basis), because the moment
-// recurrence of Algorithm 6 assumes the exact recurrences that FP32 storage
-// and residual replacement perturb.
+// r = r0 - A (x - x0) with r0 = b - A x0, computed in FP64 with the FP64
+// matrix, and convergence is tested on it.  Blocks are formed by the
+// direct-Gram path (any basis), because the moment recurrence of Algorithm 6
+// assumes the exact recurrences that FP32 storage and residual replacement
+// perturb.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -27,25 +27,31 @@ namespace sscg {
 
 namespace {
 
+// u = B^-1 r rounded to FP32 (B^-1 the array dinv, the constant dinv_c, or none).
+__device__ __forceinline__ float mx_prec(const double* dinv, double dinv_c, int i, double r) {
+    return (float)(dinv ? dinv[i] * r : (dinv_c != 0.0 ? dinv_c * r : r));
+}
+
 // r0 = r, u_1 = B^-1 r in FP32.
-__global__ void k_mx_prep(int n, const float2* __restrict__ r, float2* __restrict__ r0,
-                          const float* __restrict__ dinv_f, float* __restrict__ u0, const Ctrl* ctrl) {
+__global__ void k_mx_prep(int n, const double* __restrict__ r, double* __restrict__ r0,
+                          const double* __restrict__ dinv, double dinv_c, float* __restrict__ u0, const Ctrl* ctrl) {
     if (__ldcg(&ctrl->done)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        float2 v = r[i];
+        const double v = r[i];
         r0[i] = v;
-        u0[i] = dinv_f ? dinv_f[i] * v.x : v.x;
+        u0[i] = mx_prec(dinv, dinv_c, i, v);
     }
 }
 
-// AU_j = A u_j in double-float from the FP32 u_j; u_{j+1} from B^-1 AU_j by
-// the basis recurrence, rounded to FP32.  With DM != 0 the matrix's diagonal
-// form (mode DM of spmv_dia_df; B^-1 the constant dinv_c or the identity, the
-// FP32 basis columns carry margins).
+// AU_j = A u_j from the FP32 u_j (exact products, double-float row sums),
+// stored in FP64; u_{j+1} from B^-1 AU_j by the basis recurrence, rounded to
+// FP32.  With DM != 0 the matrix's diagonal form (mode DM of spmv_dia_df;
+// B^-1 the constant dinv_c or the identity, the FP32 basis columns carry
+// margins).
 template <int VM, int DM = 0>
 __global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1)
     k_mx_level(MatView M, const float2* __restrict__ dinv_df, double dinv_c, const float* __restrict__ u_in,
-               const float* __restrict__ u_prev, float2* __restrict__ au_out, float* __restrict__ u_next, int j,
+               const float* __restrict__ u_prev, double* __restrict__ au_out, float* __restrict__ u_next, int j,
                Basis B, Ctrl* ctrl) {
     if (__ldcg(&ctrl->done)) return;
     if constexpr (DM != 0) {
@@ -53,8 +59,8 @@ __global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1)
         const df64 cb = df_from_double(B.c);
         const df64 sc = df_from_double(B.cheb ? (j == 0 ? 1.0 : 2.0) / B.delta : 1.0);
         spmv_dia_df<DM>(M, u_in, [&](int i, df64 y0, df64 x0, df64 y1, df64 x1, bool has1) {
-            if (has1) st_pair(au_out + i, y0, y1);
-            else au_out[i] = make_float2(y0.hi, y0.lo);
+            if (has1) *reinterpret_cast<double2*>(au_out + i) = make_double2(df_to_double(y0), df_to_double(y1));
+            else au_out[i] = df_to_double(y0);
             if (!u_next) return;
             df64 w0 = df_mul(dcv, y0), w1 = df_mul(dcv, y1);
             if (B.cheb) {
@@ -77,7 +83,7 @@ __global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1)
     spmv_pipe<ArithDF64, VM, kStages>(
         M, smem, [&](int c) { return df_make(__ldg(u_in + c), 0.f); },
         [&](int row, df64 y) {
-            au_out[row] = make_float2(y.hi, y.lo);
+            au_out[row] = df_to_double(y);
             if (u_next) {
                 df64 w = dinv_df ? df_mul(ArithDF64::ld(dinv_df + row), y) : y;
                 df64 un = w;
@@ -112,75 +118,72 @@ __device__ __forceinline__ void close_step(Ctrl* ctrl, double* hist, double rr) 
     }
 }
 
-// P = U + P_old beta, AP = AU + AP_old beta, x += P alpha in double-float
-// (U, AU FP32); with write_r also r -= AP alpha, u_1 = B^-1 r in FP32 and the
-// stop test on the recursive residual (steps without residual replacement).
+// P = U + P_old beta, AP = AU + AP_old beta, x += P alpha in FP64 (U FP32);
+// with write_r also r -= AP alpha, u_1 = B^-1 r in FP32 and the stop test on
+// the recursive residual (steps without residual replacement).
 template <int SB>
 __global__ void __launch_bounds__(kThreads) k_mx_update(int n, int ldn, int s, float* __restrict__ ublk,
-                                                        const float2* __restrict__ aublk,
-                                                        float2* __restrict__ p_new, const float2* __restrict__ p_old,
-                                                        float2* __restrict__ xw, float2* __restrict__ r,
-                                                        const float* __restrict__ dinv_f, double* __restrict__ part,
-                                                        int first, int write_r, Ctrl* ctrl,
+                                                        const double* __restrict__ aublk,
+                                                        double* __restrict__ p_new, const double* __restrict__ p_old,
+                                                        double* __restrict__ xw, double* __restrict__ r,
+                                                        const double* __restrict__ dinv, double dinv_c,
+                                                        double* __restrict__ part, int first, int write_r, Ctrl* ctrl,
                                                         double* __restrict__ hist) {
     if (__ldcg(&ctrl->done)) return;
-    __shared__ df64 sb[SB * SB];
-    __shared__ df64 sa[SB];
+    __shared__ double sb[SB * SB];
+    __shared__ double sa[SB], sna[SB];
     __shared__ double red[kThreads / 32];
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) sb[(e % s) + (e / s) * SB] = df_from_double(ctrl->beta[e]);
-    for (int e = threadIdx.x; e < s; e += blockDim.x) sa[e] = df_from_double(ctrl->alpha[e]);
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) sb[(e % s) + (e / s) * SB] = ctrl->beta[e];
+    for (int e = threadIdx.x; e < s; e += blockDim.x) {
+        sa[e] = ctrl->alpha[e];
+        sna[e] = -ctrl->alpha[e];
+    }
     __syncthreads();
     const size_t ld = (size_t)ldn;
-    df64 rr = df_make(0.f, 0.f);
+    double rr = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         // every load of the row is issued (L2 path) before its arithmetic
-        df64 po[SB], apo[SB], uu[SB], au[SB];
+        double po[SB], apo[SB], uu[SB], au[SB];
 #pragma unroll
         for (int l = 0; l < SB; l++)
             if (l < s) {
-                const float2 a = __ldcg(aublk + l * ld + i);
-                uu[l] = df_make(__ldcg(ublk + l * ld + i), 0.f);
-                au[l] = df_make(a.x, a.y);
+                uu[l] = (double)__ldcg(ublk + l * ld + i);
+                au[l] = __ldcg(aublk + l * ld + i);
                 if (!first) {
-                    const float2 b = __ldcg(p_old + l * ld + i), c = __ldcg(p_old + (s + l) * ld + i);
-                    po[l] = df_make(b.x, b.y);
-                    apo[l] = df_make(c.x, c.y);
+                    po[l] = __ldcg(p_old + l * ld + i);
+                    apo[l] = __ldcg(p_old + (s + l) * ld + i);
                 }
             }
-        df64 xa = df_make(0.f, 0.f), ra = df_make(0.f, 0.f);
+        double xn = xw[i], rn = write_r ? r[i] : 0.0;
 #pragma unroll
         for (int jj = 0; jj < SB; jj++) {
             if (jj < s) {
-                df64 p = uu[jj], ap = au[jj];
+                double p = uu[jj], ap = au[jj];
                 if (!first) {
 #pragma unroll
                     for (int l = 0; l < SB; l++)
                         if (l < s) {
-                            p = df_fma(po[l], sb[l + jj * SB], p);
-                            ap = df_fma(apo[l], sb[l + jj * SB], ap);
+                            p = fma(po[l], sb[l + jj * SB], p);
+                            ap = fma(apo[l], sb[l + jj * SB], ap);
                         }
                 }
-                __stcs(p_new + jj * ld + i, make_float2(p.hi, p.lo));  // read again only next step
-                __stcs(p_new + (s + jj) * ld + i, make_float2(ap.hi, ap.lo));
-                xa = df_fma(p, sa[jj], xa);
-                ra = df_fma(ap, sa[jj], ra);
+                __stcs(p_new + jj * ld + i, p);  // read again only next step
+                __stcs(p_new + (s + jj) * ld + i, ap);
+                xn = fma(p, sa[jj], xn);
+                if (write_r) rn = fma(ap, sna[jj], rn);
             }
         }
-        float2 xv = xw[i];
-        df64 xn = df_add(df_make(xv.x, xv.y), xa);
-        xw[i] = make_float2(xn.hi, xn.lo);
+        xw[i] = xn;
         if (write_r) {
-            float2 rv = r[i];
-            df64 rn = df_add(df_make(rv.x, rv.y), df_neg(ra));
-            r[i] = make_float2(rn.hi, rn.lo);
-            ublk[i] = dinv_f ? dinv_f[i] * rn.hi : rn.hi;
-            rr = df_fma(rn, rn, rr);
+            r[i] = rn;
+            ublk[i] = mx_prec(dinv, dinv_c, i, rn);
+            rr = fma(rn, rn, rr);
         }
     }
     if (!write_r) return;
-    df64 v[1] = {rr};
+    double v[1] = {rr};
     double out[1];
-    block_sum<ArithDF64, 1>(v, red, out);
+    block_sum<ArithF64, 1>(v, red, out);
     if (threadIdx.x == 0) part[blockIdx.x] = out[0];
     if (!last_cta(&ctrl->ticket[2])) return;
     __shared__ double sh[32];
@@ -188,57 +191,41 @@ __global__ void __launch_bounds__(kThreads) k_mx_update(int n, int ldn, int s, f
     if (threadIdx.x == 0) close_step(ctrl, hist, t);
 }
 
-// Residual replacement: r = r0 - A (x - x0) in double-float, u_1 = B^-1 r
-// in FP32; the stop test on this true residual.  DM as in k_mx_level (x - x0
-// carries margins; B^-1 is then the constant dinv_c or the identity).
-template <int VM, int DM = 0>
-__global__ void __launch_bounds__(kThreads) k_mx_replace(MatView M, const float2* __restrict__ xw,
-                                                         const float2* __restrict__ r0, float2* __restrict__ r,
-                                                         const float* __restrict__ dinv_f, double dinv_c,
+// Residual replacement: r = r0 - A (x - x0) in FP64 with the FP64 matrix,
+// u_1 = B^-1 r in FP32; the stop test on this true residual.  DM as in
+// k_mx_level (x - x0 carries margins; B^-1 is then the constant dinv_c or the
+// identity): 7 / 27 the FP64 Laplacian-class neighbour sum, 2 the clamped
+// diagonal form, 0 CSR tiles.
+template <int DM = 0>
+__global__ void __launch_bounds__(kThreads) k_mx_replace(MatView M, const double* __restrict__ xw,
+                                                         const double* __restrict__ r0, double* __restrict__ r,
+                                                         const double* __restrict__ dinv, double dinv_c,
                                                          float* __restrict__ u0, double* __restrict__ part,
                                                          Ctrl* ctrl, double* __restrict__ hist) {
     if (__ldcg(&ctrl->done)) return;
     extern __shared__ __align__(16) char smem_raw[];
     char* smem = align128(smem_raw);
     __shared__ double red[kThreads / 32];
-    df64 rr = df_make(0.f, 0.f);
+    double rr = 0.0;
+    auto epi = [&](int row, double y) {
+        const double rn = r0[row] - y;
+        r[row] = rn;
+        u0[row] = mx_prec(dinv, dinv_c, row, rn);
+        rr = fma(rn, rn, rr);
+    };
     bool ok = true;
-    if constexpr (DM != 0) {
-        const float dcf = dinv_c != 0.0 ? (float)dinv_c : 1.f;  // 1/d rounded to FP32, as dinv_f holds it
-        DotAcc acc{0.f, 0.f};
-        spmv_dia_df<DM>(M, xw, [&](int i, df64 y0, df64, df64 y1, df64, bool has1) {
-            df64 a0, a1;
-            DiaVec<float2>::ld_pair(r0 + i, a0, a1);
-            const df64 rn0 = df_add(a0, df_neg(y0));
-            const df64 rn1 = has1 ? df_add(a1, df_neg(y1)) : df_make(0.f, 0.f);
-            if (has1) {
-                st_pair(r + i, rn0, rn1);
-                *reinterpret_cast<float2*>(u0 + i) = make_float2(dcf * rn0.hi, dcf * rn1.hi);
-            } else {
-                r[i] = make_float2(rn0.hi, rn0.lo);
-                u0[i] = dcf * rn0.hi;
-            }
-            dot_add_sq(acc, rn0);
-            dot_add_sq(acc, rn1);
-            dot_renorm(acc);
-        });
-        rr = dot_value(acc);
+    if constexpr (DM >= 7) {
+        const double cc = M.dc[DM / 2], co = (double)M.dco;
+        spmv_dia_lap_f64<DM>(M, xw, [&](int i, double S, double xc) { epi(i, fma(co, S, cc * xc)); });
+    } else if constexpr (DM != 0) {
+        spmv_dia<ArithF64>(M, [&](int c) { return __ldg(xw + c); }, epi);
     } else {
-        ok = spmv_pipe<ArithDF64, VM, kStages>(
-            M, smem, [&](int c) { return ArithDF64::ldg(xw + c); },
-            [&](int row, df64 y) {
-                float2 a = r0[row];
-                df64 rn = df_add(df_make(a.x, a.y), df_neg(y));
-                r[row] = make_float2(rn.hi, rn.lo);
-                u0[row] = dinv_f ? dinv_f[row] * rn.hi : rn.hi;
-                rr = df_fma(rn, rn, rr);
-            },
-            ctrl);
+        ok = spmv_pipe<ArithF64, VAL_F64, kStages>(M, smem, [&](int c) { return __ldg(xw + c); }, epi, ctrl);
     }
     if (!ok) return;
-    df64 v[1] = {rr};
+    double v[1] = {rr};
     double out[1];
-    block_sum<ArithDF64, 1>(v, red, out);
+    block_sum<ArithF64, 1>(v, red, out);
     if (threadIdx.x == 0) part[blockIdx.x] = out[0];
     if (!last_cta(&ctrl->ticket[3])) return;
     __shared__ double sh[32];
@@ -252,11 +239,11 @@ struct MLayout {
     double* hist;
     double* part;
     float* ublk;       // U, FP32, rebuilt every outer step
-    float2* aublk;     // A U, double-float
-    float2* pblk[2];   // P | AP, double-float, alternating new / old
-    float2* r;
-    float2* r0;
-    float2* xw;
+    double* aublk;     // A U, FP64
+    double* pblk[2];   // P | AP, FP64, alternating new / old
+    double* r;
+    double* r0;
+    double* xw;        // x - x0, FP64
     double* bdev;
     double* xdev;
     size_t bytes;
@@ -275,14 +262,14 @@ MLayout mplan(const sscg_mat* mat, const sscg_opts* o, void* base, size_t cap) {
     if (g) c.take<float>(g);
     L.ublk = c.take<float>((size_t)L.ldn * o->s);
     if (g) c.take<float>(g);
-    L.aublk = c.take<float2>((size_t)L.ldn * o->s);
-    L.pblk[0] = c.take<float2>((size_t)L.ldn * 2 * o->s);
-    L.pblk[1] = c.take<float2>((size_t)L.ldn * 2 * o->s);
-    L.r = c.take<float2>((size_t)L.ldn);
-    L.r0 = c.take<float2>((size_t)L.ldn);
-    if (g) c.take<float2>(g);
-    L.xw = c.take<float2>((size_t)L.ldn);
-    if (g) c.take<float2>(g);
+    L.aublk = c.take<double>((size_t)L.ldn * o->s);
+    L.pblk[0] = c.take<double>((size_t)L.ldn * 2 * o->s);
+    L.pblk[1] = c.take<double>((size_t)L.ldn * 2 * o->s);
+    L.r = c.take<double>((size_t)L.ldn);
+    L.r0 = c.take<double>((size_t)L.ldn);
+    if (g) c.take<double>(g);
+    L.xw = c.take<double>((size_t)L.ldn);
+    if (g) c.take<double>(g);
     if (o->flags & SSCG_HOST_VECTORS) {
         L.bdev = c.take<double>((size_t)L.ldn);
         L.xdev = c.take<double>((size_t)L.ldn);
@@ -299,38 +286,38 @@ int run_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     const int cap = stage_cap(mat);
     const MatView M = mat_view(mat);
     const bool jac = mat->prec == SSCG_PREC_JACOBI;
-    const float* dinv_f = jac ? mat->dinv_f : nullptr;
     const float2* dinv_df = jac ? mat->dinv_df : nullptr;
-    const double dinv_c = (DM != 0 && jac) ? mat->dia_dinv : 0.0;  // the diagonal form's constant D^-1
-    const size_t smem_init = stage_bytes<ArithDF64, VM>(cap);
-    const size_t smem_lvl = DM != 0 ? 0 : pipe_bytes<VAL_F32, kStages>(cap) + 128;  // the diagonal form stages nothing
-    const size_t smem_df = DM != 0 ? 0 : pipe_bytes<VM, kStages>(cap) + 128;
+    // B^-1 of the FP64 steps: the diagonal form's constant, or the array
+    const double dinv_c = (DM != 0 && jac) ? mat->dia_dinv : 0.0;
+    const double* dinv_d = (DM == 0 && jac) ? mat->dinv : nullptr;
     const size_t smem64 = stage_bytes<ArithF64, VAL_F64>(cap);
+    const size_t smem_lvl = DM != 0 ? 0 : pipe_bytes<VAL_F32, kStages>(cap) + 128;  // the diagonal form stages nothing
+    const size_t smem_rep = DM != 0 ? 0 : pipe_bytes<VAL_F64, kStages>(cap) + 128;
     const GramShape gs_full = gram_shape(s, 1, 1);
-    const size_t smem_gram = std::max({2 * (size_t)gs_full.ncols * (kGramTile + 1) * sizeof(float2), sizeof(SmallScratch),
+    const size_t smem_gram = std::max({2 * (size_t)gs_full.ncols * (kGramTile + 1) * sizeof(double), sizeof(SmallScratch),
                                        (size_t)kThreads * sizeof(double)});
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<ArithDF64, VM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem_init));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_init<ArithF64, VAL_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem64));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_mx_level<VAL_F32, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem_lvl));
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_gram<ArithDF64, SB, float>,
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_gram<ArithF64, SB, float>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gram));
-    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_mx_replace<VM, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df));
+    SSCG_CUDA(ctx, cudaFuncSetAttribute(k_mx_replace<DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rep));
     SSCG_CUDA(ctx, cudaFuncSetAttribute(k_true_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
-    const int Gi = occupancy_grid(ctx, k_init<ArithDF64, VM>, smem_init, n);
+    const int Gi = occupancy_grid(ctx, k_init<ArithF64, VAL_F64>, smem64, n);
     const int Gl = occupancy_grid(ctx, k_mx_level<VAL_F32, DM>, smem_lvl, n);
-    const int Gg = occupancy_grid(ctx, k_gram<ArithDF64, SB, float>, smem_gram, n);
+    const int Gg = occupancy_grid(ctx, k_gram<ArithF64, SB, float>, smem_gram, n);
     const int Gu = occupancy_grid(ctx, k_mx_update<SB>, 0, n);
-    const int Gr = occupancy_grid(ctx, k_mx_replace<VM, DM>, smem_df, n);
+    const int Gr = occupancy_grid(ctx, k_mx_replace<DM>, smem_rep, n);
     const int Ge = occupancy_grid(ctx, k_mx_prep, 0, n);
     const int Gt = occupancy_grid(ctx, k_true_res, smem64, n);
     const size_t ld = (size_t)L.ldn;
     const int every = o->replace_every > 0 ? o->replace_every : 1;
 
     P.begin();
-    k_init<ArithDF64, VM><<<Gi, kThreads, smem_init, st>>>(M, dinv_df, b, x, L.xw, L.r, nullptr, L.part, L.ctrl,
-                                                           L.hist);
-    k_mx_prep<<<Ge, kThreads, 0, st>>>(n, L.r, L.r0, dinv_f, L.ublk, L.ctrl);
+    k_init<ArithF64, VAL_F64><<<Gi, kThreads, smem64, st>>>(M, nullptr, b, x, L.xw, L.r, nullptr, L.part, L.ctrl,
+                                                            L.hist);
+    k_mx_prep<<<Ge, kThreads, 0, st>>>(n, L.r, L.r0, dinv_d, dinv_c, L.ublk, L.ctrl);
     P.end(FAM_INIT, 0);
     P.launches++;
     SSCG_CUDA(ctx, cudaGetLastError());
@@ -344,9 +331,9 @@ int run_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
         for (int q = 0; q < c; q++) {
             const int k = launched + q;
             float* ub = L.ublk;
-            float2* aub = L.aublk;
-            float2* pn = L.pblk[k & 1];
-            float2* po = L.pblk[(k + 1) & 1];
+            double* aub = L.aublk;
+            double* pn = L.pblk[k & 1];
+            double* po = L.pblk[(k + 1) & 1];
             P.begin();
             for (int j = 0; j < s; j++) {
                 float* unext = j + 1 < s ? ub + (j + 1) * ld : nullptr;
@@ -357,16 +344,16 @@ int run_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
             }
             P.end(FAM_MPK, k);
             P.begin();
-            k_gram<ArithDF64, SB, float><<<Gg, kThreads, smem_gram, st>>>(n, (int)L.ldn, s, nullptr, ub, aub, L.r,
-                                                                          po, k > 0 ? 1 : 0, 1, L.part, k, L.ctrl);
+            k_gram<ArithF64, SB, float><<<Gg, kThreads, smem_gram, st>>>(n, (int)L.ldn, s, nullptr, ub, aub, L.r,
+                                                                         po, k > 0 ? 1 : 0, 1, L.part, k, L.ctrl);
             P.end(FAM_DIR, k);
             const bool replace = (k + 1) % every == 0;
             P.begin();
-            k_mx_update<SB><<<Gu, kThreads, 0, st>>>(n, (int)L.ldn, s, ub, aub, pn, po, L.xw, L.r, dinv_f, L.part,
-                                                     k == 0, replace ? 0 : 1, L.ctrl, L.hist);
+            k_mx_update<SB><<<Gu, kThreads, 0, st>>>(n, (int)L.ldn, s, ub, aub, pn, po, L.xw, L.r, dinv_d, dinv_c,
+                                                     L.part, k == 0, replace ? 0 : 1, L.ctrl, L.hist);
             if (replace) {
-                k_mx_replace<VM, DM><<<Gr, kThreads, smem_df, st>>>(M, L.xw, L.r0, L.r, dinv_f, dinv_c, ub,
-                                                                    L.part, L.ctrl, L.hist);
+                k_mx_replace<DM><<<Gr, kThreads, smem_rep, st>>>(M, L.xw, L.r0, L.r, dinv_d, dinv_c, ub, L.part,
+                                                                 L.ctrl, L.hist);
                 P.launches++;
             }
             P.end(FAM_UPDATE, k);
@@ -390,7 +377,7 @@ int run_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     cudaEventDestroy(ev[1]);
     if (err) return set_err(ctx, SSCG_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     P.begin();
-    k_export_x<ArithDF64><<<Ge, kThreads, 0, st>>>(n, L.xw, x, L.ctrl);
+    k_export_x<ArithF64><<<Ge, kThreads, 0, st>>>(n, L.xw, x, L.ctrl);
     k_true_res<<<Gt, kThreads, smem64, st>>>(M, b, x, L.part, L.ctrl);
     P.end(FAM_FINAL, 0);
     P.launches++;

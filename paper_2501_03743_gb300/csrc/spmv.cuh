@@ -461,14 +461,20 @@ __device__ __forceinline__ void spmv_dia_lap_f64(const MatView& M, const double*
         double v[K];
 #pragma unroll
         for (int t = 0; t < K; t++) v[t] = __ldg(x + (i + M.doff[t]));
-        double S = 0.0;
+        // off-centre terms, then a pairwise tree: K - 2 additions as a chain
+        // of depth ceil(log2(K - 1)) instead of K - 2
+        double w[K - 1];
 #pragma unroll
         for (int t = 0; t < K; t++) {
             if (t == C) continue;
-            const double w = ((m >> t) & 1u) ? v[t] : 0.0;
-            S = (t == 0) ? w : S + w;  // the first term starts the sum
+            w[t < C ? t : t - 1] = ((m >> t) & 1u) ? v[t] : 0.0;
         }
-        epi(i, S, v[C]);
+#pragma unroll
+        for (int h = 1; h < K - 1; h *= 2) {
+#pragma unroll
+            for (int q = 0; q + h < K - 1; q += 2 * h) w[q] += w[q + h];
+        }
+        epi(i, w[0], v[C]);
     }
 }
 

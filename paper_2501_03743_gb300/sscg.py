@@ -36,7 +36,7 @@ EXPORTS = (
     "sscg_mlp_workspace_bytes", "sscg_mlp_forward", "sscg_mlp_loss_grad", "sscg_mlp_adam_step", "sscg_mlp_train",
     "sscg_bounds_mlp", "sscg_set_bounds_model", "sscg_batch_workspace_bytes", "sscg_batch_create",
     "sscg_batch_destroy", "sscg_batch_solve", "sscg_batch_props", "sscg_batch_launches",
-    "sscg_probe_rate", "sscg_batch_inject_barrier_fault",
+    "sscg_probe_rate", "sscg_batch_inject_barrier_fault", "sscg_pfcg_workspace_bytes", "sscg_pfcg_solve",
 )
 # Probe kinds of include/sscg_probe.h.
 PROBE = {"dfma": 0, "dadd": 1, "dmul": 2, "dmma": 3, "dfma_dmma": 4, "ffma": 5, "ialu": 6, "imad": 7}
@@ -107,6 +107,8 @@ def load(path: str | None = None):
     L.sscg_solve.argtypes = [vp, vp, vp, vp, P(Opts), P(Info), vp, sz]
     L.sscg_pcg_workspace_bytes.argtypes = [vp, P(Opts), P(sz)]
     L.sscg_pcg_solve.argtypes = [vp, vp, vp, vp, P(Opts), P(Info), vp, sz]
+    L.sscg_pfcg_workspace_bytes.argtypes = [vp, P(Opts), P(sz)]
+    L.sscg_pfcg_solve.argtypes = [vp, vp, vp, vp, P(Opts), P(Info), vp, sz]
     L.sscg_spmv.argtypes = [vp, vp, vp, vp]
     L.sscg_bounds_workspace_bytes.argtypes = [vp, i32, P(sz)]
     L.sscg_estimate_bounds.argtypes = [vp, vp, i32, vp, vp, sz, P(dbl), P(dbl)]
@@ -317,7 +319,8 @@ def make_opts(s=4, basis="monomial", tol=1e-8, maxit=1000, arith="f64", basis_bo
 
 
 class Solver:
-    """Owns the workspace for repeated solves with one matrix and option set."""
+    """Owns the workspace for repeated solves with one matrix and option set.
+    method: "sstep" (Algorithm 3), "pcg" (Algorithm 1) or "pfcg" (Algorithm 2)."""
 
     def __init__(self, A: Matrix, method="sstep", **kw):
         torch = _torch()
@@ -325,7 +328,9 @@ class Solver:
         self.method = method
         self.opts = make_opts(**kw)
         nbytes = C.c_size_t()
-        fn = A.ctx.lib.sscg_solve_workspace_bytes if method == "sstep" else A.ctx.lib.sscg_pcg_workspace_bytes
+        lib = A.ctx.lib
+        fn = {"sstep": lib.sscg_solve_workspace_bytes, "pcg": lib.sscg_pcg_workspace_bytes,
+              "pfcg": lib.sscg_pfcg_workspace_bytes}[method]
         A.ctx.check(fn(A.h, C.byref(self.opts), C.byref(nbytes)))
         self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=A.storage.device)
         self.hist = np.zeros(self.opts.maxit + 2)
@@ -338,7 +343,7 @@ class Solver:
         info = Info()
         info.hist = self.hist.ctypes.data_as(C.c_void_p).value
         info.hist_cap = len(self.hist)
-        fn = ctx.lib.sscg_solve if self.method == "sstep" else ctx.lib.sscg_pcg_solve
+        fn = {"sstep": ctx.lib.sscg_solve, "pcg": ctx.lib.sscg_pcg_solve, "pfcg": ctx.lib.sscg_pfcg_solve}[self.method]
         bp = b.ctypes.data if isinstance(b, np.ndarray) else b.data_ptr()
         xp = x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
         rc = fn(ctx.h, self.A.h, C.c_void_p(bp), C.c_void_p(xp), C.byref(self.opts), C.byref(info),

@@ -38,6 +38,8 @@ def test_traffic_only_for_the_captured_configuration():
     a = SimpleNamespace(s=4, arith="df64", fused_mpk=False)
     t = bench.traffic(a, "update", 4_096_000, True)
     assert t == round(732.694e6)
+    assert bench.traffic(SimpleNamespace(s=4, arith="f64", fused_mpk=False), "update", 4_096_000, True) == \
+        round(734.1e6)
     assert bench.traffic(SimpleNamespace(s=8, arith="df64", fused_mpk=False), "update", 4_096_000, True) is None
     assert bench.traffic(a, "update", 4_096_000, False) is None
     assert bench.traffic(a, "dir", 4_096_000, True) is None
