@@ -28,6 +28,8 @@ MUTANTS = {
                          "C[l + (size_t)j * s] = -orc_dot(n, COL(Po, n, l), COL(U, n, j));"),
     "gram-G-transposed-triangle": ("G[i + (size_t)j * s] = orc_dot(n, COL(U, n, i), COL(AU, n, j));",
                                    "G[i + (size_t)j * s] = orc_dot(n, COL(U, n, i), COL(AU, n, i));"),
+    "newton-shift-sign": ("un[i] = (w[i] - theta[j] * uj[i]) / sigma;", "un[i] = (w[i] + theta[j] * uj[i]) / sigma;"),
+    "newton-leja-first-point": ("v = fabs(t[k]);", "v = -fabs(t[k]);"),
     "cheb-basis-dropped-term": ("un[i] = 2.0 * (w[i] - c * uj[i]) / delta - um[i];", "un[i] = 2.0 * (w[i] - c * uj[i]) / delta;"),
     "cheb-prec-rho": ("double rho_new = 1.0 / (2.0 * theta / delta - rho);", "double rho_new = 1.0 / (2.0 * theta / delta + rho);"),
     "lanczos-diag-term": ("d[j] = 1.0 / a[j] + (j > 0 ? bb[j - 1] / a[j - 1] : 0.0);", "d[j] = 1.0 / a[j];"),

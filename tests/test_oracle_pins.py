@@ -146,7 +146,7 @@ def _random_diag_laplace(N, seed):
 
 
 @pytest.mark.parametrize("s", [2, 3, 4])
-@pytest.mark.parametrize("variant", ["literal", "gram-monomial", "gram-chebyshev"])
+@pytest.mark.parametrize("variant", ["literal", "gram-monomial", "gram-chebyshev", "gram-newton"])
 def test_block_equivalence_with_pcg(s, variant):
     """The s-step iterate x_i lies in x_0 + K_{is} and minimises the A-norm
     error there (Section II-A), so it equals PCG's x_{is}."""
@@ -367,12 +367,13 @@ def _laplace_modes(N, ks):
     return vs, lams
 
 
-@pytest.mark.parametrize("basis", ["monomial", "chebyshev"])
+@pytest.mark.parametrize("basis", ["monomial", "chebyshev", "newton"])
 def test_basis_vectors_closed_form(basis):
     """With b = A sum_k v_k over eigenvectors of D^-1 A (Jacobi, x0 = 0),
     z = D^-1 b = sum_k lam_k v_k and the basis vectors are
-    u_j = sum_k lam_k q_{j-1}(lam_k) v_k with q_m(l) = l^m (monomial) or
-    T_m((l - c)/delta) (Chebyshev, T_m(x) = cos(m arccos x))."""
+    u_j = sum_k lam_k q_{j-1}(lam_k) v_k with q_m(l) = l^m (monomial),
+    T_m((l - c)/delta) (Chebyshev, T_m(x) = cos(m arccos x)) or
+    prod_{i<m} (l - theta_i) / sigma (Newton, the oracle's shifts)."""
     N, s = 7, 4
     vs, lams = _laplace_modes(N, [(1, 1, 1), (1, 2, 1), (2, 2, 3), (3, 1, 4), (5, 4, 2), (6, 6, 6)])
     M = oracle.Matrix(*inputs.poisson7(N))
@@ -384,9 +385,55 @@ def test_basis_vectors_closed_form(basis):
     for j in range(s):
         if basis == "monomial":
             want = sum(l * l ** j * v for l, v in zip(lams, vs))
-        else:
+        elif basis == "chebyshev":
             want = sum(l * _cheb_T(j, (l - c) / delta) * v for l, v in zip(lams, vs))
+        else:
+            th, sig = oracle.newton_shifts(s, lo, hi)
+            want = sum(l * np.prod([(l - t) / sig for t in th[:j]]) * v for l, v in zip(lams, vs))
         assert rel(U[:, j], want) < 1e-12
+
+
+@pytest.mark.parametrize("s", [2, 3, 5, 8, 12])
+def test_newton_shifts_are_leja_ordered_chebyshev_points(s):
+    """The shifts are the zeros of T_{s-1} on [lo, hi] (numpy's Chebyshev
+    roots), in Leja order: the first of largest modulus, each next maximising
+    the product of its distances to the earlier ones (checked by brute force
+    over the remaining points); sigma = (hi - lo)/4 is the interval's
+    capacity: the monic polynomial with these zeros has sup norm 2 sigma^m
+    on [lo, hi]."""
+    lo, hi = 0.07, 2.3
+    th, sig = oracle.newton_shifts(s, lo, hi)
+    m = s - 1
+    assert len(th) == m
+    if m == 0:
+        return
+    c, d = (lo + hi) / 2, (hi - lo) / 2
+    roots = np.sort(np.real(c + d * np.polynomial.chebyshev.Chebyshev.basis(m).roots()))
+    assert np.allclose(np.sort(th), roots, rtol=0, atol=1e-13)
+    assert abs(th[0]) == max(abs(th))
+    for q in range(1, m):
+        rest = th[q:]  # the points not chosen before step q
+        score = [np.prod(np.abs(t - th[:q])) for t in rest]
+        assert np.prod(np.abs(th[q] - th[:q])) == max(score)
+    assert sig == pytest.approx((hi - lo) / 4, rel=1e-15)
+    xs = np.linspace(lo, hi, 200001)
+    sup = np.max(np.abs(np.prod(xs[:, None] - th[None, :], axis=1)))
+    assert sup == pytest.approx(2 * sig ** m, rel=1e-6)
+
+
+def test_newton_basis_converges_where_monomial_breaks_down():
+    """Section IV: Newton (like Chebyshev) bases keep large blocks usable."""
+    A = inputs.system("varcoef7", 10, seed=2, sigma=1.0)
+    M = oracle.as_matrix(A)
+    d = oracle.diag(M)
+    ev = np.linalg.eigvalsh(np.diag(d ** -0.5) @ M.to_dense() @ np.diag(d ** -0.5))
+    mono = oracle.pcgs(M, A["b"], 12, tol=1e-10, maxit=200)
+    newt = oracle.pcgs_gram(M, A["b"], 12, basis="newton", bounds=(ev[0] * 0.95, ev[-1] * 1.05), tol=1e-10,
+                            maxit=200)
+    assert mono.status != oracle.OK
+    assert newt.status == oracle.OK
+    ref = oracle.pcg(M, A["b"], tol=1e-12)
+    assert rel(newt.x, ref.x) < 1e-8
 
 
 def test_jacobi_pcg_equals_cg_for_constant_stencil():
