@@ -48,8 +48,13 @@ typedef enum {
 } sscg_status;
 
 /* Polynomial basis of the s-step block (Section II-A uses the monomial basis;
- * Section IV names Chebyshev bases as the stable alternative). */
-typedef enum { SSCG_BASIS_MONOMIAL = 0, SSCG_BASIS_CHEBYSHEV = 1 } sscg_basis;
+ * Section IV names Newton and Chebyshev bases as the stable alternatives).
+ * Both take the interval [basis_lmin, basis_lmax] of B^-1 A (estimated when
+ * 0, 0).  CHEBYSHEV: the three-term recurrence of the Chebyshev polynomials
+ * of the interval.  NEWTON: u_{j+1} = (B^-1 A u_j - theta_j u_j) / sigma with
+ * the shifts theta_j the s - 1 Chebyshev points of the interval (zeros of
+ * T_{s-1}) in Leja order and sigma = (basis_lmax - basis_lmin) / 4. */
+typedef enum { SSCG_BASIS_MONOMIAL = 0, SSCG_BASIS_CHEBYSHEV = 1, SSCG_BASIS_NEWTON = 2 } sscg_basis;
 
 /* Preconditioner B (Section II-A leaves B general: any SPD operator). */
 typedef enum {
@@ -75,6 +80,7 @@ typedef enum { SSCG_ARITH_F64 = 0, SSCG_ARITH_DF64 = 1, SSCG_ARITH_MIXED = 2 } s
 #define SSCG_PROFILE 0x2u      /* bracket every kernel with CUDA events; fills the t_* fields of sscg_info */
 #define SSCG_DIRECT_GRAM 0x4u  /* form the Gram blocks directly even for the monomial basis */
 #define SSCG_FUSED_MPK 0x8u    /* several matrix-powers levels per launch, intermediate levels kept in L2 */
+#define SSCG_ADAPTIVE_S 0x20u  /* after a breakdown restart from the last good iterate with s halved */
 #define SSCG_HOST_ARRAYS 0x1u  /* CSR arrays are host pointers (sscg_mat_create_csr) */
 #define SSCG_MAT_CSR_ONLY 0x2u /* keep CSR kernels even for a constant-coefficient diagonal pattern */
 
@@ -94,7 +100,7 @@ typedef struct sscg_mat sscg_mat;
 typedef struct {
     int s;              /* block size, 1..16 (Alg. 3) */
     int basis;          /* sscg_basis */
-    double basis_lmin;  /* Chebyshev basis: spectral interval of B^-1 A; 0,0 = estimated by the solve:
+    double basis_lmin;  /* Chebyshev / Newton basis: spectral interval of B^-1 A; 0,0 = estimated by the solve:
                            the matrix's bounds network (sscg_set_bounds_model) under the Jacobi
                            preconditioner, else 20 Lanczos steps; widened by 0.95 / 1.05 */
     double basis_lmax;
@@ -122,6 +128,8 @@ typedef struct {
      * SpMV + p.Ap, update = x, r update + dots, dir = direction update. */
     double t_init_ms, t_mpk_ms, t_update_ms, t_dir_ms, t_final_ms;
     int64_t n_mpk, n_update, n_dir;
+    int s_final;               /* sscg_solve: the block size of the last segment (SSCG_ADAPTIVE_S halves it
+                                  after each breakdown; otherwise opts->s) */
 } sscg_info;
 
 typedef struct {
@@ -190,7 +198,10 @@ int sscg_solve_workspace_bytes(const sscg_mat* mat, const sscg_opts* opts, size_
  * the solution on exit (device pointers unless SSCG_HOST_VECTORS).
  * info may be NULL.  Returns SSCG_OK, SSCG_NOT_CONVERGED, SSCG_BREAKDOWN,
  * SSCG_TIMEOUT or a negative error (SSCG_ERR_INVALID also for DF64 with the
- * monomial basis and s > 6).  On b = 0, x = 0 and SSCG_OK. */
+ * monomial basis and s > 6).  On b = 0, x = 0 and SSCG_OK.
+ * With SSCG_ADAPTIVE_S in opts->flags, a breakdown restarts the solve from
+ * the last good iterate with s halved (the budget stays maxit * s CG steps),
+ * down to s = 1; info then sums the segments (s_final: the last one's s). */
 int sscg_solve(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x,
                const sscg_opts* opts, sscg_info* info, void* workspace, size_t workspace_bytes);
 
@@ -247,6 +258,12 @@ int sscg_spmv(sscg_ctx* ctx, const sscg_mat* mat, const double* x, double* y);
 #define SSCG_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
 int sscg_solve_static(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x,
                       const sscg_opts* opts, sscg_info* info);
+
+/* The Newton basis's shifts theta_0 .. theta_{s-2} and scale sigma over
+ * [lmin, lmax], as the solver uses them (see sscg_basis).  Host-only.
+ * Errors: SSCG_ERR_INVALID (s outside 1..16, an empty interval, null
+ * outputs). */
+int sscg_newton_shifts(int s, double lmin, double lmax, double* theta, double* sigma);
 
 /* -------------------------------------------------- spectral bounds */
 

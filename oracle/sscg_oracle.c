@@ -487,7 +487,7 @@ int orc_newton_shifts(int s, double lo, double hi, double* theta, double* sigma)
                 v = 1.0;
                 for (int i = 0; i < q; i++) v *= fabs(t[k] - theta[i]);
             }
-            if (v > bv) {
+            if (best < 0 || v > bv * (1.0 + 1e-12)) {  /* near-ties go to the lower index */
                 bv = v;
                 best = k;
             }

@@ -93,7 +93,8 @@ int orc_pcgs_gram(const orc_csr* A, const orc_prec* B, const double* b, double* 
  * zeros of the Chebyshev polynomial T_{s-1} mapped to [lo, hi],
  * t_k = c + delta cos((2k + 1) pi / (2 (s - 1))), put in Leja order (first
  * the point of largest modulus, then each next point maximising the product
- * of its distances to the points already chosen; ties to the lower index),
+ * of its distances to the points already chosen; scores within 1e-12
+ * relative of each other count as ties and go to the lower index k),
  * and the scale sigma = (hi - lo) / 4, the logarithmic capacity of the
  * interval.  The basis is u_1 = B^-1 r, u_{j+1} = (B^-1 A u_j - theta_j u_j)
  * / sigma.  Returns ORC_ERR_INVALID for s < 1 or an empty interval. */

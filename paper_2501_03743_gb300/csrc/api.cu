@@ -450,11 +450,11 @@ int sscg_set_preconditioner(sscg_mat* m, int prec, int degree, double lmin, doub
 // The moment recurrence of Algorithm 6 serves the monomial basis with a
 // diagonal preconditioner; every other combination forms the Gram blocks.
 static bool use_gram(const sscg_mat* m, const sscg_opts* o) {
-    return o->basis == SSCG_BASIS_CHEBYSHEV || m->prec == SSCG_PREC_CHEB || (o->flags & SSCG_DIRECT_GRAM);
+    return o->basis != SSCG_BASIS_MONOMIAL || m->prec == SSCG_PREC_CHEB || (o->flags & SSCG_DIRECT_GRAM);
 }
 
 static bool auto_bounds(const sscg_opts* o) {
-    return o->basis == SSCG_BASIS_CHEBYSHEV && o->basis_lmin == 0.0 && o->basis_lmax == 0.0;
+    return o->basis != SSCG_BASIS_MONOMIAL && o->basis_lmin == 0.0 && o->basis_lmax == 0.0;
 }
 
 // The network predicts the interval of D^-1 A, which is the operator of the
@@ -475,13 +475,12 @@ int sscg_solve_workspace_bytes(const sscg_mat* m, const sscg_opts* o, size_t* by
     return SSCG_OK;
 }
 
-int sscg_solve(sscg_ctx* ctx, const sscg_mat* m, const double* b, double* x, const sscg_opts* o, sscg_info* info,
-               void* ws, size_t ws_bytes) {
-    if (!ctx) return SSCG_ERR_INVALID;
+static int solve_once(sscg_ctx* ctx, const sscg_mat* m, const double* b, double* x, const sscg_opts* o,
+                      sscg_info* info, void* ws, size_t ws_bytes) {
     if (!m || !o || !b || !x) return set_err(ctx, SSCG_ERR_INVALID, "null argument");
     if (o->s < 1 || o->s > kMaxS) return set_err(ctx, SSCG_ERR_INVALID, "s = %d outside 1..%d", o->s, kMaxS);
     if (o->maxit < 0 || !(o->tol >= 0.0)) return set_err(ctx, SSCG_ERR_INVALID, "bad maxit or tol");
-    if (o->basis != SSCG_BASIS_MONOMIAL && o->basis != SSCG_BASIS_CHEBYSHEV)
+    if (o->basis != SSCG_BASIS_MONOMIAL && o->basis != SSCG_BASIS_CHEBYSHEV && o->basis != SSCG_BASIS_NEWTON)
         return set_err(ctx, SSCG_ERR_INVALID, "unknown basis %d", o->basis);
     if (o->arith != SSCG_ARITH_F64 && o->arith != SSCG_ARITH_DF64 && o->arith != SSCG_ARITH_MIXED)
         return set_err(ctx, SSCG_ERR_INVALID, "arith %d not supported", o->arith);
@@ -506,10 +505,69 @@ int sscg_solve(sscg_ctx* ctx, const sscg_mat* m, const double* b, double* x, con
         lo *= kAutoBoundLow;
         hi *= kAutoBoundHigh;
     }
-    if (o->basis == SSCG_BASIS_CHEBYSHEV && !(hi > lo && lo >= 0.0))
-        return set_err(ctx, SSCG_ERR_INVALID, "Chebyshev basis needs 0 <= basis_lmin < basis_lmax");
+    if (o->basis != SSCG_BASIS_MONOMIAL && !(hi > lo && lo >= 0.0))
+        return set_err(ctx, SSCG_ERR_INVALID, "Chebyshev and Newton bases need 0 <= basis_lmin < basis_lmax");
     if (o->arith == SSCG_ARITH_MIXED) return solve_mixed(ctx, m, b, x, o, info, ws, ws_bytes, lo, hi);
     return solve_gram(ctx, m, b, x, o, info, ws, ws_bytes, lo, hi);
+}
+
+// Adaptive block size (Section IV lists adaptive s among the remedies for
+// the s-step basis's loss of independence): a solve that breaks down leaves
+// x at its last good iterate; it is restarted from there with s halved, on
+// the CG steps left of the budget maxit * s, until it converges, stops for
+// another reason, or breaks down at s = 1.  The history concatenates the
+// segments (each restart's first entry, its true initial residual, replaces
+// the previous segment's last one).
+int sscg_solve(sscg_ctx* ctx, const sscg_mat* m, const double* b, double* x, const sscg_opts* o, sscg_info* info,
+               void* ws, size_t ws_bytes) {
+    if (!ctx) return SSCG_ERR_INVALID;
+    if (!o || !(o->flags & SSCG_ADAPTIVE_S)) {
+        const int rc = solve_once(ctx, m, b, x, o, info, ws, ws_bytes);
+        if (info && rc >= 0) info->s_final = o->s;
+        return rc;
+    }
+    sscg_opts cur = *o;
+    cur.flags &= ~SSCG_ADAPTIVE_S;
+    int64_t budget = (int64_t)o->maxit * o->s;  // CG steps
+    sscg_info tot;
+    memset(&tot, 0, sizeof(tot));
+    int used = 0;  // history entries written
+    for (;;) {
+        cur.maxit = (int)std::min<int64_t>(INT32_MAX, (budget + cur.s - 1) / cur.s);
+        sscg_info seg;
+        memset(&seg, 0, sizeof(seg));
+        if (info && info->hist && info->hist_cap > 0) {
+            const int at = used > 0 ? used - 1 : 0;
+            seg.hist = info->hist + at;
+            seg.hist_cap = info->hist_cap - at;
+        }
+        const int rc = solve_once(ctx, m, b, x, &cur, &seg, ws, ws_bytes);
+        if (rc < 0) return rc;
+        tot.outer_iters += seg.outer_iters;
+        tot.equiv_iters += seg.equiv_iters;
+        tot.kernel_launches += seg.kernel_launches;
+        tot.t_init_ms += seg.t_init_ms, tot.t_mpk_ms += seg.t_mpk_ms, tot.t_update_ms += seg.t_update_ms;
+        tot.t_dir_ms += seg.t_dir_ms, tot.t_final_ms += seg.t_final_ms;
+        tot.n_mpk += seg.n_mpk, tot.n_update += seg.n_update, tot.n_dir += seg.n_dir;
+        if (seg.hist) used = (int)(seg.hist - info->hist) + seg.hist_len;
+        budget -= seg.equiv_iters;
+        if (rc != SSCG_BREAKDOWN || cur.s == 1 || budget <= 0) {
+            if (info) {
+                double* h = info->hist;
+                const int cap = info->hist_cap;
+                *info = tot;
+                info->hist = h;
+                info->hist_cap = cap;
+                info->hist_len = h ? used : 0;
+                info->status = rc;
+                info->rel_res_recursive = seg.rel_res_recursive;
+                info->rel_res_true = seg.rel_res_true;
+                info->s_final = cur.s;
+            }
+            return rc;
+        }
+        cur.s = std::max(1, cur.s / 2);
+    }
 }
 
 int sscg_bounds_workspace_bytes(const sscg_mat* m, int steps, size_t* bytes) {

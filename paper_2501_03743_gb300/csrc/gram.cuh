@@ -2,6 +2,7 @@
 // DF64/F64 driver (sstep_gram.cu) and the mixed-precision driver (mixed.cu).
 #pragma once
 
+#include <cmath>
 #include <cstring>
 #include <type_traits>
 
@@ -14,16 +15,62 @@ namespace sscg {
 
 namespace {
 
-// Basis recurrence coefficients: monomial u_{j+1} = w; Chebyshev
-// u_2 = (w - c u_1)/delta, u_{j+1} = 2 (w - c u_j)/delta - u_{j-1}.
+// Basis recurrence coefficients with w = B^-1 A u_j: monomial u_{j+1} = w;
+// Chebyshev u_2 = (w - c u_1)/delta, u_{j+1} = 2 (w - c u_j)/delta - u_{j-1};
+// Newton u_{j+1} = (w - theta_j u_j) / sigma.
 struct Basis {
     int cheb;
+    int newton;
     double c, delta;
+    double theta[kMaxS];  // Newton shifts theta_0 .. theta_{s-2}
+    double isig;          // 1 / sigma
 };
+
+// The basis of a solve over the interval [lo, hi] of B^-1 A.  Newton shifts
+// (Section IV names the Newton basis; the shift choice is this library's):
+// the s - 1 Chebyshev points of [lo, hi] (zeros of T_{s-1}) in Leja order,
+// each next point the one whose distances to the points already taken have
+// the largest product (the first: the largest in modulus; scores within
+// 1e-12 relative of each other go to the lower index), with the scale
+// sigma = (hi - lo)/4, the capacity of the interval, which keeps the basis
+// vectors' norms of the order of the first one's.
+inline Basis make_basis(int kind, int s, double lo, double hi) {
+    Basis b{};
+    b.cheb = kind == SSCG_BASIS_CHEBYSHEV;
+    b.newton = kind == SSCG_BASIS_NEWTON;
+    b.c = 0.5 * (hi + lo);
+    b.delta = 0.5 * (hi - lo);
+    b.isig = 1.0;
+    if (b.newton && s > 1 && b.delta > 0.0) {
+        const int m = s - 1;
+        double pts[kMaxS];
+        bool taken[kMaxS] = {};
+        for (int k = 0; k < m; k++) pts[k] = b.c + b.delta * std::cos(M_PI * (2 * k + 1) / (2.0 * m));
+        for (int q = 0; q < m; q++) {
+            int pick = -1;
+            double best = -1.0;
+            for (int k = 0; k < m; k++) {
+                if (taken[k]) continue;
+                double score = std::fabs(pts[k]);
+                if (q > 0) {
+                    score = 1.0;
+                    for (int i = 0; i < q; i++) score *= std::fabs(pts[k] - b.theta[i]);
+                }
+                if (pick < 0 || score > best * (1.0 + 1e-12)) best = score, pick = k;  // near-ties: lower k
+            }
+            taken[pick] = true;
+            b.theta[q] = pts[pick];
+        }
+        b.isig = 4.0 / (hi - lo);
+    }
+    return b;
+}
 
 template <class A>
 __device__ __forceinline__ typename A::R basis_next(const Basis& B, int j, typename A::R w,
                                                     const typename A::S* uj, const typename A::S* ujm1, int row) {
+    if (B.newton)
+        return A::mul(A::sub(w, A::mul(A::from_d(B.theta[j]), A::ld(uj + row))), A::from_d(B.isig));
     if (!B.cheb) return w;
     typename A::R t = A::sub(w, A::mul(A::from_d(B.c), A::ld(uj + row)));
     if (j == 0) return A::mul(t, A::from_d(1.0 / B.delta));
@@ -52,7 +99,11 @@ __global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1)
             else A::st(au_out + i, y0);
             if (!nxt) return;
             df64 w0 = df_mul(dcv, y0), w1 = df_mul(dcv, y1);
-            if (B.cheb) {  // Chebyshev recurrence on w = B^-1 A u_j
+            if (B.newton) {  // Newton recurrence on w = B^-1 A u_j
+                const df64 th = df_from_double(B.theta[j]), is = df_from_double(B.isig);
+                w0 = df_mul(df_add(w0, df_neg(df_mul(th, x0))), is);
+                w1 = df_mul(df_add(w1, df_neg(df_mul(th, x1))), is);
+            } else if (B.cheb) {  // Chebyshev recurrence on w = B^-1 A u_j
                 w0 = df_mul(df_add(w0, df_neg(df_mul(cb, x0))), sc);
                 w1 = df_mul(df_add(w1, df_neg(df_mul(cb, x1))), sc);
                 if (j > 0) {

@@ -63,7 +63,11 @@ __global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1)
             else au_out[i] = df_to_double(y0);
             if (!u_next) return;
             df64 w0 = df_mul(dcv, y0), w1 = df_mul(dcv, y1);
-            if (B.cheb) {
+            if (B.newton) {
+                const df64 th = df_from_double(B.theta[j]), is = df_from_double(B.isig);
+                w0 = df_mul(df_add(w0, df_neg(df_mul(th, x0))), is);
+                w1 = df_mul(df_add(w1, df_neg(df_mul(th, x1))), is);
+            } else if (B.cheb) {
                 w0 = df_mul(df_add(w0, df_neg(df_mul(cb, x0))), sc);
                 w1 = df_mul(df_add(w1, df_neg(df_mul(cb, x1))), sc);
                 if (j > 0) {
@@ -87,7 +91,10 @@ __global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1)
             if (u_next) {
                 df64 w = dinv_df ? df_mul(ArithDF64::ld(dinv_df + row), y) : y;
                 df64 un = w;
-                if (B.cheb) {
+                if (B.newton) {
+                    un = df_mul(df_add(w, df_neg(df_mul(df_from_double(B.theta[j]), df_make(u_in[row], 0.f)))),
+                                df_from_double(B.isig));
+                } else if (B.cheb) {
                     df64 t = df_add(w, df_neg(df_mul(df_from_double(B.c), df_make(u_in[row], 0.f))));
                     un = j == 0 ? df_mul(t, df_from_double(1.0 / B.delta))
                                 : df_add(df_mul(t, df_from_double(2.0 / B.delta)), df_make(-u_prev[row], 0.f));
@@ -426,10 +433,7 @@ int solve_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, 
     h.s = o->s;
     h.tol = o->tol;
     SSCG_CUDA(ctx, cudaMemcpyAsync(L.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
-    Basis basis;
-    basis.cheb = o->basis == SSCG_BASIS_CHEBYSHEV;
-    basis.c = 0.5 * (bhi + blo);
-    basis.delta = 0.5 * (bhi - blo);
+    const Basis basis = make_basis(o->basis, o->s, blo, bhi);
     const int s = o->s;
     Prof* prof = new Prof(ctx, (o->flags & SSCG_PROFILE) != 0);
     if (!prof->reserve((int)std::min<int64_t>(65536, (int64_t)o->maxit * 3 + 64))) {

@@ -232,11 +232,9 @@ int solve_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, c
     h.s = o->s;
     h.tol = o->tol;
     SSCG_CUDA(ctx, cudaMemcpyAsync(L.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
-    Basis basis;
-    basis.cheb = o->basis == SSCG_BASIS_CHEBYSHEV;
-    basis.c = 0.5 * (bhi + blo);
-    basis.delta = 0.5 * (bhi - blo);
-    if (basis.cheb && !(basis.delta > 0.0)) return set_err(ctx, SSCG_ERR_INVALID, "empty Chebyshev basis interval");
+    const Basis basis = make_basis(o->basis, o->s, blo, bhi);
+    if ((basis.cheb || basis.newton) && !(basis.delta > 0.0))
+        return set_err(ctx, SSCG_ERR_INVALID, "empty basis interval");
     const int s = o->s;
     Prof* prof = new Prof(ctx, (o->flags & SSCG_PROFILE) != 0);
     if (!prof->reserve((int)std::min<int64_t>(65536, (int64_t)o->maxit * 3 + 64))) {
@@ -295,3 +293,11 @@ int solve_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, c
 }
 
 }  // namespace sscg
+
+extern "C" int sscg_newton_shifts(int s, double lmin, double lmax, double* theta, double* sigma) {
+    if (s < 1 || s > sscg::kMaxS || !(lmax > lmin) || !theta || !sigma) return SSCG_ERR_INVALID;
+    const sscg::Basis b = sscg::make_basis(SSCG_BASIS_NEWTON, s, lmin, lmax);
+    for (int j = 0; j + 1 < s; j++) theta[j] = b.theta[j];
+    *sigma = 0.25 * (lmax - lmin);
+    return SSCG_OK;
+}

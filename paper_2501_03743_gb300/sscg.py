@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsscg.so")
 
 OK, NOT_CONVERGED, BREAKDOWN, TIMEOUT = 0, 1, 2, 3
 ERR_INVALID, ERR_NOT_SPD, ERR_CUDA, ERR_SPACE, ERR_NONFINITE = -1, -2, -3, -4, -5
-BASIS = {"monomial": 0, "chebyshev": 1}
+BASIS = {"monomial": 0, "chebyshev": 1, "newton": 2}
 PREC = {"none": 0, "jacobi": 1, "cheb": 2}
 ARITH = {"f64": 0, "df64": 1, "mixed": 2}
 HOST_VECTORS = 0x1
@@ -37,6 +37,7 @@ EXPORTS = (
     "sscg_bounds_mlp", "sscg_set_bounds_model", "sscg_batch_workspace_bytes", "sscg_batch_create",
     "sscg_batch_destroy", "sscg_batch_solve", "sscg_batch_props", "sscg_batch_launches",
     "sscg_probe_rate", "sscg_batch_inject_barrier_fault", "sscg_pfcg_workspace_bytes", "sscg_pfcg_solve",
+    "sscg_newton_shifts",
 )
 # Probe kinds of include/sscg_probe.h.
 PROBE = {"dfma": 0, "dadd": 1, "dmul": 2, "dmma": 3, "dfma_dmma": 4, "ffma": 5, "ialu": 6, "imad": 7}
@@ -65,12 +66,12 @@ class Info(C.Structure):
                 ("hist_cap", C.c_int), ("hist_len", C.c_int), ("kernel_launches", C.c_int64),
                 ("t_init_ms", C.c_double), ("t_mpk_ms", C.c_double), ("t_update_ms", C.c_double),
                 ("t_dir_ms", C.c_double), ("t_final_ms", C.c_double), ("n_mpk", C.c_int64),
-                ("n_update", C.c_int64), ("n_dir", C.c_int64)]
+                ("n_update", C.c_int64), ("n_dir", C.c_int64), ("s_final", C.c_int)]
 
 
 PROFILE = 0x2
 _PROFILE_FIELDS = ("kernel_launches", "t_init_ms", "t_mpk_ms", "t_update_ms", "t_dir_ms", "t_final_ms", "n_mpk",
-                   "n_update", "n_dir")
+                   "n_update", "n_dir", "s_final")
 
 
 class MatProps(C.Structure):
@@ -132,8 +133,21 @@ def load(path: str | None = None):
     L.sscg_batch_launches.argtypes = [vp, P(C.c_int64)]
     L.sscg_probe_rate.argtypes = [vp, i32, i64, i64, P(dbl), P(dbl)]
     L.sscg_batch_inject_barrier_fault.argtypes = [vp, i32, i32]
+    L.sscg_newton_shifts.argtypes = [i32, dbl, dbl, vp, P(dbl)]
     _lib = L
     return L
+
+
+def newton_shifts(s, lmin, lmax):
+    """(theta[0..s-2], sigma) of the solver's Newton basis over [lmin, lmax]
+    (host-only; no GPU needed)."""
+    L = load()
+    theta = (C.c_double * max(s - 1, 1))()
+    sig = C.c_double()
+    rc = L.sscg_newton_shifts(int(s), float(lmin), float(lmax), theta, C.byref(sig))
+    if rc != OK:
+        raise SscgError(rc, "sscg_newton_shifts: invalid arguments")
+    return np.array(theta[: s - 1]), sig.value
 
 
 def _torch():
@@ -308,12 +322,14 @@ class Matrix:
 
 DIRECT_GRAM = 0x4
 FUSED_MPK = 0x8
+ADAPTIVE_S = 0x20
 
 
 def make_opts(s=4, basis="monomial", tol=1e-8, maxit=1000, arith="f64", basis_bounds=(0.0, 0.0),
-              replace_every=0, host_vectors=False, profile=False, direct_gram=False, fused_mpk=False) -> Opts:
+              replace_every=0, host_vectors=False, profile=False, direct_gram=False, fused_mpk=False,
+              adaptive_s=False) -> Opts:
     flags = (HOST_VECTORS if host_vectors else 0) | (PROFILE if profile else 0) | (DIRECT_GRAM if direct_gram else 0)
-    flags |= FUSED_MPK if fused_mpk else 0
+    flags |= (FUSED_MPK if fused_mpk else 0) | (ADAPTIVE_S if adaptive_s else 0)
     return Opts(int(s), BASIS[basis], float(basis_bounds[0]), float(basis_bounds[1]), float(tol), int(maxit),
                 ARITH[arith], int(replace_every), flags)
 

@@ -76,3 +76,21 @@ def test_binding_fails_loudly_without_library(tmp_path):
             sscg.load(str(tmp_path / "missing.so"))
     finally:
         sscg._lib = saved
+
+
+def test_newton_shifts_host_logic_matches_the_oracle():
+    """The library's Newton shifts (host code, no GPU) are the oracle's: the
+    Leja-ordered Chebyshev points of the interval and sigma = (hi - lo)/4."""
+    import numpy as np
+
+    import oracle
+    from paper_2501_03743_gb300 import sscg
+
+    for s, lo, hi in ((1, 0.1, 2.0), (2, 0.1, 2.0), (5, 0.05, 1.95), (8, 0.3, 7.0), (12, 1e-3, 2.0), (16, 2.0, 9.5)):
+        th, sig = sscg.newton_shifts(s, lo, hi)
+        tho, sigo = oracle.newton_shifts(s, lo, hi)
+        assert len(th) == s - 1 and sig == sigo
+        assert np.allclose(th, tho, rtol=1e-14, atol=0)
+    for bad in ((0, 0.1, 2.0), (17, 0.1, 2.0), (4, 2.0, 2.0)):
+        with pytest.raises(sscg.SscgError):
+            sscg.newton_shifts(*bad)
