@@ -311,16 +311,17 @@ def workload_name(N, s, arith):
 
 def fp64_ops_model(s, K=7):
     """FP64 operations per row of the FP64 kernels on a Laplacian-class stencil
-    with K offsets in the diagonal form under a constant Jacobi scale (one
-    DFMA, DADD or DMUL per thread is one operation): level j: K - 2 additions
-    for the neighbour sum, one FMA for u_{j+1}, one for each moment (the
-    second moment is skipped on the last level); block update: s^2 FMAs each
-    for P and Q, s each for x and z, one for sum z^2 (first step: no P, Q
-    FMAs); PCG: SpMV K - 2 + 1, p . Ap 1; update x, r, ||r||^2; direction
+    in the diagonal form under a constant Jacobi scale (one DFMA, DADD or DMUL
+    per thread is one operation).  The neighbour sum runs on the integer units
+    (fixed point, csrc/fixsum.cuh) and costs no FP64 operation, whatever K:
+    level j: one FMA for u_{j+1} and one for each moment (the second moment is
+    skipped on the last level); block update: s^2 FMAs each for P and Q, s
+    each for x and z, one for sum z^2 (first step: no P, Q FMAs); PCG: SpMV
+    one FMA for A p and one for p . Ap; update x, r, ||r||^2; direction
     u = D^-1 r and p = u + beta p."""
-    lvl = [(K - 2) + 2 + (1 if 2 * j + 2 <= 2 * s - 1 else 0) for j in range(s)]
+    lvl = [2 + (1 if 2 * j + 2 <= 2 * s - 1 else 0) for j in range(s)]
     return dict(level=lvl, level_avg=sum(lvl) / s, update=2 * s * s + 2 * s + 1, update_first=2 * s + 1,
-                pcg_spmv=K, pcg_update=3, pcg_dir=2)
+                pcg_spmv=2, pcg_update=3, pcg_dir=2)
 
 
 def alu_peak(sm_count, mhz=2070.0):

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(MatView M, const typename
 }
 
 template <class A, int VM, int DM>
-__global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1) k_pcg_spmv(MatView M, const typename A::S* __restrict__ p,
+__global__ void __launch_bounds__(kThreads, dia_min_blocks<A, DM>()) k_pcg_spmv(MatView M, const typename A::S* __restrict__ p,
                                                        typename A::S* __restrict__ q, double* __restrict__ part,
                                                        Ctrl* ctrl) {
     using R = typename A::R;

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_pfcg_init(MatView M, const typenam
 
 // w = A u and the coupled dot products (see the file comment).
 template <class A, int VM, int DM>
-__global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1)
+__global__ void __launch_bounds__(kThreads, dia_min_blocks<A, DM>())
     k_pfcg_dots(MatView M, const typename A::S* __restrict__ u, const typename A::S* __restrict__ r,
                 const typename A::S* __restrict__ s, typename A::S* __restrict__ w, double* __restrict__ part,
                 Ctrl* ctrl, double* __restrict__ hist) {

@@ -11,6 +11,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "fixsum.cuh"
 #include "internal.h"
 
 namespace sscg {
@@ -440,15 +441,26 @@ __device__ __forceinline__ void spmv_dia_df(const MatView& M, const TX* __restri
     }
 }
 
+// Minimum resident CTAs per SM the diagonal-form kernels are built for: 6
+// (40 registers a thread), except the FP64 27-point form, whose 26 neighbour
+// terms the fixed-point sum holds at once (2 CTAs, 128 registers).
+template <class A, int DM>
+__host__ __device__ constexpr int dia_min_blocks() {
+    return (A::kind == 0 && DM == 27) ? 2 : (DM >= 2 ? 6 : 1);
+}
+
 // ---------------------------------------------------------------------------
 // Diagonal form in FP64, Laplacian class, over a margined vector.
 //
 // On a GB300 the FP64 units retire about 2 operations per clock per SM, 1/60
 // of the FP32 and 1/40 of the integer rate, so an FP64 stencil row is bound by
 // its FP64 operations, not its bytes.  This form spends the fewest: the
-// off-centre neighbours are summed (K - 2 additions; a term whose mask bit is
-// clear is replaced by zero with an integer select before it enters) and the
-// caller combines the sum S with the centre value in one FMA, e.g.
+// off-centre neighbours (a term whose mask bit is clear replaced by zero with
+// an integer select) are summed on the integer units in fixed point
+// (fixsum.cuh: one rounding to FP64, error inside that of K - 2 FP64
+// additions), or, for the rare row that path declines (NaN or infinity,
+// every term below 2^-966, overflow), by K - 2 FP64 additions as a pairwise
+// tree; the caller combines the sum S with the centre value in one FMA, e.g.
 // D^-1 A x = x + (c_off / d) S for the Jacobi-scaled level.  x must be
 // readable at every index in [-g, n + g) for g >= max |offset| (the solvers
 // carve such margins).  epi(i, S, x_i) runs once per row, rows grid-stride.
@@ -461,20 +473,28 @@ __device__ __forceinline__ void spmv_dia_lap_f64(const MatView& M, const double*
         double v[K];
 #pragma unroll
         for (int t = 0; t < K; t++) v[t] = __ldg(x + (i + M.doff[t]));
-        // off-centre terms, then a pairwise tree: K - 2 additions as a chain
-        // of depth ceil(log2(K - 1)) instead of K - 2
-        double w[K - 1];
+        uint64_t w[K - 1];
 #pragma unroll
         for (int t = 0; t < K; t++) {
             if (t == C) continue;
-            w[t < C ? t : t - 1] = ((m >> t) & 1u) ? v[t] : 0.0;
+            w[t < C ? t : t - 1] = ((m >> t) & 1u) ? (uint64_t)__double_as_longlong(v[t]) : 0ull;
         }
+        uint64_t sb;
+        double S;
+        if (fixsum<K - 1>(w, &sb)) {
+            S = __longlong_as_double((long long)sb);
+        } else {  // a pairwise tree of FP64 additions
+            double d[K - 1];
 #pragma unroll
-        for (int h = 1; h < K - 1; h *= 2) {
+            for (int q = 0; q < K - 1; q++) d[q] = __longlong_as_double((long long)w[q]);
 #pragma unroll
-            for (int q = 0; q + h < K - 1; q += 2 * h) w[q] += w[q + h];
+            for (int h = 1; h < K - 1; h *= 2) {
+#pragma unroll
+                for (int q = 0; q + h < K - 1; q += 2 * h) d[q] += d[q + h];
+            }
+            S = d[0];
         }
-        epi(i, w[0], v[C]);
+        epi(i, S, v[C]);
     }
 }
 

@@ -41,7 +41,7 @@ namespace {
 // mu_{2j+1} = u_j . y and mu_{2j+2} = y . B^-1 y.  With `last` set, the last
 // CTA reduces mu_1..mu_{2s-1} and runs Algorithm 6.
 template <class A, int VM, int DM>
-__global__ void __launch_bounds__(kThreads, DM >= 2 ? 6 : 1) k_level(MatView M, const typename A::S* __restrict__ dinv,
+__global__ void __launch_bounds__(kThreads, dia_min_blocks<A, DM>()) k_level(MatView M, const typename A::S* __restrict__ dinv,
                                                     double dinv_c, const typename A::S* __restrict__ u_in,
                                                     typename A::S* __restrict__ au_out,
                                                     typename A::S* __restrict__ u_next, double* __restrict__ part,

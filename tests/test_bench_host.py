@@ -72,12 +72,12 @@ def test_value_is_kernel_bytes_over_time_and_stays_below_the_copy_bandwidth():
 
 def test_fp64_operation_model():
     ops = bench.fp64_ops_model(4, K=7)
-    # level: 5 additions (6 neighbours), u_{j+1}, two moments (one on the last level)
-    assert ops["level"] == [8, 8, 8, 7]
+    # level: the neighbour sum on the integer units; u_{j+1} and two moments (one on the last level)
+    assert ops["level"] == [3, 3, 3, 2]
     # update: s^2 for P and Q each, s for x and z each, one for sum z^2
     assert ops["update"] == 2 * 16 + 2 * 4 + 1 and ops["update_first"] == 9
-    assert (ops["pcg_spmv"], ops["pcg_update"], ops["pcg_dir"]) == (7, 3, 2)
-    assert bench.fp64_ops_model(2, K=27)["level"] == [28, 27]
+    assert (ops["pcg_spmv"], ops["pcg_update"], ops["pcg_dir"]) == (2, 3, 2)
+    assert bench.fp64_ops_model(2, K=27)["level"] == [3, 2]
 
 
 def test_fp64_alu_peak_is_two_per_clock_per_sm():
