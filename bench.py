@@ -806,14 +806,15 @@ def run_mixed27(a, world, rank, local, pg):
             # bytes per timed record (the mixed driver times the s levels, the Gram pass and
             # the update + residual replacement of an outer step as one record each)
             # FP64 operations per timed record (the s levels, the Gram pass, the update with the
-            # replacement): levels 3 a row each (A U widened to FP64); Gram s(s+1)/2 + s + s^2 + s
-            # FMAs and s widenings; update 2 s^2 + s FMAs and s widenings, replacement 25
-            # additions, 3 FMAs and the FP32 rounding of B^-1 r
+            # replacement; residual replaced every step, so no A P): levels 3 a row each (A U
+            # widened to FP64); Gram s(s+1)/2 + s + s^2 + s FMAs and s widenings; update s^2 + s
+            # FMAs and s widenings; replacement (neighbour sum on the integer units) an FMA, r0 - y,
+            # ||r||^2 and B^-1 r rounded to FP32: 5
             fam_ops = {"mpk": 3 * sv * n, "dir": (sv * (sv + 1) // 2 + 3 * sv + sv * sv) * n,
-                       "update": (2 * sv * sv + 2 * sv + 30) * n}
+                       "update": (sv * sv + 2 * sv + 5) * n}
             names = {"mpk": "k_mx_level x s (diagonal-form SpMV of the FP32 basis, AU widened to FP64)",
-                     "dir": "k_gram (G, C, m and q of the direct-Gram blocks, FP64 sums)",
-                     "update": "k_mx_update + k_mx_replace (P, AP, x; r = r0 - A(x - x0) in FP64)"}
+                     "dir": "k_gram (G, C = P_old^T (A U), m and q of the direct-Gram blocks, FP64 sums)",
+                     "update": "k_mx_update + k_mx_replace (P, x; r = r0 - A(x - x0) in FP64)"}
             mixed_roof = family_alu_roofline(res, fam_ops, names, torch.cuda.get_device_properties(local)
                                              .multi_processor_count)
         out[name] = dict(ms=statistics.median(ms), outer=res.outer_iters, status=res.status, launches=nl,

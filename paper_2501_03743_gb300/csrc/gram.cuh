@@ -147,8 +147,10 @@ __global__ void __launch_bounds__(kThreads) k_combine(int n, const typename A::S
 // Gram entries: e < ng: G(i, j), i >= j (u_i . AU_j); then m(i) (u_i . r);
 // then C(l, j) ((A p_l^old) . u_j) when a previous block exists.
 // then, with a true (replaced) residual, q(l) = p_l^old . r.
+// with_q = 2 (cp): C(l, j) is formed as p_l^old . (A u_j), equal for a
+// symmetric A, so the previous block's A P is not needed.
 struct GramShape {
-    int s, ng, nm, nc, nq, E, ncols;
+    int s, ng, nm, nc, nq, E, ncols, cp;
 };
 
 __host__ __device__ inline GramShape gram_shape(int s, int has_old, int with_q = 0) {
@@ -158,13 +160,14 @@ __host__ __device__ inline GramShape gram_shape(int s, int has_old, int with_q =
     g.nm = s;
     g.nc = has_old ? s * s : 0;
     g.nq = (has_old && with_q) ? s : 0;
+    g.cp = (has_old && with_q == 2) ? 1 : 0;
     g.E = g.ng + g.nm + g.nc + g.nq;
-    g.ncols = 2 * s + 1 + (has_old ? s : 0) + g.nq;
+    g.ncols = g.cp ? 3 * s + 1 : 2 * s + 1 + (has_old ? s : 0) + g.nq;
     return g;
 }
 
 // Columns staged per tile: U_0..U_{s-1}, AU_0..AU_{s-1}, r,
-// AP_old_0..AP_old_{s-1}, P_old_0..P_old_{s-1}.
+// AP_old_0..AP_old_{s-1}, P_old_0..P_old_{s-1} (cp: U, AU, r, P_old).
 __device__ __forceinline__ void gram_entry(const GramShape& g, int e, int& a, int& b) {
     const int s = g.s;
     if (e < g.ng) {  // lower-triangle index -> (i, j), i >= j
@@ -180,10 +183,10 @@ __device__ __forceinline__ void gram_entry(const GramShape& g, int e, int& a, in
         int q = e - g.ng - g.nm;
         int l = q % s, j = q / s;
         a = 2 * s + 1 + l;
-        b = j;
+        b = g.cp ? s + j : j;
     } else {
         int l = e - g.ng - g.nm - g.nc;
-        a = 3 * s + 1 + l;
+        a = (g.cp ? 2 * s + 1 : 3 * s + 1) + l;
         b = 2 * s;
     }
 }
@@ -257,6 +260,7 @@ __global__ void __launch_bounds__(kThreads) k_gram(int n, int ldn, int s, const 
         if (c < s) p = ublk ? static_cast<const void*>(ublk + c * ld) : static_cast<const void*>(blk_new + c * ld);
         else if (c < 2 * s) p = au + (c - s) * ld;
         else if (c == 2 * s) p = r;
+        else if (g.cp) p = blk_old + (c - 2 * s - 1) * ld;  // P_old
         else if (c <= 3 * s) p = blk_old + (s + (c - 2 * s - 1)) * ld;
         else p = blk_old + (c - 3 * s - 1) * ld;
         s_src[c] = p;
@@ -335,10 +339,10 @@ __global__ void __launch_bounds__(kThreads) k_gram(int n, int ldn, int s, const 
         } else if (e < g.ng + g.nm) {
             ctrl->m[a] = v;
         } else if (e < g.ng + g.nm + g.nc) {
-            int l = a - 2 * s - 1, j = b;
+            int l = a - 2 * s - 1, j = g.cp ? b - s : b;
             ctrl->C[l + j * s] = v;
         } else {
-            ctrl->q[a - 3 * s - 1] = v;
+            ctrl->q[a - (g.cp ? 2 * s + 1 : 3 * s + 1)] = v;
         }
     });
     if (threadIdx.x == 0) ctrl->with_q = g.nq > 0;

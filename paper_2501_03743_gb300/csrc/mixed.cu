@@ -127,15 +127,17 @@ __device__ __forceinline__ void close_step(Ctrl* ctrl, double* hist, double rr) 
 
 // P = U + P_old beta, AP = AU + AP_old beta, x += P alpha in FP64 (U FP32);
 // with write_r also r -= AP alpha, u_1 = B^-1 r in FP32 and the stop test on
-// the recursive residual (steps without residual replacement).
+// the recursive residual (steps without residual replacement).  Without
+// keep_ap (the residual replaced every step, and C formed from P_old and
+// A U) A P is neither formed nor stored.
 template <int SB>
 __global__ void __launch_bounds__(kThreads) k_mx_update(int n, int ldn, int s, float* __restrict__ ublk,
                                                         const double* __restrict__ aublk,
                                                         double* __restrict__ p_new, const double* __restrict__ p_old,
                                                         double* __restrict__ xw, double* __restrict__ r,
                                                         const double* __restrict__ dinv, double dinv_c,
-                                                        double* __restrict__ part, int first, int write_r, Ctrl* ctrl,
-                                                        double* __restrict__ hist) {
+                                                        double* __restrict__ part, int first, int write_r, int keep_ap,
+                                                        Ctrl* ctrl, double* __restrict__ hist) {
     if (__ldcg(&ctrl->done)) return;
     __shared__ double sb[SB * SB];
     __shared__ double sa[SB], sna[SB];
@@ -155,29 +157,34 @@ __global__ void __launch_bounds__(kThreads) k_mx_update(int n, int ldn, int s, f
         for (int l = 0; l < SB; l++)
             if (l < s) {
                 uu[l] = (double)__ldcg(ublk + l * ld + i);
-                au[l] = __ldcg(aublk + l * ld + i);
+                if (keep_ap) au[l] = __ldcg(aublk + l * ld + i);
                 if (!first) {
                     po[l] = __ldcg(p_old + l * ld + i);
-                    apo[l] = __ldcg(p_old + (s + l) * ld + i);
+                    if (keep_ap) apo[l] = __ldcg(p_old + (s + l) * ld + i);
                 }
             }
         double xn = xw[i], rn = write_r ? r[i] : 0.0;
 #pragma unroll
         for (int jj = 0; jj < SB; jj++) {
             if (jj < s) {
-                double p = uu[jj], ap = au[jj];
+                double p = uu[jj];
                 if (!first) {
 #pragma unroll
                     for (int l = 0; l < SB; l++)
-                        if (l < s) {
-                            p = fma(po[l], sb[l + jj * SB], p);
-                            ap = fma(apo[l], sb[l + jj * SB], ap);
-                        }
+                        if (l < s) p = fma(po[l], sb[l + jj * SB], p);
                 }
                 __stcs(p_new + jj * ld + i, p);  // read again only next step
-                __stcs(p_new + (s + jj) * ld + i, ap);
                 xn = fma(p, sa[jj], xn);
-                if (write_r) rn = fma(ap, sna[jj], rn);
+                if (keep_ap) {
+                    double ap = au[jj];
+                    if (!first) {
+#pragma unroll
+                        for (int l = 0; l < SB; l++)
+                            if (l < s) ap = fma(apo[l], sb[l + jj * SB], ap);
+                    }
+                    __stcs(p_new + (s + jj) * ld + i, ap);
+                    if (write_r) rn = fma(ap, sna[jj], rn);
+                }
             }
         }
         xw[i] = xn;
@@ -351,13 +358,16 @@ int run_mixed(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
             }
             P.end(FAM_MPK, k);
             P.begin();
+            // with the residual replaced every step, C = P_old^T (A U) and A P is never formed
             k_gram<ArithF64, SB, float><<<Gg, kThreads, smem_gram, st>>>(n, (int)L.ldn, s, nullptr, ub, aub, L.r,
-                                                                         po, k > 0 ? 1 : 0, 1, L.part, k, L.ctrl);
+                                                                         po, k > 0 ? 1 : 0, every == 1 ? 2 : 1,
+                                                                         L.part, k, L.ctrl);
             P.end(FAM_DIR, k);
             const bool replace = (k + 1) % every == 0;
             P.begin();
             k_mx_update<SB><<<Gu, kThreads, 0, st>>>(n, (int)L.ldn, s, ub, aub, pn, po, L.xw, L.r, dinv_d, dinv_c,
-                                                     L.part, k == 0, replace ? 0 : 1, L.ctrl, L.hist);
+                                                     L.part, k == 0, replace ? 0 : 1, every == 1 ? 0 : 1, L.ctrl,
+                                                     L.hist);
             if (replace) {
                 k_mx_replace<DM><<<Gr, kThreads, smem_rep, st>>>(M, L.xw, L.r0, L.r, dinv_d, dinv_c, ub, L.part,
                                                                  L.ctrl, L.hist);
