@@ -289,6 +289,20 @@ struct BK {
                 }
                 return dot2_result(d);
             } else {
+                if constexpr (A::kind == 0 && LAP) {
+                    // FP64 7-point Laplacian class: the neighbour sum in fixed point on
+                    // the integer units (lap_neighbour_sum), then one FMA with the centre
+                    // (the 27-point rows keep the FMA loop below: their 26 fixed-point
+                    // terms would triple this kernel's registers)
+                    if (y.dlap && y.dk == 7 && y.dcen == 3) {
+                        auto ld = [&](int t) {
+                            const S* px = v + (size_t)(i + soff[t]) * R + r;
+                            return RO ? A::ldg(px) : A::ldcg(px);
+                        };
+                        const double Sn = lap_neighbour_sum<7>(m, ld);
+                        return ::fma((double)scf[3], ld(3), (double)y.dco * Sn);
+                    }
+                }
                 for (int t = 0; t < y.dk; t++) {
                     if (!((m >> t) & 1u)) continue;
                     const S* px = v + (size_t)(i + soff[t]) * R + r;

@@ -464,37 +464,39 @@ __host__ __device__ constexpr int dia_min_blocks() {
 // D^-1 A x = x + (c_off / d) S for the Jacobi-scaled level.  x must be
 // readable at every index in [-g, n + g) for g >= max |offset| (the solvers
 // carve such margins).  epi(i, S, x_i) runs once per row, rows grid-stride.
+// Sum of the off-centre terms (mask bit t set) of a Laplacian-class row with K
+// offsets, offset 0 at index K/2; ld(t) loads the term of offset t as a double.
+template <int K, class LD>
+__device__ __forceinline__ double lap_neighbour_sum(uint32_t m, LD ld) {
+    constexpr int C = K / 2;
+    uint64_t w[K - 1];
+#pragma unroll
+    for (int t = 0; t < K; t++) {
+        if (t == C) continue;
+        const double v = ld(t);
+        w[t < C ? t : t - 1] = ((m >> t) & 1u) ? (uint64_t)__double_as_longlong(v) : 0ull;
+    }
+    uint64_t sb;
+    if (fixsum<K - 1>(w, &sb)) return __longlong_as_double((long long)sb);
+    double d[K - 1];  // the rare row the fixed-point path declines: a pairwise tree of FP64 additions
+#pragma unroll
+    for (int q = 0; q < K - 1; q++) d[q] = __longlong_as_double((long long)w[q]);
+#pragma unroll
+    for (int h = 1; h < K - 1; h *= 2) {
+#pragma unroll
+        for (int q = 0; q + h < K - 1; q += 2 * h) d[q] += d[q + h];
+    }
+    return d[0];
+}
+
 template <int K, class EPI>
 __device__ __forceinline__ void spmv_dia_lap_f64(const MatView& M, const double* __restrict__ x, EPI epi) {
     constexpr int C = K / 2;  // symmetric pattern: offset 0 sits in the middle
     const int n = M.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t m = __ldg(M.dmask + i);
-        double v[K];
-#pragma unroll
-        for (int t = 0; t < K; t++) v[t] = __ldg(x + (i + M.doff[t]));
-        uint64_t w[K - 1];
-#pragma unroll
-        for (int t = 0; t < K; t++) {
-            if (t == C) continue;
-            w[t < C ? t : t - 1] = ((m >> t) & 1u) ? (uint64_t)__double_as_longlong(v[t]) : 0ull;
-        }
-        uint64_t sb;
-        double S;
-        if (fixsum<K - 1>(w, &sb)) {
-            S = __longlong_as_double((long long)sb);
-        } else {  // a pairwise tree of FP64 additions
-            double d[K - 1];
-#pragma unroll
-            for (int q = 0; q < K - 1; q++) d[q] = __longlong_as_double((long long)w[q]);
-#pragma unroll
-            for (int h = 1; h < K - 1; h *= 2) {
-#pragma unroll
-                for (int q = 0; q + h < K - 1; q += 2 * h) d[q] += d[q + h];
-            }
-            S = d[0];
-        }
-        epi(i, S, v[C]);
+        const double S = lap_neighbour_sum<K>(m, [&](int t) { return __ldg(x + (i + M.doff[t])); });
+        epi(i, S, __ldg(x + i));
     }
 }
 
