@@ -88,6 +88,8 @@ def parse():
     p.add_argument("--no-sweep", action="store_true", help="skip the s in {1,2,4,6,8} sweep")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--fused-mpk", action="store_true", help="several matrix-powers levels per launch (L2-resident)")
+    p.add_argument("--fma-update", action="store_true",
+                   help="FP64, s <= 4: form the block update's P and Q with FP64 FMAs instead of fixed point")
     p.add_argument("--workload", default="poisson", choices=["poisson", "batch", "mixed27", "cheb", "peaks"],
                    help="poisson: one 7-point solve (the headline); batch: the batched serving mix; "
                         "mixed27: 27-point 192^3 in mixed precision to 1e-10; cheb: Chebyshev basis with "
@@ -134,9 +136,9 @@ def byte_model(n, nnz, vbytes, s, arith, fused=False, dia=False):
                 pcg_spmv=Md + 2 * V, pcg_update=6 * V + dv, pcg_dir=3 * V + dv)
 
 
-def traffic(a, family, n, dia):
+def traffic(a, family, n, dia, fixed=False):
     """Measured DRAM bytes per launch of `family`, scaled to n rows, or None."""
-    per = NCU_TRAFFIC_PER_ROW.get(a.arith)
+    per = NCU_TRAFFIC_PER_ROW.get(a.arith + ("-fixed" if fixed and family == "update" else ""))
     if per is None or a.s != 4 or a.fused_mpk or not dia or family not in per:
         return None
     return round(per[family] * n)
@@ -309,19 +311,26 @@ def workload_name(N, s, arith):
             f"seed=rank, x0=0, tol 1e-8; arithmetic {arith}")
 
 
-def fp64_ops_model(s, K=7):
+def fp64_ops_model(s, K=7, fixed_update=False):
     """FP64 operations per row of the FP64 kernels on a Laplacian-class stencil
     in the diagonal form under a constant Jacobi scale (one DFMA, DADD or DMUL
     per thread is one operation).  The neighbour sum runs on the integer units
     (fixed point, csrc/fixsum.cuh) and costs no FP64 operation, whatever K:
     level j: one FMA for u_{j+1} and one for each moment (the second moment is
-    skipped on the last level); block update: s^2 FMAs each for P and Q, s
+    skipped on the last level); block update: s^2 FMAs each for P and Q (none
+    with the fixed-point update, whose P and Q are integer dot products), s
     each for x and z, one for sum z^2 (first step: no P, Q FMAs); PCG: SpMV
     one FMA for A p and one for p . Ap; update x, r, ||r||^2; direction
     u = D^-1 r and p = u + beta p."""
     lvl = [2 + (1 if 2 * j + 2 <= 2 * s - 1 else 0) for j in range(s)]
-    return dict(level=lvl, level_avg=sum(lvl) / s, update=2 * s * s + 2 * s + 1, update_first=2 * s + 1,
+    upd = 2 * s + 1 if fixed_update else 2 * s * s + 2 * s + 1
+    return dict(level=lvl, level_avg=sum(lvl) / s, update=upd, update_first=2 * s + 1,
                 pcg_spmv=2, pcg_update=3, pcg_dir=2)
+
+
+def fixed_update_used(a):
+    """The FP64 block update forms P and Q in fixed point at s <= 4 (csrc/kernels.cuh k_update_fix)."""
+    return a.arith == "f64" and a.s <= 4 and not a.fma_update and not a.fused_mpk
 
 
 def alu_peak(sm_count, mhz=2070.0):
@@ -374,7 +383,7 @@ def main():
     b = torch.from_numpy(sysm["b"]).cuda()
     x = torch.zeros_like(b)
     solver = sscg.Solver(A, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, profile=True,
-                         fused_mpk=a.fused_mpk)
+                         fused_mpk=a.fused_mpk, fma_update=a.fma_update)
     stream = ctx.stream
 
     def timed(fn, count):
@@ -415,7 +424,8 @@ def main():
     value_yard = sum_over_ranks(pg, yard_solve * a.steps) / (total_ms * 1e-3) / 1e9
 
     # kernel families over the timed steps (the library's CUDA events on its stream)
-    ops = fp64_ops_model(a.s)
+    fixed = fixed_update_used(a)
+    ops = fp64_ops_model(a.s, fixed_update=fixed)
     fam = {}
     for key, cnt, per, fops in (("mpk", "n_mpk", bm["level_avg"], ops["level_avg"]),
                                 ("update", "n_update", bm["update"], ops["update"])):
@@ -429,6 +439,8 @@ def main():
     kernel_names = {"mpk": ("k_level (matrix-powers level: diagonal-form SpMV + Jacobi + moments)" if dia else
                             "k_level (matrix-powers level: CSR SpMV + Jacobi + moments)"),
                     "update": ("k_update_tma (block update P, AP, x, r + next z)" if a.fused_mpk else
+                               "k_update_fix (block update: P, Q = D^-1 A P as fixed-point dot products on the "
+                               "integer multipliers; x, z FP64 FMAs)" if fixed else
                                "k_update_q (block update P, Q = D^-1 A P, x, z)")}
     gbs = {k: round(v["bytes_per_launch"] / (v["ms"] / max(v["launches"], 1) * 1e-3) / 1e9, 1) for k, v in fam.items()}
     if a.arith == "f64" and dia and not a.fused_mpk:
@@ -436,12 +448,19 @@ def main():
         gops = {k: round(v["ops_per_launch"] / (v["ms"] / max(v["launches"], 1) * 1e-3) / 1e9, 1)
                 for k, v in fam.items()}
         achieved = d["ops_per_launch"] / avg_s / 1e9
-        roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak / 1e9, 1), "unit": "Gop/s",
-                    "frac": round(achieved * 1e9 / peak, 4), "traffic": traffic(a, dom, n, dia),
+        fp64_frac = achieved * 1e9 / peak
+        hbm_frac = gbs[dom] / hbm
+        if fp64_frac >= hbm_frac:  # the dominant kernel's binding roof: the larger of its two fractions
+            head = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak / 1e9, 1), "unit": "Gop/s",
+                    "frac": round(fp64_frac, 4),
+                    "peak_source": f"FP64 operations (DFMA/DADD/DMUL per thread) at 2 per clock per SM x "
+                                   f"{sm_count} SMs x 2070 MHz, from the nominal 1.25 TFLOP/s and maximum SM clock; "
+                                   "the probe of include/sscg_probe.h measures 529 Gop/s"}
+        else:
+            head = {"bound": "hbm", "achieved": gbs[dom], "peak": hbm, "unit": "GB/s", "frac": round(hbm_frac, 4),
+                    "peak_source": f"measured copy bandwidth ({hbm_src})"}
+        roofline = {**head, "traffic": traffic(a, dom, n, dia, fixed),
                     "kernel": kernel_names[dom],
-                    "peak_source": f"FP64 operations (DFMA/DADD/DMUL per thread) at 2 per clock per SM x {sm_count} "
-                                   "SMs x 2070 MHz, from the nominal 1.25 TFLOP/s and maximum SM clock; "
-                                   "the probe of include/sscg_probe.h measures 529 Gop/s",
                     "ops_per_row": {"level": round(ops["level_avg"], 2), "update": ops["update"]},
                     "family_ms_per_solve": {k: round(v["ms"] / a.steps, 3) for k, v in fam.items()},
                     "family_gops": gops, "family_frac": {k: round(g * 1e9 / peak, 4) for k, g in gops.items()},
@@ -450,7 +469,8 @@ def main():
     else:
         achieved = d["bytes_per_launch"] / avg_s / 1e9
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                    "frac": round(achieved / hbm, 4), "traffic": traffic(a, dom, n, dia), "kernel": kernel_names[dom],
+                    "frac": round(achieved / hbm, 4), "traffic": traffic(a, dom, n, dia, fixed),
+                    "kernel": kernel_names[dom],
                     "peak_source": f"measured copy bandwidth ({hbm_src})",
                     "family_ms_per_solve": {k: round(v["ms"] / a.steps, 3) for k, v in fam.items()},
                     "family_gbs": gbs}
@@ -487,6 +507,23 @@ def main():
                    pfcg_rel_res_true=fres[-1].rel_res_true, speedup_vs_pfcg=round(pfcg_ms / ms_per_step, 4))
         del fsolver
 
+    # the same FP64 solve with the block update's P and Q formed by FP64 FMAs
+    fmau = None
+    if fixed and not a.no_pcg:
+        msolver = sscg.Solver(A, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, profile=True, fma_update=True)
+        x.zero_()
+        msolver.solve(b, x)
+        mms, mres = timed(lambda: msolver.solve(b, x), 2)
+        m_ms = max_over_ranks(pg, sum(mms)) / len(mms)
+        tu = sum(r.profile["t_update_ms"] for r in mres) / len(mres)
+        fmau = {"fma_update_solve_ms": round(m_ms, 3), "fma_update_outer_iters": mres[-1].outer_iters,
+                "fma_update_rel_res_true": mres[-1].rel_res_true,
+                "fma_update_update_ms_per_solve": round(tu, 3),
+                "fixed_update_speedup": round(m_ms / ms_per_step, 4)}
+        if pcg:
+            fmau["fma_update_speedup_vs_pcg"] = round(pcg["pcg_solve_ms"] / m_ms, 4)
+        del msolver
+
     # the same solve and PCG in double-float (pairs of FP32, about 48 bits, FP32 exponent range)
     df = None
     if a.arith == "f64" and not a.no_df64:
@@ -516,7 +553,8 @@ def main():
                 sweep[str(sv)] = dict(ms=round(ms_per_step, 3), outer=r0.outer_iters, rel_res_true=r0.rel_res_true,
                                       status=r0.status, true_res_below_tol=bool(r0.rel_res_true <= a.tol))
                 continue
-            ssolver = sscg.Solver(A, s=sv, tol=a.tol, maxit=5000, arith=a.arith, fused_mpk=a.fused_mpk)
+            ssolver = sscg.Solver(A, s=sv, tol=a.tol, maxit=5000, arith=a.arith, fused_mpk=a.fused_mpk,
+                                  fma_update=a.fma_update)
             x.zero_()
             ssolver.solve(b, x)
             sms, sres = timed(lambda: ssolver.solve(b, x), 2)
@@ -529,7 +567,7 @@ def main():
     bh = torch.from_numpy(sysm["b"]).pin_memory()
     xh = torch.zeros(n, dtype=torch.float64).pin_memory()
     hsolver = sscg.Solver(A, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, host_vectors=True,
-                          fused_mpk=a.fused_mpk)
+                          fused_mpk=a.fused_mpk, fma_update=a.fma_update)
     xh.zero_()
     hsolver.solve(bh, xh)
     e2e_t = []
@@ -576,6 +614,8 @@ def main():
         }
         if pcg:
             line.update(pcg)
+        if fmau:
+            line.update(fmau)
         if df:
             line.update(df)
         if sweep:
@@ -1007,7 +1047,7 @@ def run_peaks(a, world, rank, local, pg):
     clocks = Clocks(local)
     clocks.start()
     rates = {}
-    for kind in ("dfma", "dadd", "dmul", "dmma", "ffma", "ialu", "imad"):
+    for kind in ("dfma", "dadd", "dmul", "dmma", "ffma", "ialu", "imad", "imad_wide", "i2f64", "f2i64"):
         ops, ms, it = probe_calibrated(ctx, kind)
         rates[kind] = {"ops_per_s": ops, "ms": round(ms, 3), "iters": it}
     # equal solo times: the DMMA warps' iteration count scaled from the solo rates

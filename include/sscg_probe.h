@@ -22,8 +22,9 @@ extern "C" {
 
 /* Probe kinds.  Operation counts: one FP64 fused multiply-add, add or
  * multiply per thread and instruction is one operation; one warp-wide
- * mma.sync.m8n8k4.f64 is 256 multiply-adds (8 x 8 x 4); one FP32 FMA or one
- * 32-bit integer instruction per thread is one operation. */
+ * mma.sync.m8n8k4.f64 is 256 multiply-adds (8 x 8 x 4); one FP32 FMA, one
+ * 32-bit integer instruction, one wide multiply-add or one conversion per
+ * thread is one operation. */
 typedef enum {
     SSCG_PROBE_DFMA = 0,      /* fma(a, m, c), FP64 */
     SSCG_PROBE_DADD = 1,      /* a + c, FP64 */
@@ -32,7 +33,10 @@ typedef enum {
     SSCG_PROBE_DFMA_DMMA = 4, /* even warps DFMA (iters_a), odd warps DMMA (iters_b), one launch */
     SSCG_PROBE_FFMA = 5,      /* fmaf, FP32 */
     SSCG_PROBE_IALU = 6,      /* (x ^ x' ^ y) + z on 32-bit integers (x' another chain): one LOP3 and one add */
-    SSCG_PROBE_IMAD = 7       /* x * m + x' on 32-bit integers (x' another chain) */
+    SSCG_PROBE_IMAD = 7,      /* x * m + x' on 32-bit integers (x' another chain) */
+    SSCG_PROBE_IMAD_WIDE = 8, /* mad.wide.s32: a * m + c, 32 x 32 bits into a 64-bit sum (c another chain) */
+    SSCG_PROBE_I2F64 = 9,     /* cvt.rn.f64.s64: a 64-bit integer to FP64 */
+    SSCG_PROBE_F2I64 = 10     /* cvt.rzi.s64.f64: FP64 to a 64-bit integer, truncated */
 } sscg_probe_kind;
 
 typedef struct sscg_ctx sscg_ctx;

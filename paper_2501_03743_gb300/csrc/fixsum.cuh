@@ -17,7 +17,7 @@
 // zeros sums to +0).
 //
 // Integer code only (host and device), so the CPU tests compile it and
-// compare it with exact rational sums.
+// compare it with exact rational sums and dot products.
 #pragma once
 
 #include <stdint.h>
@@ -38,22 +38,80 @@ SSCG_HD int fix_clz64(uint64_t v) {
 #endif
 }
 
+SSCG_HD int max_i(int a, int b) { return a > b ? a : b; }
+
+SSCG_HD int fix_exp(uint64_t b) { return (int)((b >> 52) & 0x7FFu); }
+
+// m >> sh for 0 <= sh; shift amounts of 64 or more give 0 (PTX clamps them).
+SSCG_HD uint64_t fix_shr(uint64_t m, int sh) {
+#if defined(__CUDA_ARCH__)
+    uint64_t r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(m), "r"(sh));
+    return r;
+#else
+    return sh >= 64 ? 0ull : m >> sh;
+#endif
+}
+
+// The magnitude a with the sign of the FP64 bit pattern b: (a ^ s) - s with
+// s all ones for a negative b.
+SSCG_HD int64_t fix_apply_sign(uint64_t a, uint64_t b) {
+    const uint64_t sg = (uint64_t)((int64_t)b >> 63);
+    return (int64_t)((a ^ sg) - sg);
+}
+
+// Round the value acc 2^(e0 - 1075) (|acc| < 2^63) to FP64, to nearest with
+// ties to even.  Returns true with the bit pattern in *out (+0 for acc = 0),
+// or false when the result is not a normal FP64 number.
+SSCG_HD bool fix_pack(int64_t acc, int e0, uint64_t* out) {
+    if (acc == 0) {
+        *out = 0ull;  // +0, as x + (-x) gives in FP64
+        return true;
+    }
+    const uint64_t sg = (uint64_t)(acc >> 63);
+    const uint64_t mag = ((uint64_t)acc ^ sg) - sg;  // |acc| < 2^63
+    const int lz = fix_clz64(mag);                   // >= 1
+    const uint64_t nrm = mag << lz;                  // leading bit at bit 63
+    // 53 bits rounded to nearest, ties to even: bits 63..11 plus the round bit
+    // (10) when the sticky bits (9..0) or the last kept bit (11) are set
+    const uint64_t keep = nrm >> 11;
+    const uint64_t up = (nrm >> 10) & (keep | (uint64_t)((nrm & 0x3FFull) != 0)) & 1ull;
+    const int E = e0 - lz + 11;  // biased exponent of mag 2^(e0 - 1075): leading bit 63 - lz
+    if (E <= 0 || E >= 0x7FF) return false;  // a subnormal result, or overflow
+    // the exponent field E - 1 plus the mantissa with its implicit bit: a
+    // rounding carry into bit 53 raises the exponent by one
+    const uint64_t bits = ((uint64_t)(E - 1) << 52) + keep + up;
+    if ((bits >> 52) >= 0x7FF) return false;  // rounded up to overflow
+    *out = bits | (sg << 63);
+    return true;
+}
+
+#if defined(__CUDACC__)
+// fix_pack on the conversion unit, for 53 <= e0 <= 2035 (then every nonzero
+// |R| < 2^63 lands in the normal range): R rounded to FP64 (to nearest, ties
+// to even) and scaled by 2^(e0 - 1075) exactly through its exponent field.
+// The same result as fix_pack; the conversion runs at the FP64 rate.
+__device__ __forceinline__ double fix_pack_cvt(int64_t R, int e0) {
+    const double d = (double)R;
+    const long long b = __double_as_longlong(d) + ((long long)(e0 - 1075) << 52);
+    return R == 0 ? 0.0 : __longlong_as_double(b);
+}
+#endif
+
 // Sum of the K values with raw FP64 bit patterns t[0..K-1] (K <= 31).
 // Returns true with the FP64 bit pattern of the rounded sum in *out, or
 // false when the fixed-point path does not apply (see the file comment).
 template <int K>
 SSCG_HD bool fixsum(const uint64_t (&t)[K], uint64_t* out) {
     static_assert(K >= 1 && K <= 31, "4 guard bits leave room for 31 terms below 2^57");
-    int emax = 1;
-    uint64_t any = 0;
+    int emax = 0;
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        const int E = (int)((t[k] >> 52) & 0x7FFu);
-        if (E == 0x7FF) return false;  // NaN or infinity
-        emax = E > emax ? E : emax;    // subnormals (E = 0) share exponent 1 without the implicit bit
-        any |= t[k] << 1;              // nonzero unless the term is +0 or -0
-    }
-    if (emax < 57) {  // the result's scale 2^(emax - 1079) would not be a normal number
+    for (int k = 0; k < K; k++) emax = max_i(emax, fix_exp(t[k]));
+    if (emax == 0x7FF) return false;  // a NaN or an infinity
+    if (emax < 57) {                  // the result's scale 2^(emax - 1079) would not be a normal number
+        uint64_t any = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) any |= t[k] << 1;  // nonzero unless the term is +0 or -0
         if (any) return false;
         *out = 0ull;  // every term is zero
         return true;
@@ -61,37 +119,117 @@ SSCG_HD bool fixsum(const uint64_t (&t)[K], uint64_t* out) {
     int64_t acc = 0;
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        const int E = (int)((t[k] >> 52) & 0x7FFu);
-        const uint64_t implicit = E ? (1ull << 52) : 0ull;
-        const uint64_t m = ((t[k] & 0xFFFFFFFFFFFFFull) | implicit) << 4;  // < 2^57
-        const int sh = emax - (E ? E : 1);
-        const int64_t a = sh >= 64 ? 0 : (int64_t)(m >> sh);
-        acc += (t[k] >> 63) ? -a : a;
+        // the implicit bit is set for zeros and subnormals too: their shift emax - 0 >= 57 clears them
+        const uint64_t m = ((t[k] & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 4;  // < 2^57
+        acc += fix_apply_sign(fix_shr(m, emax - fix_exp(t[k])), t[k]);
     }
-    if (acc == 0) {
-        *out = 0ull;  // +0, as x + (-x) gives in FP64
+#if defined(__CUDA_ARCH__)
+    if (emax <= 2039) {  // e0 = emax - 4 <= 2035: round on the conversion unit
+        *out = (uint64_t)__double_as_longlong(fix_pack_cvt(acc, emax - 4));
         return true;
     }
-    const uint64_t sign = acc < 0 ? (1ull << 63) : 0ull;
-    uint64_t mag = acc < 0 ? (uint64_t)(-acc) : (uint64_t)acc;  // < 2^62
-    const int p = 63 - fix_clz64(mag);                          // leading bit: mag in [2^p, 2^(p+1))
-    int E = p + emax - 56;                                      // biased exponent of mag 2^(emax - 1079)
-    uint64_t mant;
-    if (p <= 52) {
-        mant = mag << (52 - p);  // exact
-    } else {
-        const int sh = p - 52;
-        mant = mag >> sh;
-        const uint64_t rem = mag & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (mant & 1ull))) mant++;
-        if (mant == (1ull << 53)) {  // rounding carried into a new leading bit
-            mant >>= 1;
-            E++;
-        }
-    }
-    if (E >= 0x7FF) return false;  // overflow: the FP64 additions give the infinity
-    *out = sign | ((uint64_t)E << 52) | (mant & 0xFFFFFFFFFFFFFull);
-    return true;
+#endif
+    return fix_pack(acc, emax - 4, out);  // acc counts units of 2^(emax - 1079)
 }
+
+// ---------------------------------------------------------------------------
+// Short dot products  v_0 c_0 + ... + v_{K-1} c_{K-1}  of FP64 values v (one
+// row's entries of a few vectors) with FP64 coefficients c that are the same
+// for every row (one column of a small matrix), on the integer multipliers.
+// The values of a row are aligned to the row's largest exponent E and the
+// coefficients of a column to the column's largest exponent Fc, both with
+// kFixGuard guard bits:
+//   a = trunc(v 2^(1075 + kFixGuard - E)),  C = round(c 2^(1075 + kFixGuard - Fc)),
+// so |a|, |C| < 2^61 (53 significant bits and 8 guard bits).  Each is split
+// into signed 32-bit limbs, a = a_h 2^32 + a_l with a_l in [-2^31, 2^31), and
+// the products are summed with 32 x 32 -> 64-bit multiply-adds:
+//   hh = sum a_h C_h,  ma = sum a_h C_l,  mc = sum a_l C_h   (all exact)
+//   R  = hh + round(ma / 2^32) + round(mc / 2^32)
+// (the a_l C_l products, below 2^62, are dropped); R 2^(E + Fc - 2102)
+// approximates the dot product and is rounded once to FP64.  For K <= 5
+// terms every sum stays below 2^63 (|a_h|, |C_h| <= 2^29).  Error: the
+// dropped products and the two roundings, at most (1 + K/4) 2^64 units of
+// a C, and the truncation of a and the rounding of C, below K (2^61 + 2^60)
+// units; in all at most (1 + 7K/16) 2^(E + Fc - 2102), that is
+// (1 + 7K/16) 2^-56 times the row's largest |v| times the column's largest
+// |c|, plus half an ulp of the result.  A sequence of K - 1 FP64 fused
+// multiply-adds is bounded by (K - 1) 2^-53 sum |v c|: on vectors of similar
+// magnitude the fixed-point error is the smaller of the two.
+constexpr int kFixGuard = 8;
+constexpr int kFixMaxTerms = 5;
+
+struct FixLimbs {
+    int32_t h, l;  // value h 2^32 + l
+};
+
+// ma and mc start at 2^31, so that their high words are the rounded
+// quotients by 2^32.
+struct FixAcc {
+    int64_t hh = 0, ma = 0x80000000ll, mc = 0x80000000ll;
+};
+
+// a = h 2^32 + l with l the low word read as a signed number: h is the high
+// word plus one when l < 0.
+SSCG_HD FixLimbs fix_split(int64_t a) {
+    FixLimbs r;
+    const uint32_t lo = (uint32_t)(uint64_t)a;
+    r.l = (int32_t)lo;
+    r.h = (int32_t)((uint32_t)((uint64_t)a >> 32) + (lo >> 31));
+    return r;
+}
+
+// The aligned value a = trunc(v 2^(1075 + kFixGuard - E)) of the FP64 value
+// with bit pattern b, for a row exponent E >= the value's exponent and
+// E >= 62 (then subnormal values, below 2^-1022, truncate to 0).
+SSCG_HD FixLimbs fix_align(uint64_t b, int E) {
+    // the implicit bit is set for zeros and subnormals too: with E >= 62 their
+    // shift E - 0 clears them (m < 2^61)
+    const uint64_t m = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << kFixGuard;  // < 2^61
+    return fix_split(fix_apply_sign(fix_shr(m, E - fix_exp(b)), b));
+}
+
+// The aligned coefficient C = round(c 2^(1075 + kFixGuard - Fc)) (ties away
+// from zero) of the FP64 coefficient with bit pattern b, for a column
+// exponent Fc >= the coefficient's exponent and Fc >= 63 (then subnormal
+// coefficients round to 0).
+SSCG_HD FixLimbs fix_coef(uint64_t b, int Fc) {
+    const int e = fix_exp(b);
+    const int d = Fc - e;
+    const uint64_t m = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << kFixGuard;  // < 2^61
+    int64_t c;
+    if (e == 0 || d >= 63) c = 0;  // below 2^-1022, or below half a unit
+    else c = (int64_t)(d == 0 ? m : ((m >> (d - 1)) + 1) >> 1);
+    if (b >> 63) c = -c;
+    return fix_split(c);
+}
+
+// acc += a b for signed 32-bit a, b (exact in 64 bits): one mad.wide.s32.
+SSCG_HD void fix_mad_wide(int64_t& acc, int32_t a, int32_t b) {
+#if defined(__CUDA_ARCH__)
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+#else
+    acc += (int64_t)a * (int64_t)b;
+#endif
+}
+
+SSCG_HD void fix_mad(FixAcc& s, FixLimbs a, FixLimbs c) {
+    fix_mad_wide(s.hh, a.h, c.h);
+    fix_mad_wide(s.ma, a.h, c.l);
+    fix_mad_wide(s.mc, a.l, c.h);
+}
+
+// R of the accumulated products (units of 2^64 of a C).
+SSCG_HD int64_t fix_total(const FixAcc& s) { return s.hh + (s.ma >> 32) + (s.mc >> 32); }
+
+// The exponent offset e0 of a dot product: R 2^(e0 - 1075) = R 2^(E + Fc - 2102).
+SSCG_HD int fix_dot_e0(int E, int Fc) { return E + Fc - 2 * kFixGuard - 1011; }
+
+// The FP64 dot product from R, for row exponent E and column exponent Fc:
+// R 2^(E + Fc - 2102) rounded to nearest; false when not a normal number.
+SSCG_HD bool fix_dot_result(const FixAcc& s, int E, int Fc, uint64_t* out) {
+    return fix_pack(fix_total(s), fix_dot_e0(E, Fc), out);
+}
+
+
 
 }  // namespace sscg

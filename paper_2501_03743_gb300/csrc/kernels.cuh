@@ -378,6 +378,51 @@ inline int update_tma_setup(sscg_ctx* ctx, int64_t n, int s, size_t* smem, int* 
     return 0;
 }
 
+// End of the z / Q block updates: the grid's sums of ||r||^2 and mu_0 = r . z
+// (rr and rz of this thread; without a diagonal array rz holds sum z^2 and r =
+// diag_c z), the step count, the residual history and the stopping test.
+template <class A>
+__device__ __forceinline__ void update_q_finish(typename A::R rr, typename A::R rz, bool has_diag, double diag_c,
+                                                double* red, double* __restrict__ part, Ctrl* ctrl,
+                                                double* __restrict__ hist) {
+    if (!has_diag) {  // r = d z: ||r||^2 = d^2 sum z^2, mu_0 = d sum z^2 (d = 1 without a preconditioner)
+        const typename A::R dcst = A::from_d(diag_c);
+        if (diag_c != 0.0) rz = A::mul(dcst, rz);
+        rr = diag_c != 0.0 ? A::mul(dcst, rz) : rz;
+    }
+    typename A::R v[2] = {rr, rz};
+    double out[2];
+    block_sum<A, 2>(v, red, out);
+    const int G = gridDim.x;
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = out[0];
+        part[G + blockIdx.x] = out[1];
+    }
+    if (!last_cta(&ctrl->ticket[2])) return;
+    __shared__ double sh[32];
+    double srr = cta_sum_partials(part, G, sh);
+    double srz = cta_sum_partials(part + G, G, sh);
+    if (threadIdx.x == 0) {
+        int step = ctrl->step + 1;
+        double rel = sqrt(srr) / ctrl->bnorm;
+        ctrl->step = step;
+        ctrl->relres = rel;
+        ctrl->mu[0] = srz;
+        hist[step] = rel;
+        ctrl->nhist = step + 1;
+        if (!isfinite(rel)) {
+            ctrl->status = 2;
+            ctrl->done = 1;
+        } else if (rel < ctrl->tol) {
+            ctrl->status = 0;
+            ctrl->done = 1;
+        } else if (step >= ctrl->maxit) {
+            ctrl->status = 1;
+            ctrl->done = 1;
+        }
+    }
+}
+
 // Block update carrying z = D^-1 r and Q = D^-1 A P (diagonal
 // preconditioner D, or none).  With u_{j+1} = D^-1 A u_j the level kernel
 // never stores A U: D^-1 A U_{1..s} = U_{2..s+1}, so
@@ -414,7 +459,6 @@ __global__ void __launch_bounds__(kThreads) k_update_q(int n, int ldn, int s, ty
         sa[e] = A::from_d(ctrl->alpha[e]);
         sna[e] = A::from_d(-ctrl->alpha[e]);
     }
-    const R dcst = A::from_d(diag_c);
     __syncthreads();
     const size_t ld = (size_t)ldn;
     R rr = A::zero(), rz = A::zero();
@@ -463,40 +507,176 @@ __global__ void __launch_bounds__(kThreads) k_update_q(int n, int ldn, int s, ty
             rz = A::fma(zn, zn, rz);  // sum z^2; scaled by the constant diagonal below
         }
     }
-    if (!diag) {  // r = d z: ||r||^2 = d^2 sum z^2, mu_0 = d sum z^2 (d = 1 without a preconditioner)
-        if (diag_c != 0.0) rz = A::mul(dcst, rz);
-        rr = diag_c != 0.0 ? A::mul(dcst, rz) : rz;
+    update_q_finish<A>(rr, rz, diag != nullptr, diag_c, red, part, ctrl, hist);
+}
+
+// One half of the fixed-point block update: out_j = v_j + sum_l w_l beta_lj
+// (j < S) for one row's values v_0..v_{S-1} and w_0..w_{S-1}, all aligned to
+// their largest exponent E (fixsum.cuh), the coefficient column j of [1; beta]
+// in scf[j] with exponent fc[j].  Returns false, out untouched, when E lies
+// outside [Elo, Ehi].
+template <int S>
+__device__ __forceinline__ bool fix_update_group(const double (&v)[S], const double (&w)[S],
+                                                 const FixLimbs (&scf)[S][S + 1], const int (&fc)[S], int Elo,
+                                                 int Ehi, double (&out)[S]) {
+    unsigned hmax = 0;  // the largest exponent field (sign cleared, as an integer)
+#pragma unroll
+    for (int l = 0; l < S; l++)
+        hmax = max(hmax, max((unsigned)__double2hiint(v[l]) & 0x7FF00000u,
+                             (unsigned)__double2hiint(w[l]) & 0x7FF00000u));
+    const int E = (int)(hmax >> 20);
+    if (E < Elo || E > Ehi) return false;
+    FixLimbs av[S], aw[S];
+#pragma unroll
+    for (int l = 0; l < S; l++) {
+        av[l] = fix_align((uint64_t)__double_as_longlong(v[l]), E);
+        aw[l] = fix_align((uint64_t)__double_as_longlong(w[l]), E);
     }
-    R v[2] = {rr, rz};
-    double out[2];
-    block_sum<A, 2>(v, red, out);
-    const int G = gridDim.x;
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = out[0];
-        part[G + blockIdx.x] = out[1];
+#pragma unroll
+    for (int j = 0; j < S; j++) {
+        FixAcc acc;
+        fix_mad(acc, av[j], scf[j][0]);
+#pragma unroll
+        for (int l = 0; l < S; l++) fix_mad(acc, aw[l], scf[j][1 + l]);
+        out[j] = fix_pack_cvt(fix_total(acc), fix_dot_e0(E, fc[j]));
     }
-    if (!last_cta(&ctrl->ticket[2])) return;
-    __shared__ double sh[32];
-    double srr = cta_sum_partials(part, G, sh);
-    double srz = cta_sum_partials(part + G, G, sh);
-    if (threadIdx.x == 0) {
-        int step = ctrl->step + 1;
-        double rel = sqrt(srr) / ctrl->bnorm;
-        ctrl->step = step;
-        ctrl->relres = rel;
-        ctrl->mu[0] = srz;
-        hist[step] = rel;
-        ctrl->nhist = step + 1;
-        if (!isfinite(rel)) {
-            ctrl->status = 2;
-            ctrl->done = 1;
-        } else if (rel < ctrl->tol) {
-            ctrl->status = 0;
-            ctrl->done = 1;
-        } else if (step >= ctrl->maxit) {
-            ctrl->status = 1;
-            ctrl->done = 1;
+    return true;
+}
+
+// The same half with FP64 FMAs, in k_update_q's order.
+template <int S>
+__device__ __forceinline__ void fma_update_group(const double (&v)[S], const double (&w)[S], const double* sb,
+                                                 double (&out)[S]) {
+#pragma unroll
+    for (int j = 0; j < S; j++) {
+        double t = v[j];
+#pragma unroll
+        for (int l = 0; l < S; l++) t = ::fma(w[l], sb[l + j * S], t);
+        out[j] = t;
+    }
+}
+
+// The FP64 block update of k_update_q with P and Q formed as fixed-point dot
+// products on the integer multipliers (fixsum.cuh), for block sizes S <= 4:
+//   P_j = U_j + sum_l P_old_l beta_lj,   Q_j = U_{j+1} + sum_l Q_old_l beta_lj
+// take 3 (S + 1) 32 x 32 -> 64-bit multiply-adds each in place of S FP64 FMAs
+// (a GB300 retires about 53 of those per SM and clock against 2 FP64
+// operations).  A row's values U_1..U_S and P_old share one alignment
+// exponent, U_2..U_{S+1} and Q_old another; each column j of the coefficients
+// [1; beta_0j .. beta_{S-1}j] has its own.  x += P alpha and z -= Q alpha stay
+// FP64 FMAs on the rounded P and Q, as in k_update_q.  A half row (P or Q)
+// holding a NaN, an infinity or only values below 2^-961, or whose entries
+// could leave the normal range, takes the FP64 FMAs of k_update_q; so does
+// every row when a coefficient is not finite.  Not for the first step (no
+// P_old, Q_old).
+template <int S>
+__global__ void __launch_bounds__(kThreads, 2) k_update_fix(int n, int ldn, double* __restrict__ blk_new,
+                                                            double* __restrict__ blk_old, double* __restrict__ x,
+                                                            const double* __restrict__ diag, double diag_c,
+                                                            double* __restrict__ part, Ctrl* ctrl,
+                                                            double* __restrict__ hist) {
+    static_assert(S + 1 <= kFixMaxTerms, "the 64-bit sums of fixsum.cuh hold at most kFixMaxTerms products");
+    if (ctrl_done(ctrl)) return;
+    __shared__ double sb[S * S];
+    __shared__ double sa[S];
+    __shared__ double sna[S];
+    __shared__ FixLimbs scf[S][S + 1];
+    __shared__ int sfc[S];
+    __shared__ double red[2 * (kThreads / 32)];
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) sb[e] = ctrl->beta[e];
+    for (int e = threadIdx.x; e < S; e += blockDim.x) {
+        sa[e] = ctrl->alpha[e];
+        sna[e] = -ctrl->alpha[e];
+    }
+    __syncthreads();
+    if (threadIdx.x < S) {  // column j of [1; beta]: its exponent and aligned coefficients
+        const int j = threadIdx.x;
+        int Fc = 1023;  // the coefficient 1 of U_j
+        for (int l = 0; l < S; l++) Fc = max(Fc, fix_exp((uint64_t)__double_as_longlong(sb[l + j * S])));
+        sfc[j] = Fc;
+        scf[j][0] = fix_coef((uint64_t)__double_as_longlong(1.0), Fc);
+        for (int l = 0; l < S; l++)
+            scf[j][1 + l] = Fc < 0x7FF ? fix_coef((uint64_t)__double_as_longlong(sb[l + j * S]), Fc) : FixLimbs{0, 0};
+    }
+    __syncthreads();
+    // rows whose exponent E puts every column's result offset e0 = E + Fc - 1027
+    // in [53, 2035] (fix_pack_cvt) and E >= 62 (fix_align) take the fixed point
+    // (none when a coefficient is not finite: its column exponent is 0x7FF)
+    int fc[S];
+    int fcmin = 0x7FF, fcmax = 0;
+#pragma unroll
+    for (int j = 0; j < S; j++) {
+        fc[j] = sfc[j];
+        fcmin = min(fcmin, fc[j]);
+        fcmax = max(fcmax, fc[j]);
+    }
+    const int Elo = max(62, 53 - fix_dot_e0(0, fcmin));
+    const int Ehi = fcmax == 0x7FF ? -1 : min(0x7FE, 2035 - fix_dot_e0(0, fcmax));
+    const size_t ld = (size_t)ldn;
+    double rr = 0.0, rz = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double u[S + 1], po[S], qo[S];
+#pragma unroll
+        for (int c = 0; c <= S; c++) u[c] = __ldcg(blk_new + c * ld + i);
+#pragma unroll
+        for (int l = 0; l < S; l++) {
+            po[l] = __ldcg(blk_old + l * ld + i);
+            qo[l] = __ldcg(blk_old + (S + 1 + l) * ld + i);
         }
+        double xn = __ldcg(x + i), zn = u[0];
+        double v[S], p[S];
+        // P_j = U_j + sum_l P_old_l beta_lj
+#pragma unroll
+        for (int j = 0; j < S; j++) v[j] = u[j];
+        if (!fix_update_group<S>(v, po, scf, fc, Elo, Ehi, p)) fma_update_group<S>(v, po, sb, p);
+#pragma unroll
+        for (int j = 0; j < S; j++) {
+            __stcs(blk_new + j * ld + i, p[j]);
+            xn = ::fma(p[j], sa[j], xn);
+        }
+        // Q_j = U_{j+1} + sum_l Q_old_l beta_lj
+#pragma unroll
+        for (int j = 0; j < S; j++) v[j] = u[j + 1];
+        if (!fix_update_group<S>(v, qo, scf, fc, Elo, Ehi, p)) fma_update_group<S>(v, qo, sb, p);
+#pragma unroll
+        for (int j = 0; j < S; j++) {
+            __stcs(blk_new + (S + 1 + j) * ld + i, p[j]);
+            zn = ::fma(p[j], sna[j], zn);
+        }
+        x[i] = xn;
+        blk_old[i] = zn;  // U_1 of the next step (P_old_1 already read)
+        if (diag) {
+            const double rn = __ldcg(diag + i) * zn;
+            rr = ::fma(rn, rn, rr);
+            rz = ::fma(rn, zn, rz);
+        } else {
+            rz = ::fma(zn, zn, rz);
+        }
+    }
+    update_q_finish<ArithF64>(rr, rz, diag != nullptr, diag_c, red, part, ctrl, hist);
+}
+
+// Grid of k_update_fix for the block size s (1..4): its occupancy times the SMs.
+inline int update_fix_grid(sscg_ctx* ctx, int s, int64_t n) {
+    switch (s) {
+        case 1: return occupancy_grid(ctx, k_update_fix<1>, 0, n);
+        case 2: return occupancy_grid(ctx, k_update_fix<2>, 0, n);
+        case 3: return occupancy_grid(ctx, k_update_fix<3>, 0, n);
+        case 4: return occupancy_grid(ctx, k_update_fix<4>, 0, n);
+        default: return 0;
+    }
+}
+
+inline void launch_update_fix(int s, int grid, int64_t n, int ldn, double* blk_new, double* blk_old, double* x,
+                              const double* diag, double diag_c, double* part, Ctrl* ctrl, double* hist,
+                              cudaStream_t st) {
+    const int N = (int)n;
+    switch (s) {
+        case 1: k_update_fix<1><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 2: k_update_fix<2><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 3: k_update_fix<3><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 4: k_update_fix<4><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        default: break;
     }
 }
 

@@ -113,6 +113,66 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(long long iters_a, long
 #pragma unroll
         for (int k = 0; k < kChains; k++) u ^= x[k];
         t = (double)u - 1.0;  // -1 only if every chain ends at 0
+    } else if constexpr (KIND == SSCG_PROBE_IMAD_WIDE) {
+        // the low word of each 64-bit sum is the next multiplicand (a register, no instruction)
+        long long c[kChains];
+        const int m = (int)(2654435761u ^ (unsigned)seed);
+#pragma unroll
+        for (int k = 0; k < kChains; k++) c[k] = (long long)threadIdx.x * 40503 + k;
+#pragma unroll 4
+        for (long long it = 0; it < iters_a; it++) {
+            long long nc[kChains];
+#pragma unroll
+            for (int k = 0; k < kChains; k++) {
+                const int a = (int)c[k];
+                asm volatile("mad.wide.s32 %0, %1, %2, %3;" : "=l"(nc[k]) : "r"(a), "r"(m), "l"(c[(k + 1) % kChains]));
+            }
+#pragma unroll
+            for (int k = 0; k < kChains; k++) c[k] = nc[k];
+        }
+        long long u = 0;
+#pragma unroll
+        for (int k = 0; k < kChains; k++) u ^= c[k];
+        t = (double)(u & 0xFFFF) - 1.0;  // -1 only if every chain's low bits end at 0
+    } else if constexpr (KIND == SSCG_PROBE_I2F64) {
+        // the bit pattern of each converted value is the next integer (a register, no instruction)
+        double d[kChains];
+#pragma unroll
+        for (int k = 0; k < kChains; k++) d[k] = seed + k;
+#pragma unroll 4
+        for (long long it = 0; it < iters_a; it++) {
+            double nd[kChains];
+#pragma unroll
+            for (int k = 0; k < kChains; k++) {
+                const long long v = __double_as_longlong(d[(k + 1) % kChains]);
+                asm volatile("cvt.rn.f64.s64 %0, %1;" : "=d"(nd[k]) : "l"(v));
+            }
+#pragma unroll
+            for (int k = 0; k < kChains; k++) d[k] = nd[k];
+        }
+#pragma unroll
+        for (int k = 0; k < kChains; k++) t += d[k];
+    } else if constexpr (KIND == SSCG_PROBE_F2I64) {
+        // the converted integer with the exponent of 2^52 set is the next FP64 value (one LOP3 on
+        // its high word): every value lies in [2^52, 2^53)
+        long long v[kChains];
+#pragma unroll
+        for (int k = 0; k < kChains; k++) v[k] = (long long)(seed * 1e15) + k;
+#pragma unroll 4
+        for (long long it = 0; it < iters_a; it++) {
+            long long nv[kChains];
+#pragma unroll
+            for (int k = 0; k < kChains; k++) {
+                const double d = __longlong_as_double(v[(k + 1) % kChains] | 0x4330000000000000ll);
+                asm volatile("cvt.rzi.s64.f64 %0, %1;" : "=l"(nv[k]) : "d"(d));
+            }
+#pragma unroll
+            for (int k = 0; k < kChains; k++) v[k] = nv[k];
+        }
+        long long u = 0;
+#pragma unroll
+        for (int k = 0; k < kChains; k++) u ^= v[k];
+        t = (double)(u & 0xFFFF) - 1.0;
     } else {
         unsigned x[kChains];
         const unsigned m = 2654435761u ^ (unsigned)seed;
@@ -187,6 +247,9 @@ extern "C" int sscg_probe_rate(sscg_ctx* ctx, int kind, int64_t iters_a, int64_t
         case SSCG_PROBE_FFMA: return run_probe<SSCG_PROBE_FFMA>(ctx, iters_a, iters_b, ops_per_s, ms);
         case SSCG_PROBE_IALU: return run_probe<SSCG_PROBE_IALU>(ctx, iters_a, iters_b, ops_per_s, ms);
         case SSCG_PROBE_IMAD: return run_probe<SSCG_PROBE_IMAD>(ctx, iters_a, iters_b, ops_per_s, ms);
+        case SSCG_PROBE_IMAD_WIDE: return run_probe<SSCG_PROBE_IMAD_WIDE>(ctx, iters_a, iters_b, ops_per_s, ms);
+        case SSCG_PROBE_I2F64: return run_probe<SSCG_PROBE_I2F64>(ctx, iters_a, iters_b, ops_per_s, ms);
+        case SSCG_PROBE_F2I64: return run_probe<SSCG_PROBE_F2I64>(ctx, iters_a, iters_b, ops_per_s, ms);
         default: return sscg::set_err(ctx, SSCG_ERR_INVALID, "unknown probe kind %d", kind);
     }
 }

@@ -472,6 +472,9 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     size_t smem_updq = 0;
     int Gq = 0;
     if (int e = update_q_setup<A, SB>(ctx, n, s, &smem_updq, &Gq)) return e;
+    // FP64 at s <= 4: P and Q as fixed-point dot products from the second step on
+    const bool fix_upd = A::kind == 0 && s + 1 <= kFixMaxTerms && !(o->flags & SSCG_FMA_UPDATE);
+    const int Gx = fix_upd ? update_fix_grid(ctx, s, n) : 0;
     const int Gt = occupancy_grid(ctx, k_true_res, smem64, n);
     k_init<A, VM><<<Gi, kThreads, smem, st>>>(M, dinv, b, x, A::kind == 0 ? nullptr : xw, r, blk[0], L.part,
                                               L.ctrl, L.hist);
@@ -514,7 +517,13 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
             if (fp.F > 0)
                 k_update_tma<A, SB><<<Gu, kUpdRows, smem_upd, st>>>(n, (int)L.ldn, s, bn, bo, xw, r, dinv, L.part,
                                                                     k == 0, 1, L.ctrl, L.hist);
-            else
+            else if constexpr (A::kind == 0) {
+                if (fix_upd && k > 0)
+                    launch_update_fix(s, Gx, n, (int)L.ldn, bn, bo, xw, diag_u, diag_c, L.part, L.ctrl, L.hist, st);
+                else
+                    k_update_q<A, SB><<<Gq, kThreads, 0, st>>>(n, (int)L.ldn, s, bn, bo, xw, diag_u, diag_c,
+                                                               L.part, k == 0, L.ctrl, L.hist);
+            } else
                 k_update_q<A, SB><<<Gq, kThreads, 0, st>>>(n, (int)L.ldn, s, bn, bo, xw, diag_u, diag_c,
                                                            L.part, k == 0, L.ctrl, L.hist);
             P.end(FAM_UPDATE, k);

@@ -40,7 +40,8 @@ EXPORTS = (
     "sscg_newton_shifts",
 )
 # Probe kinds of include/sscg_probe.h.
-PROBE = {"dfma": 0, "dadd": 1, "dmul": 2, "dmma": 3, "dfma_dmma": 4, "ffma": 5, "ialu": 6, "imad": 7}
+PROBE = {"dfma": 0, "dadd": 1, "dmul": 2, "dmma": 3, "dfma_dmma": 4, "ffma": 5, "ialu": 6, "imad": 7, "imad_wide": 8, "i2f64": 9,
+         "f2i64": 10}
 BATCH_MAX_RHS = 8
 BATCH_PERSISTENT = 0x10
 BATCH_MAX_S = 8
@@ -323,13 +324,14 @@ class Matrix:
 DIRECT_GRAM = 0x4
 FUSED_MPK = 0x8
 ADAPTIVE_S = 0x20
+FMA_UPDATE = 0x40
 
 
 def make_opts(s=4, basis="monomial", tol=1e-8, maxit=1000, arith="f64", basis_bounds=(0.0, 0.0),
               replace_every=0, host_vectors=False, profile=False, direct_gram=False, fused_mpk=False,
-              adaptive_s=False) -> Opts:
+              adaptive_s=False, fma_update=False) -> Opts:
     flags = (HOST_VECTORS if host_vectors else 0) | (PROFILE if profile else 0) | (DIRECT_GRAM if direct_gram else 0)
-    flags |= (FUSED_MPK if fused_mpk else 0) | (ADAPTIVE_S if adaptive_s else 0)
+    flags |= (FUSED_MPK if fused_mpk else 0) | (ADAPTIVE_S if adaptive_s else 0) | (FMA_UPDATE if fma_update else 0)
     return Opts(int(s), BASIS[basis], float(basis_bounds[0]), float(basis_bounds[1]), float(tol), int(maxit),
                 ARITH[arith], int(replace_every), flags)
 

@@ -1,0 +1,109 @@
+"""The FP64 block update with P and Q formed as fixed-point dot products on
+the integer multipliers (the default at s <= 4) against the FP64 FMA update
+(SSCG_FMA_UPDATE) and the FP64 oracle: the same outer-step counts (+-1),
+solutions within 1e-9 of each other and within 1e-7 of the oracle at equal
+step counts; rows whose values are all zero or below 2^-961 take the FP64 FMAs;
+block sizes above 4 are untouched by the flag."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_03743_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2501_03743_gb300 import sscg  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2501_03743_gb300 import build
+
+    build.build()
+    return sscg.Context()
+
+
+_CACHE = {}
+
+
+def system(kind, N, seed=0, sigma=0.0):
+    key = (kind, N, seed, sigma)
+    if key not in _CACHE:
+        _CACHE[key] = inputs.system(kind, N, seed=seed, sigma=sigma)
+    return _CACHE[key]
+
+
+def solve(A, b, **kw):
+    bt = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    xt = torch.zeros_like(bt)
+    res = sscg.Solver(A, **kw).solve(bt, xt)
+    return xt.cpu().numpy(), res
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+CASES = [("poisson7", 19, 0, 0.0, False), ("varcoef7", 14, 1, 1.5, False), ("poisson27", 11, 2, 0.0, False),
+         ("aniso7", 15, 3, 0.0, False), ("poisson7", 17, 4, 0.0, True)]
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 4])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_fixed_point_update_matches_fma_update_and_oracle(ctx, s, case):
+    kind, N, seed, sig, csr = CASES[case]
+    S = system(kind, N, seed, sig)
+    A = sscg.Matrix(ctx, S["rowptr"], S["col"], S["val"], csr_only=csr)
+    xf, rf = solve(A, S["b"], s=s, tol=1e-8, maxit=1000)
+    xm, rm = solve(A, S["b"], s=s, tol=1e-8, maxit=1000, fma_update=True)
+    assert rf.status == rm.status == sscg.OK
+    assert abs(rf.outer_iters - rm.outer_iters) <= 1
+    assert rf.rel_res_recursive < 1e-8 and rf.rel_res_true < 1e-7
+    if rf.outer_iters == rm.outer_iters:
+        assert rel(xf, xm) < 1e-9, rel(xf, xm)
+        hf, hm = np.array(rf.hist), np.array(rm.hist)
+        assert np.allclose(hf, hm, rtol=1e-6, atol=0)
+    same = oracle.pcgs(oracle.as_matrix(S), S["b"], s, tol=0.0, maxit=rf.outer_iters)
+    assert rel(xf, same.x) < 1e-7
+
+
+def test_fixed_point_update_runs_and_differs_in_rounding(ctx):
+    """The default s = 4 solve does not repeat the FMA update bit for bit (its
+    dot products round once, the FMA chain s times), while s = 6 (above the
+    fixed-point limit) is identical with and without the flag."""
+    S = system("poisson7", 19, 0)
+    A = sscg.Matrix(ctx, S["rowptr"], S["col"], S["val"])
+    xf, rf = solve(A, S["b"], s=4, tol=1e-10, maxit=1000)
+    xm, rm = solve(A, S["b"], s=4, tol=1e-10, maxit=1000, fma_update=True)
+    assert not np.array_equal(xf, xm) and rel(xf, xm) < 1e-9
+    x6, r6 = solve(A, S["b"], s=6, tol=1e-8, maxit=1000)
+    y6, q6 = solve(A, S["b"], s=6, tol=1e-8, maxit=1000, fma_update=True)
+    assert np.array_equal(x6, y6) and r6.outer_iters == q6.outer_iters
+
+
+def test_rows_of_zeros_and_tiny_values_take_the_fma_path(ctx):
+    """A right-hand side that is 1 on a corner block, about 1e-295 on a slab
+    and 0 elsewhere: in the first outer steps most rows of U, P and Q are all
+    zero or below 2^-961 and take the FP64 FMAs, the rest the fixed-point dot
+    products, within the same warps.  Both updates agree and match the oracle."""
+    N = 20
+    S = system("poisson7", N, 6)
+    rng = np.random.default_rng(6)
+    b = np.zeros((N, N, N))
+    b[:3, :3, :3] = rng.uniform(0.5, 1.0, (3, 3, 3))
+    b[10:13] = rng.uniform(-1, 1, (3, N, N)) * 1e-295
+    b = b.ravel()
+    A = sscg.Matrix(ctx, S["rowptr"], S["col"], S["val"])
+    xf, rf = solve(A, b, s=4, tol=1e-8, maxit=1000)
+    xm, rm = solve(A, b, s=4, tol=1e-8, maxit=1000, fma_update=True)
+    assert rf.status == rm.status == sscg.OK and abs(rf.outer_iters - rm.outer_iters) <= 1
+    if rf.outer_iters == rm.outer_iters:
+        assert rel(xf, xm) < 1e-9
+    ref = oracle.pcgs(oracle.as_matrix(S), b, 4, tol=1e-8, maxit=1000)
+    assert ref.status == oracle.OK and abs(rf.outer_iters - ref.iters) <= 1
+    same = oracle.pcgs(oracle.as_matrix(S), b, 4, tol=0.0, maxit=rf.outer_iters)
+    assert rel(xf, same.x) < 1e-7
