@@ -108,12 +108,14 @@ def parse():
 # for this workload's kernels (7-point stencil in the diagonal form, s = 4,
 # sequential levels) at n = 4,096,000: a level (mean of the captured
 # launches; at that size L2 still holds most of the level's writes when it
-# ends) and the block update, per arithmetic (profiles/
-# k_level_k_update_q_poisson7_160_f64_s4.txt, k_level_dia_k_update_q_poisson7_160_df64_s4.txt).
+# ends) and the block update, per arithmetic and update kernel (profiles/
+# k_update_fix_k_level_poisson7_160_f64_s4.txt, k_level_k_update_q_poisson7_160_f64_s4.txt,
+# k_level_dia_k_update_q_poisson7_160_df64_s4.txt).
 # The roofline's "traffic" scales them to the workload's n; it is null for any
 # other configuration.
 NCU_TRAFFIC_PER_ROW = {
-    "f64": {"mpk": 54.2e6 / 4.096e6, "update": 734.1e6 / 4.096e6},
+    "f64": {"mpk": 54.50e6 / 4.096e6, "update": 734.1e6 / 4.096e6},
+    "f64-fixed": {"update": 733.44e6 / 4.096e6},
     "df64": {"mpk": 54.0e6 / 4.096e6, "update": 732.694e6 / 4.096e6},
 }
 
@@ -458,7 +460,7 @@ def main():
                                    "the probe of include/sscg_probe.h measures 529 Gop/s"}
         else:
             head = {"bound": "hbm", "achieved": gbs[dom], "peak": hbm, "unit": "GB/s", "frac": round(hbm_frac, 4),
-                    "peak_source": f"measured copy bandwidth ({hbm_src})"}
+                    "peak_source": hbm_src}
         roofline = {**head, "traffic": traffic(a, dom, n, dia, fixed),
                     "kernel": kernel_names[dom],
                     "ops_per_row": {"level": round(ops["level_avg"], 2), "update": ops["update"]},
