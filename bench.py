@@ -683,7 +683,7 @@ def run_batch(a, world, rank, local, pg):
     X = [torch.zeros_like(b) for b in B]
     t0 = time.perf_counter()
     plan = sscg.BatchSolver(mats, R, s=a.s, tol=a.tol, maxit=5000, arith=a.arith, tune=not a.no_tune,
-                            persistent=a.persistent)
+                            persistent=a.persistent, fma_update=a.fma_update)
     t_plan = time.perf_counter() - t0
     props = plan.props()
 

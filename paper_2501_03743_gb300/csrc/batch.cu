@@ -152,6 +152,7 @@ struct BArgs {
     Ctrl* rc;  // one per right-hand side
     int skip_cta;             // fault injection: this CTA skips its first barrier arrival (-1: none)
     unsigned long long wait_ns;  // limit of every barrier wait
+    int fma_update;           // FP64 at s <= 4: P and Q by FP64 FMAs instead of fixed-point dot products
 };
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
@@ -680,6 +681,13 @@ __device__ void ph_update(const BArgs& a, int it0, int itstep) {
     __shared__ Rv s_alpha[kMaxR][kMaxSB];
     __shared__ Rv s_beta[kMaxR][kMaxSB * kMaxSB];
     __shared__ int s_act[kMaxR];
+    // FP64 with s = SB <= 4: P and Q as fixed-point dot products (fixsum.cuh),
+    // each right-hand side's coefficient columns aligned once per item
+    constexpr bool kFix = A::kind == 0 && SB + 1 <= kFixMaxTerms;
+    constexpr int FS = kFix ? SB : 1;
+    __shared__ FixLimbs s_cf[kMaxR][FS][FS + 1];
+    __shared__ int s_fc[kMaxR][FS];
+    __shared__ int s_rng[kMaxR][2];
     const int s = a.s;
     for (int it = it0; it < a.nitems; it += itstep) {
         const int k = __ldg(a.item_sys + it);
@@ -710,6 +718,19 @@ __device__ void ph_update(const BArgs& a, int it0, int itstep) {
             else s_act[rq] = __ldcg(&c->done) ? 0 : 1;
         }
         __syncthreads();
+        bool fixp = false;  // the same for every thread of the item
+        if constexpr (kFix) {
+            fixp = s == SB && kk > 0 && !a.fma_update;
+            if (fixp) {
+                for (int e = threadIdx.x; e < R * SB; e += kBThreads) {
+                    const int rq = e / SB, j = e % SB;
+                    s_fc[rq][j] = fix_coef_column<SB>(&s_beta[rq][0], j, s_cf[rq][j]);
+                }
+                __syncthreads();
+                if (threadIdx.x < R) fix_row_range<SB>(s_fc[threadIdx.x], &s_rng[threadIdx.x][0], &s_rng[threadIdx.x][1]);
+                __syncthreads();
+            }
+        }
         // z / Q form (Algorithm 3 multiplied by D^-1, as the single-system
         // path): P_j = U_j + sum P_old beta, Q_j = U_{j+1} + sum Q_old beta,
         // x += P alpha, z -= Q alpha; the next z goes to column 0 of the old block
@@ -725,6 +746,44 @@ __device__ void ph_update(const BArgs& a, int it0, int itstep) {
             if (!act) {
                 A::st(ob + o, A::ldcg(nb + o));  // frozen: carry z to the next step
                 continue;
+            }
+            if constexpr (kFix) {
+                if (fixp) {  // s == SB: the halves P (with x) and Q (with z) in fixed point
+                    double u[SB + 1], po[SB], qo[SB], v[SB], pq[SB];
+#pragma unroll
+                    for (int c = 0; c <= SB; c++) u[c] = __ldcg(nb + c * nR + o);
+#pragma unroll
+                    for (int l = 0; l < SB; l++) {
+                        po[l] = __ldcg(ob + l * nR + o);
+                        qo[l] = __ldcg(ob + (SB + 1 + l) * nR + o);
+                    }
+                    double x = __ldcg(xw + o), za = 0.0;
+#pragma unroll
+                    for (int j = 0; j < SB; j++) v[j] = u[j];
+                    if (!fix_update_group<SB>(v, po, s_cf[r], s_fc[r], s_rng[r][0], s_rng[r][1], pq))
+                        fma_update_group<SB>(v, po, &s_beta[r][0], pq);
+#pragma unroll
+                    for (int j = 0; j < SB; j++) {
+                        __stcs(nb + j * nR + o, pq[j]);
+                        x = ::fma(pq[j], s_alpha[r][j], x);
+                    }
+#pragma unroll
+                    for (int j = 0; j < SB; j++) v[j] = u[j + 1];
+                    if (!fix_update_group<SB>(v, qo, s_cf[r], s_fc[r], s_rng[r][0], s_rng[r][1], pq))
+                        fma_update_group<SB>(v, qo, &s_beta[r][0], pq);
+#pragma unroll
+                    for (int j = 0; j < SB; j++) {
+                        __stcs(nb + (SB + 1 + j) * nR + o, pq[j]);
+                        za = ::fma(pq[j], s_alpha[r][j], za);
+                    }
+                    const double z = u[0] - za;
+                    xw[o] = x;
+                    ob[o] = z;
+                    const double rn = (yb.diag ? __ldg(reinterpret_cast<const double*>(yb.diag) + i) : yb.diag_c) * z;
+                    rr = ::fma(rn, rn, rr);
+                    rz = ::fma(rn, z, rz);
+                    continue;
+                }
             }
             Rv u[SB + 1], po[SB], qo[SB];
 #pragma unroll
@@ -842,6 +901,7 @@ struct sscg_batch {
     sscg_ctx* ctx;
     int nsys, s, arith, maxit, total_rhs, nitems, grid, graph_ok;
     int persistent;              // one cooperative launch instead of per-phase launches
+    int fma_update;              // SSCG_FMA_UPDATE
     int g_init, g_level, g_level_dia, g_update;  // per-phase grids (CSR and diagonal-form levels)
     int has_csr, has_dia;                        // which level kernels an outer step launches
     cudaGraphExec_t step_exec;   // per-phase mode: one outer step
@@ -980,6 +1040,7 @@ BArgs make_args(const sscg_batch* b, int tuning, int maxit) {
     a.rc = b->d_rc;
     a.skip_cta = b->fault_cta;
     a.wait_ns = b->fault_cta >= 0 ? b->fault_wait_ns : kBarrierTimeoutNs;
+    a.fma_update = b->fma_update;
     return a;
 }
 
@@ -1349,6 +1410,7 @@ int sscg_batch_create(sscg_ctx* ctx, int nsys, const sscg_mat* const* mats, cons
         return rc;
     };
     b->persistent = (opts->flags & SSCG_BATCH_PERSISTENT) ? 1 : 0;
+    b->fma_update = (opts->flags & SSCG_FMA_UPDATE) ? 1 : 0;
     if (int rc = setup_grids(b)) return fail(rc);
     if (cudaMallocHost((void**)&b->h_io, sizeof(double*) * 2 * nsys) != cudaSuccess ||
         cudaMallocHost((void**)&b->h_rc, sizeof(Ctrl) * rhs) != cudaSuccess ||

@@ -232,4 +232,84 @@ SSCG_HD bool fix_dot_result(const FixAcc& s, int E, int Fc, uint64_t* out) {
 
 
 
+#if defined(__CUDACC__)
+// Column j of the block update's coefficients [1; beta_0j .. beta_{S-1}j]
+// (beta column-major, leading dimension S): returns its exponent (at least
+// 1023, the exponent of the 1; 0x7FF when a coefficient is not finite) and
+// stores its aligned coefficients in out.
+template <int S>
+__device__ __forceinline__ int fix_coef_column(const double* beta, int j, FixLimbs (&out)[S + 1]) {
+    int Fc = 1023;
+    for (int l = 0; l < S; l++) Fc = max_i(Fc, fix_exp((uint64_t)__double_as_longlong(beta[l + j * S])));
+    out[0] = fix_coef((uint64_t)__double_as_longlong(1.0), Fc);
+    for (int l = 0; l < S; l++)
+        out[1 + l] = Fc < 0x7FF ? fix_coef((uint64_t)__double_as_longlong(beta[l + j * S]), Fc) : FixLimbs{0, 0};
+    return Fc;
+}
+
+// The row exponents [*Elo, *Ehi] that take the fixed point with column
+// exponents fc: every result offset e0 = E + Fc - 1027 in [53, 2035]
+// (fix_pack_cvt) and E >= 62 (fix_align); an empty range when a coefficient
+// is not finite.
+template <int S>
+__device__ __forceinline__ void fix_row_range(const int (&fc)[S], int* Elo, int* Ehi) {
+    int fcmin = 0x7FF, fcmax = 0;
+#pragma unroll
+    for (int j = 0; j < S; j++) {
+        fcmin = fcmin < fc[j] ? fcmin : fc[j];
+        fcmax = max_i(fcmax, fc[j]);
+    }
+    *Elo = max_i(62, 53 - fix_dot_e0(0, fcmin));
+    const int hi = 2035 - fix_dot_e0(0, fcmax);
+    *Ehi = fcmax == 0x7FF ? -1 : (hi < 0x7FE ? hi : 0x7FE);
+}
+
+// One half of the fixed-point block update: out_j = v_j + sum_l w_l beta_lj
+// (j < S) for one row's values v_0..v_{S-1} and w_0..w_{S-1}, all aligned to
+// their largest exponent E (fixsum.cuh), the coefficient column j of [1; beta]
+// in scf[j] with exponent fc[j].  Returns false, out untouched, when E lies
+// outside [Elo, Ehi].
+template <int S>
+__device__ __forceinline__ bool fix_update_group(const double (&v)[S], const double (&w)[S],
+                                                 const FixLimbs (&scf)[S][S + 1], const int (&fc)[S], int Elo,
+                                                 int Ehi, double (&out)[S]) {
+    unsigned hmax = 0;  // the largest exponent field (sign cleared, as an integer)
+#pragma unroll
+    for (int l = 0; l < S; l++)
+        hmax = max(hmax, max((unsigned)__double2hiint(v[l]) & 0x7FF00000u,
+                             (unsigned)__double2hiint(w[l]) & 0x7FF00000u));
+    const int E = (int)(hmax >> 20);
+    if (E < Elo || E > Ehi) return false;
+    FixLimbs av[S], aw[S];
+#pragma unroll
+    for (int l = 0; l < S; l++) {
+        av[l] = fix_align((uint64_t)__double_as_longlong(v[l]), E);
+        aw[l] = fix_align((uint64_t)__double_as_longlong(w[l]), E);
+    }
+#pragma unroll
+    for (int j = 0; j < S; j++) {
+        FixAcc acc;
+        fix_mad(acc, av[j], scf[j][0]);
+#pragma unroll
+        for (int l = 0; l < S; l++) fix_mad(acc, aw[l], scf[j][1 + l]);
+        out[j] = fix_pack_cvt(fix_total(acc), fix_dot_e0(E, fc[j]));
+    }
+    return true;
+}
+
+// The same half with FP64 FMAs, in k_update_q's order.
+template <int S>
+__device__ __forceinline__ void fma_update_group(const double (&v)[S], const double (&w)[S], const double* sb,
+                                                 double (&out)[S]) {
+#pragma unroll
+    for (int j = 0; j < S; j++) {
+        double t = v[j];
+#pragma unroll
+        for (int l = 0; l < S; l++) t = ::fma(w[l], sb[l + j * S], t);
+        out[j] = t;
+    }
+}
+
+#endif
+
 }  // namespace sscg

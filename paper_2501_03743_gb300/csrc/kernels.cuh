@@ -510,52 +510,6 @@ __global__ void __launch_bounds__(kThreads) k_update_q(int n, int ldn, int s, ty
     update_q_finish<A>(rr, rz, diag != nullptr, diag_c, red, part, ctrl, hist);
 }
 
-// One half of the fixed-point block update: out_j = v_j + sum_l w_l beta_lj
-// (j < S) for one row's values v_0..v_{S-1} and w_0..w_{S-1}, all aligned to
-// their largest exponent E (fixsum.cuh), the coefficient column j of [1; beta]
-// in scf[j] with exponent fc[j].  Returns false, out untouched, when E lies
-// outside [Elo, Ehi].
-template <int S>
-__device__ __forceinline__ bool fix_update_group(const double (&v)[S], const double (&w)[S],
-                                                 const FixLimbs (&scf)[S][S + 1], const int (&fc)[S], int Elo,
-                                                 int Ehi, double (&out)[S]) {
-    unsigned hmax = 0;  // the largest exponent field (sign cleared, as an integer)
-#pragma unroll
-    for (int l = 0; l < S; l++)
-        hmax = max(hmax, max((unsigned)__double2hiint(v[l]) & 0x7FF00000u,
-                             (unsigned)__double2hiint(w[l]) & 0x7FF00000u));
-    const int E = (int)(hmax >> 20);
-    if (E < Elo || E > Ehi) return false;
-    FixLimbs av[S], aw[S];
-#pragma unroll
-    for (int l = 0; l < S; l++) {
-        av[l] = fix_align((uint64_t)__double_as_longlong(v[l]), E);
-        aw[l] = fix_align((uint64_t)__double_as_longlong(w[l]), E);
-    }
-#pragma unroll
-    for (int j = 0; j < S; j++) {
-        FixAcc acc;
-        fix_mad(acc, av[j], scf[j][0]);
-#pragma unroll
-        for (int l = 0; l < S; l++) fix_mad(acc, aw[l], scf[j][1 + l]);
-        out[j] = fix_pack_cvt(fix_total(acc), fix_dot_e0(E, fc[j]));
-    }
-    return true;
-}
-
-// The same half with FP64 FMAs, in k_update_q's order.
-template <int S>
-__device__ __forceinline__ void fma_update_group(const double (&v)[S], const double (&w)[S], const double* sb,
-                                                 double (&out)[S]) {
-#pragma unroll
-    for (int j = 0; j < S; j++) {
-        double t = v[j];
-#pragma unroll
-        for (int l = 0; l < S; l++) t = ::fma(w[l], sb[l + j * S], t);
-        out[j] = t;
-    }
-}
-
 // The FP64 block update of k_update_q with P and Q formed as fixed-point dot
 // products on the integer multipliers (fixsum.cuh), for block sizes S <= 4:
 //   P_j = U_j + sum_l P_old_l beta_lj,   Q_j = U_{j+1} + sum_l Q_old_l beta_lj
@@ -589,29 +543,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_update_fix(int n, int ldn, doub
         sna[e] = -ctrl->alpha[e];
     }
     __syncthreads();
-    if (threadIdx.x < S) {  // column j of [1; beta]: its exponent and aligned coefficients
-        const int j = threadIdx.x;
-        int Fc = 1023;  // the coefficient 1 of U_j
-        for (int l = 0; l < S; l++) Fc = max(Fc, fix_exp((uint64_t)__double_as_longlong(sb[l + j * S])));
-        sfc[j] = Fc;
-        scf[j][0] = fix_coef((uint64_t)__double_as_longlong(1.0), Fc);
-        for (int l = 0; l < S; l++)
-            scf[j][1 + l] = Fc < 0x7FF ? fix_coef((uint64_t)__double_as_longlong(sb[l + j * S]), Fc) : FixLimbs{0, 0};
-    }
+    if (threadIdx.x < S) sfc[threadIdx.x] = fix_coef_column<S>(sb, threadIdx.x, scf[threadIdx.x]);
     __syncthreads();
-    // rows whose exponent E puts every column's result offset e0 = E + Fc - 1027
-    // in [53, 2035] (fix_pack_cvt) and E >= 62 (fix_align) take the fixed point
-    // (none when a coefficient is not finite: its column exponent is 0x7FF)
     int fc[S];
-    int fcmin = 0x7FF, fcmax = 0;
 #pragma unroll
-    for (int j = 0; j < S; j++) {
-        fc[j] = sfc[j];
-        fcmin = min(fcmin, fc[j]);
-        fcmax = max(fcmax, fc[j]);
-    }
-    const int Elo = max(62, 53 - fix_dot_e0(0, fcmin));
-    const int Ehi = fcmax == 0x7FF ? -1 : min(0x7FE, 2035 - fix_dot_e0(0, fcmax));
+    for (int j = 0; j < S; j++) fc[j] = sfc[j];
+    int Elo, Ehi;  // the rows that take the fixed point
+    fix_row_range<S>(fc, &Elo, &Ehi);
     const size_t ld = (size_t)ldn;
     double rr = 0.0, rz = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {

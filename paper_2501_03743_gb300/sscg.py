@@ -394,7 +394,8 @@ class BatchSolver:
     """Plan for solving many systems (each with 1..8 right-hand sides) in one
     persistent launch; see sscg_batch_create."""
 
-    def __init__(self, mats, nrhs, s=4, tol=1e-8, maxit=1000, arith="f64", tune=False, persistent=False):
+    def __init__(self, mats, nrhs, s=4, tol=1e-8, maxit=1000, arith="f64", tune=False, persistent=False,
+                 fma_update=False):
         torch = _torch()
         self.mats = list(mats)
         self.nrhs = [int(r) for r in nrhs]
@@ -407,6 +408,8 @@ class BatchSolver:
         self.opts = make_opts(s=s, tol=tol, maxit=maxit, arith=arith)
         if persistent:
             self.opts.flags |= BATCH_PERSISTENT
+        if fma_update:
+            self.opts.flags |= FMA_UPDATE
         nbytes = C.c_size_t()
         rc = lib.sscg_batch_workspace_bytes(k, self._mh, self._nr, C.byref(self.opts), C.byref(nbytes))
         if rc != OK:
