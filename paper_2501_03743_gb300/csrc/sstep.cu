@@ -13,7 +13,10 @@
 //   1 x k_update_q : the block updates P = U + P_old beta, Q = U_{2..s+1} +
 //                    Q_old beta, x += P alpha, z -= Q alpha in one pass, with
 //                    ||r||^2 and mu_0 = r . z of the new residual; its last CTA
-//                    tests convergence.
+//                    tests convergence.  In FP64 at s <= 4 every step after the
+//                    first runs k_update_fix instead: the same update with P
+//                    and Q formed as fixed-point dot products on the integer
+//                    multipliers (fixsum.cuh).
 // A block holds 2s+1 columns (U_1..U_{s+1} | Q); the two blocks (the P1, P2 of
 // Algorithm 3) alternate between "new" and "old" with the step parity.  With
 // SSCG_FUSED_MPK the levels run in the fused kernel below instead and the
