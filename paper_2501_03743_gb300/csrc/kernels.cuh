@@ -515,13 +515,13 @@ __global__ void __launch_bounds__(kThreads) k_update_q(int n, int ldn, int s, ty
 //   P_j = U_j + sum_l P_old_l beta_lj,   Q_j = U_{j+1} + sum_l Q_old_l beta_lj
 // take 3 (S + 1) 32 x 32 -> 64-bit multiply-adds each in place of S FP64 FMAs
 // (a GB300 retires about 53 of those per SM and clock against 2 FP64
-// operations).  A row's values U_1..U_S and P_old share one alignment
-// exponent, U_2..U_{S+1} and Q_old another; each column j of the coefficients
-// [1; beta_0j .. beta_{S-1}j] has its own.  x += P alpha and z -= Q alpha stay
-// FP64 FMAs on the rounded P and Q, as in k_update_q.  A half row (P or Q)
-// holding a NaN, an infinity or only values below 2^-961, or whose entries
-// could leave the normal range, takes the FP64 FMAs of k_update_q; so does
-// every row when a coefficient is not finite.  Not for the first step (no
+// operations).  A row's values U_1..U_{S+1}, P_old and Q_old share one
+// alignment exponent; each column j of the coefficients [1; beta_0j ..
+// beta_{S-1}j] has its own.  x += P alpha and z -= Q alpha stay
+// FP64 FMAs on the rounded P and Q, as in k_update_q.  A row holding a NaN,
+// an infinity or only values below 2^-961, or whose entries could leave the
+// normal range, takes the FP64 FMAs of k_update_q; so does every row when a
+// coefficient is not finite.  Not for the first step (no
 // P_old, Q_old).
 template <int S>
 __global__ void __launch_bounds__(kThreads, 2) k_update_fix(int n, int ldn, double* __restrict__ blk_new,
@@ -562,24 +562,54 @@ __global__ void __launch_bounds__(kThreads, 2) k_update_fix(int n, int ldn, doub
             qo[l] = __ldcg(blk_old + (S + 1 + l) * ld + i);
         }
         double xn = __ldcg(x + i), zn = u[0];
-        double v[S], p[S];
-        // P_j = U_j + sum_l P_old_l beta_lj
+        // the row exponent E: the largest exponent field of its values (sign
+        // cleared, as an integer), shared by the P and Q columns
+        double p[S], q[S];
+        unsigned hmax = 0;
 #pragma unroll
-        for (int j = 0; j < S; j++) v[j] = u[j];
-        if (!fix_update_group<S>(v, po, scf, fc, Elo, Ehi, p)) fma_update_group<S>(v, po, sb, p);
+        for (int c = 0; c <= S; c++) hmax = max(hmax, (unsigned)__double2hiint(u[c]) & 0x7FF00000u);
+#pragma unroll
+        for (int l = 0; l < S; l++)
+            hmax = max(hmax, max((unsigned)__double2hiint(po[l]) & 0x7FF00000u,
+                                 (unsigned)__double2hiint(qo[l]) & 0x7FF00000u));
+        const int E = (int)(hmax >> 20);
+        if (E >= Elo && E <= Ehi) {
+            FixLimbs au[S + 1], ap[S], aq[S];
+#pragma unroll
+            for (int c = 0; c <= S; c++) au[c] = fix_align((uint64_t)__double_as_longlong(u[c]), E);
+#pragma unroll
+            for (int l = 0; l < S; l++) {
+                ap[l] = fix_align((uint64_t)__double_as_longlong(po[l]), E);
+                aq[l] = fix_align((uint64_t)__double_as_longlong(qo[l]), E);
+            }
+#pragma unroll
+            for (int j = 0; j < S; j++) {
+                FixAcc a1, a2;
+                fix_mad(a1, au[j], scf[j][0]);
+                fix_mad(a2, au[j + 1], scf[j][0]);
+#pragma unroll
+                for (int l = 0; l < S; l++) {
+                    fix_mad(a1, ap[l], scf[j][1 + l]);
+                    fix_mad(a2, aq[l], scf[j][1 + l]);
+                }
+                p[j] = fix_pack_cvt(fix_total(a1), fix_dot_e0(E, fc[j]));
+                q[j] = fix_pack_cvt(fix_total(a2), fix_dot_e0(E, fc[j]));
+            }
+        } else {  // FP64 FMAs, as k_update_q
+            double v[S];
+#pragma unroll
+            for (int j = 0; j < S; j++) v[j] = u[j];
+            fma_update_group<S>(v, po, sb, p);
+#pragma unroll
+            for (int j = 0; j < S; j++) v[j] = u[j + 1];
+            fma_update_group<S>(v, qo, sb, q);
+        }
 #pragma unroll
         for (int j = 0; j < S; j++) {
             __stcs(blk_new + j * ld + i, p[j]);
             xn = ::fma(p[j], sa[j], xn);
-        }
-        // Q_j = U_{j+1} + sum_l Q_old_l beta_lj
-#pragma unroll
-        for (int j = 0; j < S; j++) v[j] = u[j + 1];
-        if (!fix_update_group<S>(v, qo, scf, fc, Elo, Ehi, p)) fma_update_group<S>(v, qo, sb, p);
-#pragma unroll
-        for (int j = 0; j < S; j++) {
-            __stcs(blk_new + (S + 1 + j) * ld + i, p[j]);
-            zn = ::fma(p[j], sna[j], zn);
+            __stcs(blk_new + (S + 1 + j) * ld + i, q[j]);
+            zn = ::fma(q[j], sna[j], zn);
         }
         x[i] = xn;
         blk_old[i] = zn;  // U_1 of the next step (P_old_1 already read)
