@@ -442,11 +442,12 @@ __device__ __forceinline__ void spmv_dia_df(const MatView& M, const TX* __restri
 }
 
 // Minimum resident CTAs per SM the diagonal-form kernels are built for: 6
-// (40 registers a thread), except the FP64 27-point form, whose 26 neighbour
-// terms the fixed-point sum holds at once (2 CTAs, 128 registers).
+// (40 registers a thread), except the FP64 forms: the 7-point one gathers two
+// rows at a time (4 CTAs, 64 registers), the 27-point one's fixed-point sum
+// holds 26 neighbour terms at once (2 CTAs, 128 registers).
 template <class A, int DM>
 __host__ __device__ constexpr int dia_min_blocks() {
-    return (A::kind == 0 && DM == 27) ? 2 : (DM >= 2 ? 6 : 1);
+    return (A::kind == 0 && DM == 27) ? 2 : (A::kind == 0 && DM == 7) ? 4 : (DM >= 2 ? 6 : 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -466,16 +467,23 @@ __host__ __device__ constexpr int dia_min_blocks() {
 // carve such margins).  epi(i, S, x_i) runs once per row, rows grid-stride.
 // Sum of the off-centre terms (mask bit t set) of a Laplacian-class row with K
 // offsets, offset 0 at index K/2; ld(t) loads the term of offset t as a double.
+// The masked neighbours of a Laplacian-class row with K offsets (offset 0 at
+// index K/2) as FP64 bit patterns, a term whose mask bit is clear as 0;
+// ld(t) loads the term of offset t.
 template <int K, class LD>
-__device__ __forceinline__ double lap_neighbour_sum(uint32_t m, LD ld) {
+__device__ __forceinline__ void lap_gather(uint32_t m, LD ld, uint64_t (&w)[K - 1]) {
     constexpr int C = K / 2;
-    uint64_t w[K - 1];
 #pragma unroll
     for (int t = 0; t < K; t++) {
         if (t == C) continue;
         const double v = ld(t);
         w[t < C ? t : t - 1] = ((m >> t) & 1u) ? (uint64_t)__double_as_longlong(v) : 0ull;
     }
+}
+
+// Their sum: fixed point, or FP64 additions for a row fixsum declines.
+template <int K>
+__device__ __forceinline__ double lap_sum(const uint64_t (&w)[K - 1]) {
     uint64_t sb;
     if (fixsum<K - 1>(w, &sb)) return __longlong_as_double((long long)sb);
     double d[K - 1];  // the rare row the fixed-point path declines: a pairwise tree of FP64 additions
@@ -489,14 +497,43 @@ __device__ __forceinline__ double lap_neighbour_sum(uint32_t m, LD ld) {
     return d[0];
 }
 
+// Sum of the off-centre terms (mask bit t set) of a Laplacian-class row with K
+// offsets, offset 0 at index K/2; ld(t) loads the term of offset t as a double.
+template <int K, class LD>
+__device__ __forceinline__ double lap_neighbour_sum(uint32_t m, LD ld) {
+    uint64_t w[K - 1];
+    lap_gather<K>(m, ld, w);
+    return lap_sum<K>(w);
+}
+
+// For the 7-point pattern rows go two at a time per thread (i and i + the
+// grid's threads), both rows' loads issued before either row's arithmetic;
+// larger patterns take one row at a time.
 template <int K, class EPI>
 __device__ __forceinline__ void spmv_dia_lap_f64(const MatView& M, const double* __restrict__ x, EPI epi) {
-    constexpr int C = K / 2;  // symmetric pattern: offset 0 sits in the middle
     const int n = M.n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t m = __ldg(M.dmask + i);
-        const double S = lap_neighbour_sum<K>(m, [&](int t) { return __ldg(x + (i + M.doff[t])); });
-        epi(i, S, __ldg(x + i));
+    const int stride = gridDim.x * blockDim.x;
+    if constexpr (K > 7) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+            const uint32_t m = __ldg(M.dmask + i);
+            const double S = lap_neighbour_sum<K>(m, [&](int t) { return __ldg(x + (i + M.doff[t])); });
+            epi(i, S, __ldg(x + i));
+        }
+        return;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+        const int i2 = i + stride;
+        const bool two = i2 < n;
+        const int j2 = two ? i2 : i;  // a row that exists, for the second gather
+        const uint32_t m1 = __ldg(M.dmask + i), m2 = two ? __ldg(M.dmask + j2) : 0u;
+        uint64_t w1[K - 1], w2[K - 1];
+        lap_gather<K>(m1, [&](int t) { return __ldg(x + (i + M.doff[t])); }, w1);
+        lap_gather<K>(m2, [&](int t) { return __ldg(x + (j2 + M.doff[t])); }, w2);
+        const double x1 = __ldg(x + i), x2 = __ldg(x + j2);
+        const double S1 = lap_sum<K>(w1);
+        const double S2 = lap_sum<K>(w2);
+        epi(i, S1, x1);
+        if (two) epi(i2, S2, x2);
     }
 }
 
