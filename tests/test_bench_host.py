@@ -78,6 +78,24 @@ def test_fp64_operation_model():
     assert ops["update"] == 2 * 16 + 2 * 4 + 1 and ops["update_first"] == 9
     assert (ops["pcg_spmv"], ops["pcg_update"], ops["pcg_dir"]) == (2, 3, 2)
     assert bench.fp64_ops_model(2, K=27)["level"] == [3, 2]
+    # the fixed-point update: P and Q on the integer units, x and z FMAs and sum z^2 left
+    assert bench.fp64_ops_model(4, fixed_update=True)["update"] == 2 * 4 + 1
+
+
+def test_fixed_update_is_used_where_the_library_uses_it():
+    import argparse
+
+    def args(**kw):
+        d = dict(arith="f64", s=4, fma_update=False, fused_mpk=False)
+        d.update(kw)
+        return argparse.Namespace(**d)
+
+    assert bench.fixed_update_used(args())
+    assert bench.fixed_update_used(args(s=1))
+    assert not bench.fixed_update_used(args(s=6))  # the 64-bit sums hold s + 1 <= 5 terms
+    assert not bench.fixed_update_used(args(arith="df64"))
+    assert not bench.fixed_update_used(args(fma_update=True))
+    assert not bench.fixed_update_used(args(fused_mpk=True))
 
 
 def test_fp64_alu_peak_is_two_per_clock_per_sm():
