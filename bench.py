@@ -114,8 +114,8 @@ def parse():
 # The roofline's "traffic" scales them to the workload's n; it is null for any
 # other configuration.
 NCU_TRAFFIC_PER_ROW = {
-    "f64": {"mpk": 54.50e6 / 4.096e6, "update": 734.1e6 / 4.096e6},
-    "f64-fixed": {"update": 733.44e6 / 4.096e6},
+    "f64": {"mpk": 53.79e6 / 4.096e6, "update": 734.1e6 / 4.096e6},
+    "f64-fixed": {"update": 733.84e6 / 4.096e6},
     "df64": {"mpk": 54.0e6 / 4.096e6, "update": 732.694e6 / 4.096e6},
 }
 
