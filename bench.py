@@ -331,8 +331,8 @@ def fp64_ops_model(s, K=7, fixed_update=False):
 
 
 def fixed_update_used(a):
-    """The FP64 block update forms P and Q in fixed point at s <= 4 (csrc/kernels.cuh k_update_fix)."""
-    return a.arith == "f64" and a.s <= 4 and not a.fma_update and not a.fused_mpk
+    """The FP64 block update forms P and Q in fixed point at s <= 6 (csrc/kernels.cuh k_update_fix)."""
+    return a.arith == "f64" and a.s <= 6 and not a.fma_update and not a.fused_mpk
 
 
 def alu_peak(sm_count, mhz=2070.0):

@@ -67,7 +67,7 @@ typedef enum {
  * stores every value in FP64.  Where a GB300's scarce FP64 units would bound
  * a kernel, short sums and dot products run in 64-bit fixed point on the
  * integer units and are rounded once to FP64: the neighbour sums of stencil
- * rows, and with the monomial basis at s <= 4 the block update's P and Q
+ * rows, and with the monomial basis at s <= 6 the block update's P and Q
  * columns (P_j = U_j + sum_l P_old_l beta_lj; the row's values and the
  * column's coefficients aligned to their largest exponents with 8 guard bits:
  * error at most (1 + 7K/16) 2^-56 max|value| max|coefficient| for K terms,
@@ -88,7 +88,7 @@ typedef enum { SSCG_ARITH_F64 = 0, SSCG_ARITH_DF64 = 1, SSCG_ARITH_MIXED = 2 } s
 #define SSCG_DIRECT_GRAM 0x4u  /* form the Gram blocks directly even for the monomial basis */
 #define SSCG_FUSED_MPK 0x8u    /* several matrix-powers levels per launch, intermediate levels kept in L2 */
 #define SSCG_ADAPTIVE_S 0x20u  /* after a breakdown restart from the last good iterate with s halved */
-#define SSCG_FMA_UPDATE 0x40u  /* F64, s <= 4: form the block update's P and Q with FP64 FMAs, not fixed point */
+#define SSCG_FMA_UPDATE 0x40u  /* F64, s <= 6: form the block update's P and Q with FP64 FMAs, not fixed point */
 #define SSCG_HOST_ARRAYS 0x1u  /* CSR arrays are host pointers (sscg_mat_create_csr) */
 #define SSCG_MAT_CSR_ONLY 0x2u /* keep CSR kernels even for a constant-coefficient diagonal pattern */
 

@@ -152,7 +152,7 @@ struct BArgs {
     Ctrl* rc;  // one per right-hand side
     int skip_cta;             // fault injection: this CTA skips its first barrier arrival (-1: none)
     unsigned long long wait_ns;  // limit of every barrier wait
-    int fma_update;           // FP64 at s <= 4: P and Q by FP64 FMAs instead of fixed-point dot products
+    int fma_update;           // FP64 at s = 4: P and Q by FP64 FMAs instead of fixed-point dot products
 };
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {

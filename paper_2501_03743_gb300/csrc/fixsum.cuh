@@ -146,8 +146,9 @@ SSCG_HD bool fixsum(const uint64_t (&t)[K], uint64_t* out) {
 //   hh = sum a_h C_h,  ma = sum a_h C_l,  mc = sum a_l C_h   (all exact)
 //   R  = hh + round(ma / 2^32) + round(mc / 2^32)
 // (the a_l C_l products, below 2^62, are dropped); R 2^(E + Fc - 2102)
-// approximates the dot product and is rounded once to FP64.  For K <= 5
-// terms every sum stays below 2^63 (|a_h|, |C_h| <= 2^29).  Error: the
+// approximates the dot product and is rounded once to FP64.  For K <= 7
+// terms every sum stays below 2^63 (|a_h|, |C_h| <= 2^29 and |a_l|, |C_l| <=
+// 2^31: each mid product below 2^60, seven of them below 2^62.9).  Error: the
 // dropped products and the two roundings, at most (1 + K/4) 2^64 units of
 // a C, and the truncation of a and the rounding of C, below K (2^61 + 2^60)
 // units; in all at most (1 + 7K/16) 2^(E + Fc - 2102), that is
@@ -156,7 +157,7 @@ SSCG_HD bool fixsum(const uint64_t (&t)[K], uint64_t* out) {
 // multiply-adds is bounded by (K - 1) 2^-53 sum |v c|: on vectors of similar
 // magnitude the fixed-point error is the smaller of the two.
 constexpr int kFixGuard = 8;
-constexpr int kFixMaxTerms = 5;
+constexpr int kFixMaxTerms = 7;
 
 struct FixLimbs {
     int32_t h, l;  // value h 2^32 + l

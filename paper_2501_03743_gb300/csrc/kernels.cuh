@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(kThreads) k_update_q(int n, int ldn, int s, ty
 }
 
 // The FP64 block update of k_update_q with P and Q formed as fixed-point dot
-// products on the integer multipliers (fixsum.cuh), for block sizes S <= 4:
+// products on the integer multipliers (fixsum.cuh), for block sizes S <= 6:
 //   P_j = U_j + sum_l P_old_l beta_lj,   Q_j = U_{j+1} + sum_l Q_old_l beta_lj
 // take 3 (S + 1) 32 x 32 -> 64-bit multiply-adds each in place of S FP64 FMAs
 // (a GB300 retires about 53 of those per SM and clock against 2 FP64
@@ -631,6 +631,8 @@ inline int update_fix_grid(sscg_ctx* ctx, int s, int64_t n) {
         case 2: return occupancy_grid(ctx, k_update_fix<2>, 0, n);
         case 3: return occupancy_grid(ctx, k_update_fix<3>, 0, n);
         case 4: return occupancy_grid(ctx, k_update_fix<4>, 0, n);
+        case 5: return occupancy_grid(ctx, k_update_fix<5>, 0, n);
+        case 6: return occupancy_grid(ctx, k_update_fix<6>, 0, n);
         default: return 0;
     }
 }
@@ -644,6 +646,8 @@ inline void launch_update_fix(int s, int grid, int64_t n, int ldn, double* blk_n
         case 2: k_update_fix<2><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
         case 3: k_update_fix<3><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
         case 4: k_update_fix<4><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 5: k_update_fix<5><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 6: k_update_fix<6><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
         default: break;
     }
 }

@@ -13,7 +13,7 @@
 //   1 x k_update_q : the block updates P = U + P_old beta, Q = U_{2..s+1} +
 //                    Q_old beta, x += P alpha, z -= Q alpha in one pass, with
 //                    ||r||^2 and mu_0 = r . z of the new residual; its last CTA
-//                    tests convergence.  In FP64 at s <= 4 every step after the
+//                    tests convergence.  In FP64 at s <= 6 every step after the
 //                    first runs k_update_fix instead: the same update with P
 //                    and Q formed as fixed-point dot products on the integer
 //                    multipliers (fixsum.cuh).
@@ -475,7 +475,7 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     size_t smem_updq = 0;
     int Gq = 0;
     if (int e = update_q_setup<A, SB>(ctx, n, s, &smem_updq, &Gq)) return e;
-    // FP64 at s <= 4: P and Q as fixed-point dot products from the second step on
+    // FP64 at s <= 6: P and Q as fixed-point dot products from the second step on
     const bool fix_upd = A::kind == 0 && s + 1 <= kFixMaxTerms && !(o->flags & SSCG_FMA_UPDATE);
     const int Gx = fix_upd ? update_fix_grid(ctx, s, n) : 0;
     const int Gt = occupancy_grid(ctx, k_true_res, smem64, n);

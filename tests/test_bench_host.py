@@ -92,7 +92,8 @@ def test_fixed_update_is_used_where_the_library_uses_it():
 
     assert bench.fixed_update_used(args())
     assert bench.fixed_update_used(args(s=1))
-    assert not bench.fixed_update_used(args(s=6))  # the 64-bit sums hold s + 1 <= 5 terms
+    assert bench.fixed_update_used(args(s=6))
+    assert not bench.fixed_update_used(args(s=8))  # the 64-bit sums hold s + 1 <= 7 terms
     assert not bench.fixed_update_used(args(arith="df64"))
     assert not bench.fixed_update_used(args(fma_update=True))
     assert not bench.fixed_update_used(args(fused_mpk=True))

@@ -180,7 +180,7 @@ def test_dot_error_within_bound(dlib):
     rows and coefficient columns of every spread of magnitudes."""
     rng = random.Random(11)
     for _ in range(3000):
-        k = rng.randint(1, 5)
+        k = rng.randint(1, 7)
         spread_v = rng.choice([0, 2, 8, 20, 60, 100])
         spread_c = rng.choice([0, 3, 10, 40])
         base = rng.uniform(-200, 200)
@@ -227,11 +227,14 @@ def test_dot_declines_outside_normal_range(dlib):
     assert ok and got == 1e300
 
 
-def test_dot_no_less_accurate_than_fma_chain_on_krylov_rows(dlib):
+@pytest.mark.parametrize("s", [4, 6])
+def test_dot_no_less_accurate_than_fma_chain_on_krylov_rows(dlib, s):
     """On rows like the block update's (a monomial basis of the Jacobi-scaled
     7-point Laplacian, P_old and Q_old one step older, beta scaled like the
     basis), the fixed-point error is smaller than that of the FP64 FMA chain it
-    replaces, in mean and in maximum (units of 2^-53 sum |v c|)."""
+    replaces, in mean and in maximum (units of 2^-53 sum |v c|; measured at
+    s = 4: 0.24 / 1.07 against 0.36 / 2.01, at s = 6: 0.18 / 1.71 against
+    0.30 / 2.26)."""
     rng = np.random.default_rng(5)
     N = 12
     n = N ** 3
@@ -247,7 +250,6 @@ def test_dot_no_less_accurate_than_fma_chain_on_krylov_rows(dlib):
         out[:, :, :-1] -= V[:, :, 1:]
         return (out / 6).ravel()
 
-    s = 4
     U = [rng.uniform(-1, 1, n) * 1e-6]
     for _ in range(s):
         U.append(dinvA(U[-1]))
@@ -270,7 +272,8 @@ def test_dot_no_less_accurate_than_fma_chain_on_krylov_rows(dlib):
                 errs["fix"].append(float(abs(Fraction(got) - exact) / unit))
                 errs["fma"].append(float(abs(Fraction(fma_chain(vs, cs)) - exact) / unit))
     fix, fma = np.array(errs["fix"]), np.array(errs["fma"])
-    assert fix.mean() < fma.mean() and fix.max() < max(fma.max(), 1.5)
+    assert fix.mean() < fma.mean()
+    assert fix.max() < max(fma.max(), 1.5), (fix.max(), fma.max())
 
 
 def test_pack_rounds_to_nearest_even(dlib):

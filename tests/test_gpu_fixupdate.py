@@ -1,9 +1,9 @@
 """The FP64 block update with P and Q formed as fixed-point dot products on
-the integer multipliers (the default at s <= 4) against the FP64 FMA update
+the integer multipliers (the default at s <= 6) against the FP64 FMA update
 (SSCG_FMA_UPDATE) and the FP64 oracle: the same outer-step counts (+-1),
 solutions within 1e-9 of each other and within 1e-7 of the oracle at equal
 step counts; rows whose values are all zero or below 2^-961 take the FP64 FMAs;
-block sizes above 4 are untouched by the flag."""
+block sizes above 6 are untouched by the flag."""
 import numpy as np
 import pytest
 
@@ -52,7 +52,7 @@ CASES = [("poisson7", 19, 0, 0.0, False), ("varcoef7", 14, 1, 1.5, False), ("poi
          ("aniso7", 15, 3, 0.0, False), ("poisson7", 17, 4, 0.0, True)]
 
 
-@pytest.mark.parametrize("s", [1, 2, 3, 4])
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_fixed_point_update_matches_fma_update_and_oracle(ctx, s, case):
     kind, N, seed, sig, csr = CASES[case]
@@ -73,16 +73,16 @@ def test_fixed_point_update_matches_fma_update_and_oracle(ctx, s, case):
 
 def test_fixed_point_update_runs_and_differs_in_rounding(ctx):
     """The default s = 4 solve does not repeat the FMA update bit for bit (its
-    dot products round once, the FMA chain s times), while s = 6 (above the
-    fixed-point limit) is identical with and without the flag."""
+    dot products round once, the FMA chain s times), while s = 8 (above the
+    fixed-point limit of s = 6) is identical with and without the flag."""
     S = system("poisson7", 19, 0)
     A = sscg.Matrix(ctx, S["rowptr"], S["col"], S["val"])
     xf, rf = solve(A, S["b"], s=4, tol=1e-10, maxit=1000)
     xm, rm = solve(A, S["b"], s=4, tol=1e-10, maxit=1000, fma_update=True)
     assert not np.array_equal(xf, xm) and rel(xf, xm) < 1e-9
-    x6, r6 = solve(A, S["b"], s=6, tol=1e-8, maxit=1000)
-    y6, q6 = solve(A, S["b"], s=6, tol=1e-8, maxit=1000, fma_update=True)
-    assert np.array_equal(x6, y6) and r6.outer_iters == q6.outer_iters
+    x8, r8 = solve(A, S["b"], s=8, tol=1e-8, maxit=1000)
+    y8, q8 = solve(A, S["b"], s=8, tol=1e-8, maxit=1000, fma_update=True)
+    assert np.array_equal(x8, y8) and r8.outer_iters == q8.outer_iters
 
 
 def test_rows_of_zeros_and_tiny_values_take_the_fma_path(ctx):
