@@ -110,8 +110,15 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(MatView M, const typename
     }
 }
 
+// PCG's FP64 7-point SpMV measured fastest at 5 CTAs per SM (48 registers;
+// the s-step level, with its second moment, at 4).
+template <class A, int DM>
+__host__ __device__ constexpr int pcg_spmv_min_blocks() {
+    return (A::kind == 0 && DM == 7) ? 5 : dia_min_blocks<A, DM>();
+}
+
 template <class A, int VM, int DM>
-__global__ void __launch_bounds__(kThreads, dia_min_blocks<A, DM>()) k_pcg_spmv(MatView M, const typename A::S* __restrict__ p,
+__global__ void __launch_bounds__(kThreads, pcg_spmv_min_blocks<A, DM>()) k_pcg_spmv(MatView M, const typename A::S* __restrict__ p,
                                                        typename A::S* __restrict__ q, double* __restrict__ part,
                                                        Ctrl* ctrl) {
     using R = typename A::R;
