@@ -107,3 +107,19 @@ def test_rows_of_zeros_and_tiny_values_take_the_fma_path(ctx):
     assert ref.status == oracle.OK and abs(rf.outer_iters - ref.iters) <= 1
     same = oracle.pcgs(oracle.as_matrix(S), b, 4, tol=0.0, maxit=rf.outer_iters)
     assert rel(xf, same.x) < 1e-7
+
+
+@pytest.mark.parametrize("kind,N,sigma", [("poisson7", 32, 0.0), ("varcoef7", 24, 3.0), ("poisson27", 40, 0.0)])
+def test_attainable_accuracy_matches_fma_update(ctx, kind, N, sigma):
+    """Solved to 1e-12, where the gap between the recursive and the true
+    residual shows how rounding in the updates accumulates: the fixed-point
+    update's true residual is no larger than twice the FMA update's, and both
+    solutions agree with the oracle's at equal step counts."""
+    S = system(kind, N, 7, sigma)
+    A = sscg.Matrix(ctx, S["rowptr"], S["col"], S["val"])
+    xf, rf = solve(A, S["b"], s=4, tol=1e-12, maxit=3000)
+    xm, rm = solve(A, S["b"], s=4, tol=1e-12, maxit=3000, fma_update=True)
+    assert rf.status == rm.status == sscg.OK
+    assert rf.rel_res_true <= 2 * max(rm.rel_res_true, 1e-13), (rf.rel_res_true, rm.rel_res_true)
+    same = oracle.pcgs(oracle.as_matrix(S), S["b"], 4, tol=0.0, maxit=rf.outer_iters)
+    assert rel(xf, same.x) < 1e-7
