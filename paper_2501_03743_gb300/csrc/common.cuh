@@ -397,16 +397,8 @@ template <class F>
 __device__ __forceinline__ void cta_sum_rows(const double* p, int count, int G, F store) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int e = warp; e < count; e += nw) {
-        // eight independent partial sums per lane keep eight loads in flight
-        const double* q = p + (size_t)e * G;
-        double u[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        int i = lane;
-        for (; i + 7 * 32 < G; i += 8 * 32) {
-#pragma unroll
-            for (int k = 0; k < 8; k++) u[k] += __ldcg(q + i + 32 * k);
-        }
-        for (; i < G; i += 32) u[0] += __ldcg(q + i);  // fewer than eight left
-        double t = ((u[0] + u[1]) + (u[2] + u[3])) + ((u[4] + u[5]) + (u[6] + u[7]));
+        double t = 0.0;
+        for (int i = lane; i < G; i += 32) t += __ldcg(p + (size_t)e * G + i);
 #pragma unroll
         for (int m = 16; m > 0; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
         if (lane == 0) store(e, t);
