@@ -624,34 +624,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_update_fix(int n, int ldn, doub
     update_q_finish<ArithF64>(rr, rz, diag != nullptr, diag_c, red, part, ctrl, hist);
 }
 
-// Grid of k_update_fix for the block size s (1..4): its occupancy times the SMs.
-inline int update_fix_grid(sscg_ctx* ctx, int s, int64_t n) {
-    switch (s) {
-        case 1: return occupancy_grid(ctx, k_update_fix<1>, 0, n);
-        case 2: return occupancy_grid(ctx, k_update_fix<2>, 0, n);
-        case 3: return occupancy_grid(ctx, k_update_fix<3>, 0, n);
-        case 4: return occupancy_grid(ctx, k_update_fix<4>, 0, n);
-        case 5: return occupancy_grid(ctx, k_update_fix<5>, 0, n);
-        case 6: return occupancy_grid(ctx, k_update_fix<6>, 0, n);
-        default: return 0;
-    }
-}
-
-inline void launch_update_fix(int s, int grid, int64_t n, int ldn, double* blk_new, double* blk_old, double* x,
-                              const double* diag, double diag_c, double* part, Ctrl* ctrl, double* hist,
-                              cudaStream_t st) {
-    const int N = (int)n;
-    switch (s) {
-        case 1: k_update_fix<1><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
-        case 2: k_update_fix<2><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
-        case 3: k_update_fix<3><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
-        case 4: k_update_fix<4><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
-        case 5: k_update_fix<5><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
-        case 6: k_update_fix<6><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
-        default: break;
-    }
-}
-
 template <class A, int SB>
 inline int update_q_setup(sscg_ctx* ctx, int64_t n, int s, size_t* smem, int* grid) {
     (void)s;

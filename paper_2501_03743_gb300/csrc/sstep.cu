@@ -428,6 +428,34 @@ Layout plan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t c
     return L;
 }
 
+// Grid of k_update_fix for the block size s (1..6): its occupancy times the SMs.
+inline int update_fix_grid(sscg_ctx* ctx, int s, int64_t n) {
+    switch (s) {
+        case 1: return occupancy_grid(ctx, k_update_fix<1>, 0, n);
+        case 2: return occupancy_grid(ctx, k_update_fix<2>, 0, n);
+        case 3: return occupancy_grid(ctx, k_update_fix<3>, 0, n);
+        case 4: return occupancy_grid(ctx, k_update_fix<4>, 0, n);
+        case 5: return occupancy_grid(ctx, k_update_fix<5>, 0, n);
+        case 6: return occupancy_grid(ctx, k_update_fix<6>, 0, n);
+        default: return 0;
+    }
+}
+
+inline void launch_update_fix(int s, int grid, int64_t n, int ldn, double* blk_new, double* blk_old, double* x,
+                              const double* diag, double diag_c, double* part, Ctrl* ctrl, double* hist,
+                              cudaStream_t st) {
+    const int N = (int)n;
+    switch (s) {
+        case 1: k_update_fix<1><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 2: k_update_fix<2><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 3: k_update_fix<3><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 4: k_update_fix<4><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 5: k_update_fix<5><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 6: k_update_fix<6><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        default: break;
+    }
+}
+
 template <class A, int VM, int SB, int DM>
 int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, const sscg_opts* o,
               const Layout& L, const typename A::S* dinv, const typename A::S* diag, Ctrl* hctrl, Prof& P) {
