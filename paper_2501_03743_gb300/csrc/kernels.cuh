@@ -517,12 +517,11 @@ __global__ void __launch_bounds__(kThreads) k_update_q(int n, int ldn, int s, ty
 // (a GB300 retires about 53 of those per SM and clock against 2 FP64
 // operations).  A row's values U_1..U_{S+1}, P_old and Q_old share one
 // alignment exponent; each column j of the coefficients [1; beta_0j ..
-// beta_{S-1}j] has its own.  x += P alpha and z -= Q alpha stay
-// FP64 FMAs on the rounded P and Q, as in k_update_q.  A row holding a NaN,
-// an infinity or only values below 2^-961, or whose entries could leave the
-// normal range, takes the FP64 FMAs of k_update_q; so does every row when a
-// coefficient is not finite.  Not for the first step (no
-// P_old, Q_old).
+// beta_{S-1}j] has its own.  x += P alpha and z -= Q alpha stay FP64 FMAs on
+// the rounded P and Q, as in k_update_q.  A row holding a NaN, an infinity or
+// only values below 2^-961, or whose entries could leave the normal range,
+// takes the FP64 FMAs of k_update_q; so does every row when a coefficient is
+// not finite.  Not for the first step (no P_old, Q_old).
 template <int S>
 __global__ void __launch_bounds__(kThreads, 2) k_update_fix(int n, int ldn, double* __restrict__ blk_new,
                                                             double* __restrict__ blk_old, double* __restrict__ x,
