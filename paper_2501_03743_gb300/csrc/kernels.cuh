@@ -510,6 +510,20 @@ __global__ void __launch_bounds__(kThreads) k_update_q(int n, int ldn, int s, ty
     update_q_finish<A>(rr, rz, diag != nullptr, diag_c, red, part, ctrl, hist);
 }
 
+// Per-thread asynchronous copies of 8 bytes global -> shared (cp.async),
+// completion tracked per thread by commit groups.
+__device__ __forceinline__ void row_cp8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void row_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void row_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void row_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int S>
+__host__ __device__ constexpr size_t fix_row_smem() {
+    return 2 * (size_t)(3 * S + 2) * kThreads * sizeof(double);
+}
+
 // The FP64 block update of k_update_q with P and Q formed as fixed-point dot
 // products on the integer multipliers (fixsum.cuh), for block sizes S <= 6:
 //   P_j = U_j + sum_l P_old_l beta_lj,   Q_j = U_{j+1} + sum_l Q_old_l beta_lj
@@ -551,16 +565,44 @@ __global__ void __launch_bounds__(kThreads, 2) k_update_fix(int n, int ldn, doub
     fix_row_range<S>(fc, &Elo, &Ehi);
     const size_t ld = (size_t)ldn;
     double rr = 0.0, rz = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double u[S + 1], po[S], qo[S];
+    // each thread copies its next row's 3S+2 values (U_1..U_{S+1}, P_old, Q_old,
+    // x) into its own slots of one of two shared-memory buffers while it
+    // computes the current row
+    extern __shared__ __align__(16) double rowbuf[];
+    constexpr int NCOL = 3 * S + 2;
+    const int stride = gridDim.x * blockDim.x;
+    auto issue = [&](int i, int b) {
+        double* d = rowbuf + (size_t)b * NCOL * kThreads + threadIdx.x;
 #pragma unroll
-        for (int c = 0; c <= S; c++) u[c] = __ldcg(blk_new + c * ld + i);
+        for (int c = 0; c <= S; c++) row_cp8(d + c * kThreads, blk_new + c * ld + i);
 #pragma unroll
         for (int l = 0; l < S; l++) {
-            po[l] = __ldcg(blk_old + l * ld + i);
-            qo[l] = __ldcg(blk_old + (S + 1 + l) * ld + i);
+            row_cp8(d + (S + 1 + l) * kThreads, blk_old + l * ld + i);
+            row_cp8(d + (2 * S + 1 + l) * kThreads, blk_old + (S + 1 + l) * ld + i);
         }
-        double xn = __ldcg(x + i), zn = u[0];
+        row_cp8(d + (3 * S + 1) * kThreads, x + i);
+        row_commit();
+    };
+    int k = 0;
+    if (blockIdx.x * blockDim.x + threadIdx.x < n) issue(blockIdx.x * blockDim.x + threadIdx.x, 0);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride, k++) {
+        if ((unsigned)i + (unsigned)stride < (unsigned)n) {  // no overflow: i, stride < 2^31
+            issue(i + stride, (k + 1) & 1);
+            row_wait_prior();
+        } else {
+            row_wait_all();
+        }
+        double u[S + 1], po[S], qo[S];
+        const double* d = rowbuf + (size_t)(k & 1) * NCOL * kThreads + threadIdx.x;
+#pragma unroll
+        for (int c = 0; c <= S; c++) u[c] = d[c * kThreads];
+#pragma unroll
+        for (int l = 0; l < S; l++) {
+            po[l] = d[(S + 1 + l) * kThreads];
+            qo[l] = d[(2 * S + 1 + l) * kThreads];
+        }
+        double xn = d[(3 * S + 1) * kThreads];
+        double zn = u[0];
         // the row exponent E: the largest exponent field of its values (sign
         // cleared, as an integer), shared by the P and Q columns
         double p[S], q[S];

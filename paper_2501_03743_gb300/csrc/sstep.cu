@@ -429,14 +429,20 @@ Layout plan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t c
 }
 
 // Grid of k_update_fix for the block size s (1..6): its occupancy times the SMs.
+template <int S>
+inline int update_fix_grid_s(sscg_ctx* ctx, int64_t n) {
+    cudaFuncSetAttribute(k_update_fix<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fix_row_smem<S>());
+    return occupancy_grid(ctx, k_update_fix<S>, fix_row_smem<S>(), n);
+}
+
 inline int update_fix_grid(sscg_ctx* ctx, int s, int64_t n) {
     switch (s) {
-        case 1: return occupancy_grid(ctx, k_update_fix<1>, 0, n);
-        case 2: return occupancy_grid(ctx, k_update_fix<2>, 0, n);
-        case 3: return occupancy_grid(ctx, k_update_fix<3>, 0, n);
-        case 4: return occupancy_grid(ctx, k_update_fix<4>, 0, n);
-        case 5: return occupancy_grid(ctx, k_update_fix<5>, 0, n);
-        case 6: return occupancy_grid(ctx, k_update_fix<6>, 0, n);
+        case 1: return update_fix_grid_s<1>(ctx, n);
+        case 2: return update_fix_grid_s<2>(ctx, n);
+        case 3: return update_fix_grid_s<3>(ctx, n);
+        case 4: return update_fix_grid_s<4>(ctx, n);
+        case 5: return update_fix_grid_s<5>(ctx, n);
+        case 6: return update_fix_grid_s<6>(ctx, n);
         default: return 0;
     }
 }
@@ -446,12 +452,12 @@ inline void launch_update_fix(int s, int grid, int64_t n, int ldn, double* blk_n
                               cudaStream_t st) {
     const int N = (int)n;
     switch (s) {
-        case 1: k_update_fix<1><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
-        case 2: k_update_fix<2><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
-        case 3: k_update_fix<3><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
-        case 4: k_update_fix<4><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
-        case 5: k_update_fix<5><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
-        case 6: k_update_fix<6><<<grid, kThreads, 0, st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 1: k_update_fix<1><<<grid, kThreads, fix_row_smem<1>(), st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 2: k_update_fix<2><<<grid, kThreads, fix_row_smem<2>(), st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 3: k_update_fix<3><<<grid, kThreads, fix_row_smem<3>(), st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 4: k_update_fix<4><<<grid, kThreads, fix_row_smem<4>(), st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 5: k_update_fix<5><<<grid, kThreads, fix_row_smem<5>(), st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
+        case 6: k_update_fix<6><<<grid, kThreads, fix_row_smem<6>(), st>>>(N, ldn, blk_new, blk_old, x, diag, diag_c, part, ctrl, hist); break;
         default: break;
     }
 }
