@@ -115,7 +115,7 @@ def parse():
 # other configuration.
 NCU_TRAFFIC_PER_ROW = {
     "f64": {"mpk": 53.79e6 / 4.096e6, "update": 734.1e6 / 4.096e6},
-    "f64-fixed": {"update": 733.84e6 / 4.096e6},
+    "f64-fixed": {"update": 733.196e6 / 4.096e6},
     "df64": {"mpk": 54.0e6 / 4.096e6, "update": 732.694e6 / 4.096e6},
 }
 
@@ -314,20 +314,23 @@ def workload_name(N, s, arith):
 
 
 def fp64_ops_model(s, K=7, fixed_update=False):
-    """FP64 operations per row of the FP64 kernels on a Laplacian-class stencil
-    in the diagonal form under a constant Jacobi scale (one DFMA, DADD or DMUL
-    per thread is one operation).  The neighbour sum runs on the integer units
-    (fixed point, csrc/fixsum.cuh) and costs no FP64 operation, whatever K:
-    level j: one FMA for u_{j+1} and one for each moment (the second moment is
-    skipped on the last level); block update: s^2 FMAs each for P and Q (none
-    with the fixed-point update, whose P and Q are integer dot products), s
-    each for x and z, one for sum z^2 (first step: no P, Q FMAs); PCG: SpMV
-    one FMA for A p and one for p . Ap; update x, r, ||r||^2; direction
-    u = D^-1 r and p = u + beta p."""
-    lvl = [2 + (1 if 2 * j + 2 <= 2 * s - 1 else 0) for j in range(s)]
-    upd = 2 * s + 1 if fixed_update else 2 * s * s + 2 * s + 1
+    """FP64-pipe operations per row of the FP64 kernels on a Laplacian-class
+    stencil in the diagonal form under a constant Jacobi scale.  One DFMA,
+    DADD or DMUL per thread is one operation, and so is each conversion of a
+    64-bit fixed-point sum to FP64: a GB300 issues that conversion to the FP64
+    pipe at its rate (the I2F64 probe of include/sscg_probe.h).  The neighbour
+    sum itself runs on the integer units (csrc/fixsum.cuh), whatever K, and
+    costs one conversion.  Level j: the conversion, one FMA for u_{j+1} and one
+    for each moment (the second moment is skipped on the last level); block
+    update: s^2 FMAs each for P and Q (with the fixed-point update none: P and
+    Q are integer dot products, one conversion each), s FMAs each for x and z,
+    one for sum z^2 (first step: no P, Q); PCG: SpMV the conversion, one FMA
+    for A p and one for p . Ap; update x, r, ||r||^2; direction u = D^-1 r and
+    p = u + beta p."""
+    lvl = [3 + (1 if 2 * j + 2 <= 2 * s - 1 else 0) for j in range(s)]
+    upd = 4 * s + 1 if fixed_update else 2 * s * s + 2 * s + 1
     return dict(level=lvl, level_avg=sum(lvl) / s, update=upd, update_first=2 * s + 1,
-                pcg_spmv=2, pcg_update=3, pcg_dir=2)
+                pcg_spmv=3, pcg_update=3, pcg_dir=2)
 
 
 def fixed_update_used(a):

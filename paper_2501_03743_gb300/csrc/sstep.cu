@@ -428,10 +428,13 @@ Layout plan(const sscg_mat* mat, const sscg_opts* o, int G, void* base, size_t c
     return L;
 }
 
-// Grid of k_update_fix for the block size s (1..6): its occupancy times the SMs.
+// Grid of k_update_fix for the block size s (1..6): its occupancy, with its
+// two row buffers of shared memory, times the SMs; 0 when the attribute is refused.
 template <int S>
 inline int update_fix_grid_s(sscg_ctx* ctx, int64_t n) {
-    cudaFuncSetAttribute(k_update_fix<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fix_row_smem<S>());
+    if (cudaFuncSetAttribute(k_update_fix<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fix_row_smem<S>()) != cudaSuccess)
+        return 0;
     return occupancy_grid(ctx, k_update_fix<S>, fix_row_smem<S>(), n);
 }
 
@@ -512,6 +515,8 @@ int run_sstep(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, co
     // FP64 at s <= 6: P and Q as fixed-point dot products from the second step on
     const bool fix_upd = A::kind == 0 && s + 1 <= kFixMaxTerms && !(o->flags & SSCG_FMA_UPDATE);
     const int Gx = fix_upd ? update_fix_grid(ctx, s, n) : 0;
+    if (fix_upd && Gx == 0)
+        return set_err(ctx, SSCG_ERR_CUDA, "shared memory for the fixed-point block update refused");
     const int Gt = occupancy_grid(ctx, k_true_res, smem64, n);
     k_init<A, VM><<<Gi, kThreads, smem, st>>>(M, dinv, b, x, A::kind == 0 ? nullptr : xw, r, blk[0], L.part,
                                               L.ctrl, L.hist);

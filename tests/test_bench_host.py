@@ -72,14 +72,16 @@ def test_value_is_kernel_bytes_over_time_and_stays_below_the_copy_bandwidth():
 
 def test_fp64_operation_model():
     ops = bench.fp64_ops_model(4, K=7)
-    # level: the neighbour sum on the integer units; u_{j+1} and two moments (one on the last level)
-    assert ops["level"] == [3, 3, 3, 2]
+    # level: the neighbour sum on the integer units and its conversion to FP64;
+    # u_{j+1} and two moments (one on the last level)
+    assert ops["level"] == [4, 4, 4, 3]
     # update: s^2 for P and Q each, s for x and z each, one for sum z^2
     assert ops["update"] == 2 * 16 + 2 * 4 + 1 and ops["update_first"] == 9
-    assert (ops["pcg_spmv"], ops["pcg_update"], ops["pcg_dir"]) == (2, 3, 2)
-    assert bench.fp64_ops_model(2, K=27)["level"] == [3, 2]
-    # the fixed-point update: P and Q on the integer units, x and z FMAs and sum z^2 left
-    assert bench.fp64_ops_model(4, fixed_update=True)["update"] == 2 * 4 + 1
+    assert (ops["pcg_spmv"], ops["pcg_update"], ops["pcg_dir"]) == (3, 3, 2)
+    assert bench.fp64_ops_model(2, K=27)["level"] == [4, 3]
+    # the fixed-point update: P and Q on the integer units, one conversion each;
+    # x and z FMAs and sum z^2 left
+    assert bench.fp64_ops_model(4, fixed_update=True)["update"] == 2 * 4 + 2 * 4 + 1
 
 
 def test_fixed_update_is_used_where_the_library_uses_it():
