@@ -741,18 +741,27 @@ def run_batch(a, world, rank, local, pg):
     cpu = None
     if rank == 0:
         # the oracle beside it: the mix's smallest system, each of its right-hand sides
-        # solved to the same tolerance by the FP64 CPU oracle's s-step PCG on the host cores
+        # solved to the same tolerance by the FP64 CPU oracle's s-step PCG on the host
+        # cores, scaled to the whole mix by the algorithmic bytes of the solves (the
+        # byte model of this line: the sample's bytes at the oracle's own step counts,
+        # the mix's at the device's)
         import oracle
 
         k0 = min(range(len(spec)), key=lambda k: sizes[k][0])
         Mo = oracle.as_matrix(dict(zip(("rowptr", "col", "val"), inputs.batch_csr(spec[k0]))))
         t0 = time.perf_counter()
+        cpu_steps = 0
         for r in range(R[k0]):
-            oracle.pcgs(Mo, B[k0][r].cpu().numpy(), a.s, tol=a.tol, maxit=5000)
+            cpu_steps = max(cpu_steps, oracle.pcgs(Mo, B[k0][r].cpu().numpy(), a.s, tol=a.tol, maxit=5000).iters)
         t_cpu = time.perf_counter() - t0
-        cpu = {"value": round(R[k0] / t_cpu, 2), "unit": "rhs/s", "cores": oracle.num_threads(), "kind": "oracle",
+        n0, nnz0, vb0 = sizes[k0]
+        rate = batch_bytes(n0, nnz0, vb0, R[k0], a.s, cpu_steps) / t_cpu  # oracle bytes per second
+        cpu = {"value": round(total_rhs / (byts / rate), 3), "unit": "rhs/s", "cores": oracle.num_threads(),
+               "kind": "oracle",
                "sample": f"system {k0} of the mix ({spec[k0]['kind']} {spec[k0]['N']}^3, {R[k0]} right-hand "
-                         f"sides, the smallest): {t_cpu:.2f} s"}
+                         f"sides, the smallest, {cpu_steps} outer steps): {t_cpu:.2f} s, "
+                         f"{rate / 1e9:.2f} GB/s by the byte model; the whole mix's {byts / 1e9:.0f} GB at that "
+                         f"rate: {byts / rate:.0f} s"}
         peak, src = hbm_peak()
         eff = byts / (statistics.median(ms) * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(eff, 1), "peak": peak, "unit": "GB/s", "frac": round(eff / peak, 4),
