@@ -610,7 +610,8 @@ def main():
             "value_definition": "bytes the solve's kernels move (their algorithmic byte model, V = 8 n) per second "
                                 "of device time; cannot exceed the copy bandwidth",
             "value_yardstick_gbs": round(value_yard, 1),
-            "solve_ms": round(ms_per_step, 3), "outer_iters": r0.outer_iters, "equiv_iters": r0.equiv_iters,
+            "solve_ms": round(ms_per_step, 3), "solve_ms_steps": [round(t, 3) for t in ms],
+            "outer_iters": r0.outer_iters, "equiv_iters": r0.equiv_iters,
             "status": r0.status, "rel_res_recursive": r0.rel_res_recursive, "rel_res_true": r0.rel_res_true,
             "yardstick_bytes_per_solve": yard_solve, "kernel_bytes_per_solve": kernel_bytes_solve,
             "wall_s_timed": round(t_wall, 3),

@@ -1281,10 +1281,9 @@ int run_phases(sscg_batch* b) {
     if (int rc = launch_any(b, L_INIT, 0, b->maxit)) return rc;
     b->last_launches = 1;
     const int limit = b->maxit + 4, per_chunk = 8;
-    cudaEvent_t ev[2];
-    SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-    SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-    int launched = 0, chunk = 0, pending = -1, rc = SSCG_OK;
+    ChunkPoll poll;
+    SSCG_CUDA(ctx, poll.init());
+    int launched = 0, rc = SSCG_OK;
     while (launched < limit) {
         const int c = std::min(per_chunk, limit - launched);
         for (int q = 0; q < c && rc == SSCG_OK; q++) {
@@ -1298,24 +1297,15 @@ int run_phases(sscg_batch* b) {
         if (rc) break;
         launched += c;
         b->last_launches += (int64_t)c * (b->s * (b->has_csr + b->has_dia) + 2);  // levels, solves, update
-        const int slot = chunk & 1;
-        if (cudaMemcpyAsync((void*)(ctx->pinned + slot), &b->d_g->finished, sizeof(int), cudaMemcpyDeviceToHost,
-                            st) != cudaSuccess ||
-            cudaEventRecord(ev[slot], st) != cudaSuccess) {
-            rc = set_err(ctx, SSCG_ERR_CUDA, "polling copy failed");
+        int fin = 0;
+        cudaError_t pe = cudaSuccess;
+        const bool got = poll.step(ctx->pinned, &b->d_g->finished, st, &fin, &pe);
+        if (pe != cudaSuccess) {
+            rc = set_err(ctx, SSCG_ERR_CUDA, "polling: %s", cudaGetErrorString(pe));
             break;
         }
-        if (pending >= 0) {
-            if (cudaEventSynchronize(ev[pending & 1]) != cudaSuccess) {
-                rc = set_err(ctx, SSCG_ERR_CUDA, "polling wait failed");
-                break;
-            }
-            if (ctx->pinned[pending & 1] >= b->nsys) break;
-        }
-        pending = chunk++;
+        if (got && fin >= b->nsys) break;
     }
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
     if (rc) return rc;
     SSCG_CUDA(ctx, cudaMemcpyAsync(b->h_rc, b->d_rc, sizeof(Ctrl) * b->total_rhs, cudaMemcpyDeviceToHost, st));
     SSCG_CUDA(ctx, cudaMemcpyAsync(b->h_bctl, b->d_bctl, sizeof(BCtl) * b->nsys, cudaMemcpyDeviceToHost, st));

@@ -124,10 +124,9 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
     SSCG_CUDA(ctx, cudaGetLastError());
 
     const int per_chunk = std::max(1, 32 / (s + 2));
-    cudaEvent_t ev[2];
-    SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-    SSCG_CUDA(ctx, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-    int launched = 0, chunk = 0, pending = -1, err = 0;
+    ChunkPoll poll;
+    SSCG_CUDA(ctx, poll.init());
+    int launched = 0, err = 0;
     while (launched < o->maxit) {
         int c = std::min(per_chunk, o->maxit - launched);
         for (int q = 0; q < c; q++) {
@@ -168,18 +167,12 @@ int run_gram(sscg_ctx* ctx, const sscg_mat* mat, const double* b, double* x, con
             break;
         }
         launched += c;
-        const int slot = chunk & 1;
-        SSCG_CUDA(ctx, cudaMemcpyAsync((void*)(ctx->pinned + slot), &L.ctrl->done, sizeof(int),
-                                       cudaMemcpyDeviceToHost, st));
-        SSCG_CUDA(ctx, cudaEventRecord(ev[slot], st));
-        if (pending >= 0) {
-            SSCG_CUDA(ctx, cudaEventSynchronize(ev[pending & 1]));
-            if (ctx->pinned[pending & 1]) break;
-        }
-        pending = chunk++;
+        int fin = 0;
+        cudaError_t pe = cudaSuccess;
+        const bool got = poll.step(ctx->pinned, &L.ctrl->done, st, &fin, &pe);
+        SSCG_CUDA(ctx, pe);
+        if (got && fin) break;
     }
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
     if (err) return set_err(ctx, SSCG_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     P.begin();
     if (A::kind != 0) k_export_x<A><<<Ge, kThreads, 0, st>>>(n, xw, x, L.ctrl);
