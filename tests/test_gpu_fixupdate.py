@@ -123,3 +123,39 @@ def test_attainable_accuracy_matches_fma_update(ctx, kind, N, sigma):
     assert rf.rel_res_true <= 2 * max(rm.rel_res_true, 1e-13), (rf.rel_res_true, rm.rel_res_true)
     same = oracle.pcgs(oracle.as_matrix(S), S["b"], 4, tol=0.0, maxit=rf.outer_iters)
     assert rel(xf, same.x) < 1e-7
+
+
+def tridiagonal(n, seed):
+    """SPD tridiagonal CSR: -1 off the diagonal, 4 + |u_i| on it (u seeded uniform)."""
+    d = 4.0 + np.abs(inputs.uniform(seed, n))
+    rows = np.arange(n)
+    cols = np.stack([rows - 1, rows, rows + 1], axis=1)
+    vals = np.stack([-np.ones(n), d, -np.ones(n)], axis=1)
+    keep = (cols >= 0) & (cols < n)
+    rowptr = np.concatenate([[0], np.cumsum(keep.sum(1))]).astype(np.int32)
+    return dict(rowptr=rowptr, col=cols[keep].astype(np.int32), val=vals[keep])
+
+
+@pytest.mark.parametrize("s", [2, 4, 6])
+@pytest.mark.parametrize("mult,extra", [(1, 1), (2, -1), (3, 5)])
+def test_update_row_prefetch_at_grid_stride_boundaries(ctx, s, mult, extra):
+    """Each thread of the fixed-point update copies its next row (i + the grid's
+    threads) to shared memory while it computes row i.  Row counts just above,
+    just below and past multiples of the grid's threads at two CTAs per SM
+    (s = 4, 6; s = 2 runs more CTAs) leave threads with different row counts,
+    the last row of each taking the no-prefetch branch: the solution matches
+    the FMA update's and the oracle's at equal step counts."""
+    stride = torch.cuda.get_device_properties(0).multi_processor_count * 2 * 256
+    n = mult * stride + extra
+    S = tridiagonal(n, 11 + mult)
+    b = inputs.uniform(40 + mult, n)
+    A = sscg.Matrix(ctx, S["rowptr"], S["col"], S["val"])
+    xf, rf = solve(A, b, s=s, tol=1e-10, maxit=200)
+    xm, rm = solve(A, b, s=s, tol=1e-10, maxit=200, fma_update=True)
+    assert rf.status == rm.status == sscg.OK and abs(rf.outer_iters - rm.outer_iters) <= 1
+    assert rf.outer_iters >= 2  # the fixed-point update runs from the second step on
+    if rf.outer_iters == rm.outer_iters:
+        assert rel(xf, xm) < 1e-9, rel(xf, xm)
+    same = oracle.pcgs(oracle.as_matrix(S), b, s, tol=0.0, maxit=rf.outer_iters)
+    assert rel(xf, same.x) < 1e-7
+    assert rf.rel_res_true < 1e-9
