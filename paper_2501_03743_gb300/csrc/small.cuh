@@ -53,7 +53,9 @@ __device__ __forceinline__ bool warp_chol_solve(const double* L, int s, double* 
     return __all_sync(0xffffffffu, ok);
 }
 
-// Scratch for the solves: 4 s x s matrices and 2 vectors, for s <= MS.
+// Scratch for the solves: 4 s x s matrices and 2 vectors, for s <= MS, and
+// shared-memory copies of the inputs the monomial step reads more than once
+// (the moments mu_0..mu_{2s-1} and the previous alpha).
 template <int MS>
 struct SmallScratchT {
     double L[MS * MS];
@@ -62,6 +64,8 @@ struct SmallScratchT {
     double b1[MS * MS];
     double a[MS];
     double c[MS];
+    double mu[2 * MS];
+    double al[MS];
 };
 using SmallScratch = SmallScratchT<kMaxS>;
 
@@ -78,7 +82,13 @@ using SmallScratch = SmallScratchT<kMaxS>;
 template <class SC>
 __device__ inline int warp_sw_monomial(Ctrl* ctrl, int s, int step, SC* sc) {
     const int lane = threadIdx.x & 31;
-    const double* mu = ctrl->mu;
+    // the moments and the previous alpha copied to shared memory by the whole
+    // warp at once: the serial steps below then read no global memory
+    for (int e = lane; e < 2 * s; e += 32) sc->mu[e] = ctrl->mu[e];
+    if (step > 0)
+        for (int e = lane; e < s; e += 32) sc->al[e] = ctrl->alpha[e];
+    __syncwarp();
+    const double* mu = sc->mu;
     if (step == 0) {
         for (int e = lane; e < s * s; e += 32) {
             int a = e % s, b = e / s;
@@ -91,12 +101,13 @@ __device__ inline int warp_sw_monomial(Ctrl* ctrl, int s, int step, SC* sc) {
         if (!warp_cholesky(sc->L, s)) return 2;
         if (!warp_chol_solve(sc->L, s, sc->a, 1)) return 2;
     } else {
-        double as = ctrl->alpha[s - 1];
+        const double* al = sc->al;
+        double as = al[s - 1];
         if (as == 0.0 || !isfinite(as)) return 2;
         if (lane == 0) {
             for (int t = 0; t < s; t++) {
                 double v = mu[t];
-                for (int j = 0; j < t; j++) v += sc->c[j] * ctrl->alpha[s - 1 - t + j];
+                for (int j = 0; j < t; j++) v += sc->c[j] * al[s - 1 - t + j];
                 sc->c[t] = -v / as;
             }
         }
