@@ -292,6 +292,8 @@ struct Ctrl {
     double scratch[8];
     unsigned claim;  // work-item counter of the fused matrix-powers kernel
     unsigned pad1[3];
+    double Wl[kMaxS * kMaxS];  // Cholesky factor of W (lower triangle), for the next step's solve
+    double Wr[kMaxS];          // reciprocals of its diagonal
 };
 
 // ------------------------------------------------------------- reductions

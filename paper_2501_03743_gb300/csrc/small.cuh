@@ -8,18 +8,24 @@
 namespace sscg {
 
 // In-place Cholesky A = L L^T of an s x s column-major matrix in shared
-// memory (lower triangle overwritten by L), lanes parallel over rows.
-// Returns false (in every lane) if a pivot is not positive or not finite.
-__device__ __forceinline__ bool warp_cholesky(double* A, int s) {
+// memory (lower triangle overwritten by L), lanes parallel over rows, with
+// rinv[k] = 1 / L_kk: one reciprocal square root per pivot, the column below
+// it scaled by that reciprocal (a multiplication, where a division would sit
+// on the serial chain).  Returns false (in every lane) if a pivot is not
+// positive or not finite.
+__device__ __forceinline__ bool warp_cholesky(double* A, int s, double* rinv) {
     const int lane = threadIdx.x & 31;
     for (int k = 0; k < s; k++) {
         __syncwarp();
         double d = A[k + k * s];
         if (!(d > 0.0) || !isfinite(d)) return false;
-        double lkk = sqrt(d);
+        const double r = rsqrt(d);
         __syncwarp();
-        if (lane == 0) A[k + k * s] = lkk;
-        if (lane > k && lane < s) A[lane + k * s] = A[lane + k * s] / lkk;
+        if (lane == 0) {
+            A[k + k * s] = d * r;
+            rinv[k] = r;
+        }
+        if (lane > k && lane < s) A[lane + k * s] *= r;
         __syncwarp();
         if (lane > k && lane < s) {
             double lik = A[lane + k * s];
@@ -31,8 +37,9 @@ __device__ __forceinline__ bool warp_cholesky(double* A, int s) {
 }
 
 // Solve L L^T X = B for `nrhs` column-major right-hand sides (in place),
-// lanes parallel over columns.  Returns false if a result is not finite.
-__device__ __forceinline__ bool warp_chol_solve(const double* L, int s, double* B, int nrhs) {
+// lanes parallel over columns, multiplying by rinv[i] = 1 / L_ii (from
+// warp_cholesky) rather than dividing.  Returns false if a result is not finite.
+__device__ __forceinline__ bool warp_chol_solve(const double* L, int s, double* B, int nrhs, const double* rinv) {
     const int lane = threadIdx.x & 31;
     bool ok = true;
     for (int c = lane; c < nrhs; c += 32) {
@@ -40,12 +47,12 @@ __device__ __forceinline__ bool warp_chol_solve(const double* L, int s, double* 
         for (int i = 0; i < s; i++) {
             double t = b[i];
             for (int k = 0; k < i; k++) t -= L[i + k * s] * b[k];
-            b[i] = t / L[i + i * s];
+            b[i] = t * rinv[i];
         }
         for (int i = s - 1; i >= 0; i--) {
             double t = b[i];
             for (int k = i + 1; k < s; k++) t -= L[k + i * s] * b[k];
-            b[i] = t / L[i + i * s];
+            b[i] = t * rinv[i];
             ok = ok && isfinite(b[i]);
         }
     }
@@ -53,7 +60,7 @@ __device__ __forceinline__ bool warp_chol_solve(const double* L, int s, double* 
     return __all_sync(0xffffffffu, ok);
 }
 
-// Scratch for the solves: 4 s x s matrices and 2 vectors, for s <= MS, and
+// Scratch for the solves: 4 s x s matrices and 3 vectors, for s <= MS, and
 // shared-memory copies of the inputs the monomial step reads more than once
 // (the moments mu_0..mu_{2s-1} and the previous alpha).
 template <int MS>
@@ -66,13 +73,16 @@ struct SmallScratchT {
     double c[MS];
     double mu[2 * MS];
     double al[MS];
+    double r[MS];  // reciprocals of the Cholesky factor's diagonal
 };
 using SmallScratch = SmallScratchT<kMaxS>;
 
 // Algorithm 6 (SW) for the monomial basis, or its first-step form, by one
 // warp.  Inputs in ctrl: mu[0..2s-1] (vm(k) = mu_{k-1}), and for step > 0
-// the previous W and alpha.  Outputs: W, alpha, beta.  Returns an
-// sscg_status (0 or SSCG_BREAKDOWN).
+// the previous alpha and the Cholesky factor of the previous W (Wl, Wr: each
+// step keeps the factor it formed for its own W, so W_prev is not factored
+// again).  Outputs: W, its factor, alpha, beta.  Returns an sscg_status (0 or
+// SSCG_BREAKDOWN).
 //   step 0:  W(a,b) = mu_{a+b+1}, beta = 0, W alpha = (mu_0..mu_{s-1})
 //   step >0: c_t = -(mu_t + sum_{j<t} c_j alpha_prev(s-1-t+j)) / alpha_prev(s-1)
 //            b1(a,b) = -c_{a+b+1-s} (zero when a+b+1 < s), all a, b
@@ -98,17 +108,18 @@ __device__ inline int warp_sw_monomial(Ctrl* ctrl, int s, int step, SC* sc) {
         }
         if (lane < s) sc->a[lane] = mu[lane];
         __syncwarp();
-        if (!warp_cholesky(sc->L, s)) return 2;
-        if (!warp_chol_solve(sc->L, s, sc->a, 1)) return 2;
+        if (!warp_cholesky(sc->L, s, sc->r)) return 2;
+        if (!warp_chol_solve(sc->L, s, sc->a, 1, sc->r)) return 2;
     } else {
         const double* al = sc->al;
         double as = al[s - 1];
         if (as == 0.0 || !isfinite(as)) return 2;
         if (lane == 0) {
+            const double ias = 1.0 / as;
             for (int t = 0; t < s; t++) {
                 double v = mu[t];
                 for (int j = 0; j < t; j++) v += sc->c[j] * al[s - 1 - t + j];
-                sc->c[t] = -v / as;
+                sc->c[t] = -v * ias;
             }
         }
         __syncwarp();
@@ -118,11 +129,11 @@ __device__ inline int warp_sw_monomial(Ctrl* ctrl, int s, int step, SC* sc) {
             double v = q >= 0 ? -sc->c[q] : 0.0;
             sc->b1[e] = v;
             sc->X[e] = v;
-            sc->L[e] = ctrl->W[e];
+            sc->L[e] = ctrl->Wl[e];  // the factor of W_prev, from the previous step
         }
+        if (lane < s) sc->r[lane] = ctrl->Wr[lane];
         __syncwarp();
-        if (!warp_cholesky(sc->L, s)) return 2;          // W_prev
-        if (!warp_chol_solve(sc->L, s, sc->X, s)) return 2;  // beta = W_prev^-1 b1
+        if (!warp_chol_solve(sc->L, s, sc->X, s, sc->r)) return 2;  // beta = W_prev^-1 b1
         for (int e = lane; e < s * s; e += 32) {
             int a = e % s, b = e / s;
             double t = mu[a + b + 1];
@@ -133,14 +144,18 @@ __device__ inline int warp_sw_monomial(Ctrl* ctrl, int s, int step, SC* sc) {
         for (int e = lane; e < s * s; e += 32) sc->L[e] = sc->Wn[e];
         if (lane < s) sc->a[lane] = mu[lane];
         __syncwarp();
-        if (!warp_cholesky(sc->L, s)) return 2;
-        if (!warp_chol_solve(sc->L, s, sc->a, 1)) return 2;
+        if (!warp_cholesky(sc->L, s, sc->r)) return 2;
+        if (!warp_chol_solve(sc->L, s, sc->a, 1, sc->r)) return 2;
     }
     for (int e = lane; e < s * s; e += 32) {
         ctrl->W[e] = sc->Wn[e];
+        ctrl->Wl[e] = sc->L[e];
         ctrl->beta[e] = sc->X[e];
     }
-    if (lane < s) ctrl->alpha[lane] = sc->a[lane];
+    if (lane < s) {
+        ctrl->Wr[lane] = sc->r[lane];
+        ctrl->alpha[lane] = sc->a[lane];
+    }
     __syncwarp();
     return 0;
 }
@@ -150,7 +165,8 @@ __device__ inline int warp_sw_monomial(Ctrl* ctrl, int s, int step, SC* sc) {
 //   W alpha = m (+ beta^T q when q = P_old^T r was formed: the right-hand
 //   side P^T r of Section II-A for a residual that is not exactly orthogonal
 //   to P_old, as after residual replacement).
-//   G, C (column-major, C(l,j) = (A p_l^old) . u_j), m and q in ctrl.
+//   G, C (column-major, C(l,j) = (A p_l^old) . u_j), m and q in ctrl; for
+//   step > 0 the Cholesky factor of W_prev that the previous step kept (Wl, Wr).
 __device__ inline int warp_sw_gram(Ctrl* ctrl, int s, int step, SmallScratch* sc) {
     const int lane = threadIdx.x & 31;
     if (step == 0) {
@@ -160,12 +176,12 @@ __device__ inline int warp_sw_gram(Ctrl* ctrl, int s, int step, SmallScratch* sc
         }
     } else {
         for (int e = lane; e < s * s; e += 32) {
-            sc->L[e] = ctrl->W[e];
+            sc->L[e] = ctrl->Wl[e];  // the factor of W_prev, from the previous step
             sc->X[e] = -ctrl->C[e];
         }
+        if (lane < s) sc->r[lane] = ctrl->Wr[lane];
         __syncwarp();
-        if (!warp_cholesky(sc->L, s)) return 2;
-        if (!warp_chol_solve(sc->L, s, sc->X, s)) return 2;
+        if (!warp_chol_solve(sc->L, s, sc->X, s, sc->r)) return 2;
         for (int e = lane; e < s * s; e += 32) {
             int i = e % s, j = e / s;
             double t = ctrl->G[e];
@@ -182,13 +198,17 @@ __device__ inline int warp_sw_gram(Ctrl* ctrl, int s, int step, SmallScratch* sc
         sc->a[lane] = mi;
     }
     __syncwarp();
-    if (!warp_cholesky(sc->L, s)) return 2;
-    if (!warp_chol_solve(sc->L, s, sc->a, 1)) return 2;
+    if (!warp_cholesky(sc->L, s, sc->r)) return 2;
+    if (!warp_chol_solve(sc->L, s, sc->a, 1, sc->r)) return 2;
     for (int e = lane; e < s * s; e += 32) {
         ctrl->W[e] = sc->Wn[e];
+        ctrl->Wl[e] = sc->L[e];
         ctrl->beta[e] = sc->X[e];
     }
-    if (lane < s) ctrl->alpha[lane] = sc->a[lane];
+    if (lane < s) {
+        ctrl->Wr[lane] = sc->r[lane];
+        ctrl->alpha[lane] = sc->a[lane];
+    }
     __syncwarp();
     return 0;
 }
