@@ -119,8 +119,8 @@ L2_BYTES = 129 * 10 ** 6  # the GB300's L2
 L2_FLUSH_BYTES = 256 << 20
 
 NCU_TRAFFIC_PER_ROW = {
-    "f64": {"mpk": 53.79e6 / 4.096e6, "update": 734.1e6 / 4.096e6},
-    "f64-fixed": {"update": 733.196e6 / 4.096e6},
+    "f64": {"mpk": 53.86e6 / 4.096e6, "update": 734.1e6 / 4.096e6},
+    "f64-fixed": {"update": 733.296e6 / 4.096e6},
     "df64": {"mpk": 54.0e6 / 4.096e6, "update": 732.694e6 / 4.096e6},
 }
 
