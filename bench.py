@@ -1092,6 +1092,8 @@ def run_peaks(a, world, rank, local, pg):
     rates["dfma_dmma"] = {"ops_per_s": best[0], "ms": round(best[1], 3), "iters": [itf, itm],
                           "time_vs_solo": round(best[1] / t_f, 3)}
     clk = clocks.stop()
+    # latency of the on-chip s x s solves (one warp, SM cycles), s = 2, 4, 8
+    small = {str(s): {k: round(v, 1) for k, v in ctx.probe_small_solve(s, 200).items()} for s in (2, 4, 8)}
     if rank == 0:
         mhz = (clk or {}).get("sm_mhz") or 2070.0
         per = {k: round(v["ops_per_s"] / (sm * mhz * 1e6), 3) for k, v in rates.items()}
@@ -1103,6 +1105,7 @@ def run_peaks(a, world, rank, local, pg):
                 "rates_gops": {k: round(v["ops_per_s"] / 1e9, 2) for k, v in rates.items()},
                 "per_sm_per_clock": per, "sm_count": sm, "detail": rates,
                 "fp64_nominal_derived_gops_at_max_clock": round(fp64_alu_peak(sm, 2070.0) / 1e9, 1),
+                "small_solve_cycles": small,
                 "clocks": clk}
         print(json.dumps(line), flush=True)
     barrier(pg)

@@ -49,6 +49,19 @@ typedef struct sscg_ctx sscg_ctx;
  * or above 2^40, null outputs), SSCG_ERR_CUDA. */
 int sscg_probe_rate(sscg_ctx* ctx, int kind, int64_t iters_a, int64_t iters_b, double* ops_per_s, double* ms);
 
+/* Latency of the on-chip s x s solves of Algorithm 6 (the serial tail of
+ * each outer step, run by one warp of the last CTA): one warp times, with the
+ * SM's cycle counter, the library's own routines on an s x s SPD matrix and
+ * on the moments of a positive 16-point measure, each `reps` times, and
+ * reports mean cycles in cycles[0..3]: the Cholesky factorisation, the
+ * triangular solves with 1 and with s right-hand sides, and the monomial
+ * step's first-step form (factorisation and one solve of the moment matrix).
+ * Uses the library's static device storage, no caller memory; synchronises
+ * the context's stream.  Errors: SSCG_ERR_INVALID (s outside 1..8, reps
+ * outside 1..100000, null output), SSCG_BREAKDOWN (a factorisation
+ * failed, which the fixed inputs do not cause), SSCG_ERR_CUDA. */
+int sscg_probe_small_solve(sscg_ctx* ctx, int s, int reps, double* cycles);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 // work.
 #include "../../include/sscg_probe.h"
 #include "internal.h"
+#include "small.cuh"
 
 namespace {
 
@@ -252,4 +253,78 @@ extern "C" int sscg_probe_rate(sscg_ctx* ctx, int kind, int64_t iters_a, int64_t
         case SSCG_PROBE_F2I64: return run_probe<SSCG_PROBE_F2I64>(ctx, iters_a, iters_b, ops_per_s, ms);
         default: return sscg::set_err(ctx, SSCG_ERR_INVALID, "unknown probe kind %d", kind);
     }
+}
+
+namespace {
+
+using sscg::Ctrl;
+using sscg::SmallScratch;
+
+__device__ Ctrl g_probe_ctrl;               // moments for the monomial step
+__device__ long long g_probe_cycles[5];     // sums of cycles; [4]: failed factorisations
+
+// One warp: the small-solve routines on fixed inputs, timed with clock64.
+__global__ void __launch_bounds__(32) k_probe_small(int s, int reps) {
+    __shared__ SmallScratch sc;
+    __shared__ double A0[64], L[64], X[64], b[8], rv[8];
+    const int lane = threadIdx.x;
+    // A0 = diag(2 + i) + 0.1 (all ones): SPD
+    for (int e = lane; e < s * s; e += 32) A0[e] = (e % s == e / s ? 2.0 + e % s : 0.0) + 0.1;
+    // mu_k = sum_m w_m lam_m^k over 16 points lam_m in (0, 2): Hankel matrices SPD for s <= 8
+    if (lane < 2 * s) {
+        double mu = 0.0;
+        for (int m = 0; m < 16; m++) {
+            const double lam = 0.0625 + 0.118 * m, w = 1.0 + 0.05 * m;
+            double p = w;
+            for (int q = 0; q < lane; q++) p *= lam;
+            mu += p;
+        }
+        g_probe_ctrl.mu[lane] = mu;
+    }
+    __syncwarp();
+    long long c[4] = {0, 0, 0, 0};
+    long long fails = 0;
+    for (int r = 0; r < reps; r++) {
+        for (int e = lane; e < s * s; e += 32) {
+            L[e] = A0[e];
+            X[e] = e % s == e / s ? 1.0 : 0.0;
+        }
+        if (lane < s) b[lane] = 1.0 + lane;
+        __syncwarp();
+        const long long t0 = clock64();
+        bool ok = sscg::warp_cholesky(L, s, rv);
+        const long long t1 = clock64();
+        ok = sscg::warp_chol_solve(L, s, b, 1, rv) && ok;
+        const long long t2 = clock64();
+        ok = sscg::warp_chol_solve(L, s, X, s, rv) && ok;
+        const long long t3 = clock64();
+        const int st = sscg::warp_sw_monomial(&g_probe_ctrl, s, 0, &sc);
+        const long long t4 = clock64();
+        c[0] += t1 - t0;
+        c[1] += t2 - t1;
+        c[2] += t3 - t2;
+        c[3] += t4 - t3;
+        if (!ok || st != 0) fails++;
+    }
+    if (lane == 0) {
+        for (int k = 0; k < 4; k++) g_probe_cycles[k] = c[k];
+        g_probe_cycles[4] = fails;
+    }
+}
+
+}  // namespace
+
+extern "C" int sscg_probe_small_solve(sscg_ctx* ctx, int s, int reps, double* cycles) {
+    if (!ctx) return SSCG_ERR_INVALID;
+    if (!cycles) return sscg::set_err(ctx, SSCG_ERR_INVALID, "null output");
+    if (s < 1 || s > 8 || reps < 1 || reps > 100000)
+        return sscg::set_err(ctx, SSCG_ERR_INVALID, "s must lie in 1..8 and reps in 1..100000");
+    k_probe_small<<<1, 32, 0, ctx->stream>>>(s, reps);
+    SSCG_CUDA(ctx, cudaGetLastError());
+    long long h[5];
+    SSCG_CUDA(ctx, cudaMemcpyFromSymbolAsync(h, g_probe_cycles, sizeof(h), 0, cudaMemcpyDeviceToHost, ctx->stream));
+    SSCG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (h[4] != 0) return sscg::set_err(ctx, SSCG_BREAKDOWN, "a probe factorisation failed");
+    for (int k = 0; k < 4; k++) cycles[k] = (double)h[k] / reps;
+    return SSCG_OK;
 }

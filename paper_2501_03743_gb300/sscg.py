@@ -37,7 +37,7 @@ EXPORTS = (
     "sscg_bounds_mlp", "sscg_set_bounds_model", "sscg_batch_workspace_bytes", "sscg_batch_create",
     "sscg_batch_destroy", "sscg_batch_solve", "sscg_batch_props", "sscg_batch_launches",
     "sscg_probe_rate", "sscg_batch_inject_barrier_fault", "sscg_pfcg_workspace_bytes", "sscg_pfcg_solve",
-    "sscg_newton_shifts",
+    "sscg_newton_shifts", "sscg_probe_small_solve",
 )
 # Probe kinds of include/sscg_probe.h.
 PROBE = {"dfma": 0, "dadd": 1, "dmul": 2, "dmma": 3, "dfma_dmma": 4, "ffma": 5, "ialu": 6, "imad": 7, "imad_wide": 8, "i2f64": 9,
@@ -133,6 +133,7 @@ def load(path: str | None = None):
     L.sscg_batch_props.argtypes = [vp, vp, P(i32), P(i32), P(C.c_float)]
     L.sscg_batch_launches.argtypes = [vp, P(C.c_int64)]
     L.sscg_probe_rate.argtypes = [vp, i32, i64, i64, P(dbl), P(dbl)]
+    L.sscg_probe_small_solve.argtypes = [vp, i32, i32, P(dbl)]
     L.sscg_batch_inject_barrier_fault.argtypes = [vp, i32, i32]
     L.sscg_newton_shifts.argtypes = [i32, dbl, dbl, vp, P(dbl)]
     _lib = L
@@ -201,6 +202,14 @@ class Context:
         self.check(self.lib.sscg_probe_rate(self.h, PROBE[kind], int(iters_a), int(iters_b), C.byref(ops),
                                             C.byref(ms)))
         return ops.value, ms.value
+
+    def probe_small_solve(self, s, reps=100):
+        """Latency probe of include/sscg_probe.h: mean SM cycles of the s x s
+        Cholesky, the solves with 1 and with s right-hand sides, and the
+        monomial step's first-step form."""
+        out = (C.c_double * 4)()
+        self.check(self.lib.sscg_probe_small_solve(self.h, int(s), int(reps), out))
+        return dict(cholesky=out[0], solve_1=out[1], solve_s=out[2], monomial_step0=out[3])
 
     def check(self, rc, allow_positive=False):
         if rc < 0 or (rc > 0 and not allow_positive):
