@@ -246,7 +246,7 @@ struct BK {
     // their gathers are contiguous.  RO: v was written by an earlier launch
     // (read-only path); otherwise through L2.  soff/scf: the diagonal form's
     // offsets and values in shared memory.
-    template <bool RO, bool LAP = true>
+    template <bool RO, bool LAP = true, bool LAP27 = false>
     static __device__ __forceinline__ Rv spmv_elem(const BReg& y, const int* soff, const float* scf, int i, int r,
                                                    const S* v) {
         const int R = y.R;
@@ -302,6 +302,18 @@ struct BK {
                         };
                         const double Sn = lap_neighbour_sum<7>(m, ld);
                         return ::fma((double)scf[3], ld(3), (double)y.dco * Sn);
+                    }
+                    // FP64 27-point Laplacian class: the 26 neighbours in fixed point
+                    // (only in the level kernel of kind 3, built for 128 registers)
+                    if constexpr (LAP27) {
+                        if (y.dlap && y.dk == 27 && y.dcen == 13) {
+                            auto ld = [&](int t) {
+                                const S* px = v + (size_t)(i + soff[t]) * R + r;
+                                return RO ? A::ldg(px) : A::ldcg(px);
+                            };
+                            const double Sn = lap_neighbour_sum<27>(m, ld);
+                            return ::fma((double)scf[13], ld(13), (double)y.dco * Sn);
+                        }
                     }
                 }
                 for (int t = 0; t < y.dk; t++) {
@@ -424,9 +436,10 @@ __device__ void ph_init(const BArgs& a, int it0, int itstep) {
 // Level j of every active system (RO: u_j was written by an earlier launch,
 // so the gathers may use the read-only path; inside one cooperative launch
 // they go through L2).
-// KIND: 0 every system; 1 CSR systems only; 2 diagonal-form systems only (the
-// per-phase mode launches the two separately, so each keeps its own register
-// budget).
+// KIND: 0 every system; 1 CSR systems only; 2 diagonal-form systems only; 3
+// FP64 27-point Laplacian-class diagonal-form systems only, which kind 2 then
+// skips (the per-phase mode launches the kinds separately, so each keeps its
+// own register budget: kind 3's fixed-point sum of 26 neighbours holds 128).
 template <class A, bool RO, int KIND = 0>
 __device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
     using K = BK<A>;
@@ -441,7 +454,9 @@ __device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
         const BSys& y = a.sys[k];
         const int state = __ldcg(&a.bctl[k].state);
         if (state == SYS_FINISHED || (state == SYS_EXPORT && (j > 0 || a.tuning))) continue;
-        if ((KIND == 1 && y.dk) || (KIND == 2 && !y.dk)) continue;  // the other kernel's system
+        // the other kernels' systems (kind 3: FP64 27-point Laplacian-class diagonal form)
+        const bool lap27 = A::kind == 0 && y.dk == 27 && y.dlap && y.dcen == 13;
+        if ((KIND == 1 && y.dk) || (KIND == 2 && (!y.dk || lap27)) || (KIND == 3 && !lap27)) continue;
         ITEM_MAP(y);
         const int li = it - y.item0;
         const int r0 = li * y.T, r1 = min(y.n, r0 + y.T);
@@ -501,12 +516,12 @@ __device__ void ph_level(const BArgs& a, int j, int it0, int itstep) {
                 if constexpr (KIND == 1) {
                     epi(i, K::template spmv_elem<RO, false>(yb, s_doff, s_dcf, i, r, uj));
                 } else {
-                    const Rv av = K::template spmv_elem<RO, true>(yb, s_doff, s_dcf, i, r, uj);
+                    const Rv av = K::template spmv_elem<RO, true, KIND == 3>(yb, s_doff, s_dcf, i, r, uj);
                     if (yb.dk) epi_dia(i, av);
                     else epi(i, av);
                 }
             }
-        } else if constexpr (KIND != 2) {
+        } else if constexpr (KIND != 2 && KIND != 3) {
             // CSR: stage each 256-row sub-tile's row pointers, column indices
             // and values in shared memory with coalesced loads; the R threads
             // of a row then read them from there
@@ -870,6 +885,13 @@ __global__ void __launch_bounds__(kBThreads) k_bp_level(BArgs a, int j) {
     ph_level<A, true, KIND>(a, j, blockIdx.x, gridDim.x);
 }
 
+// Kind 3 (FP64 27-point Laplacian-class systems), built for 2 CTAs per SM.
+template <class A>
+__global__ void __launch_bounds__(kBThreads, 2) k_bp_level27(BArgs a, int j) {
+    if (batch_done(a)) return;
+    ph_level<A, true, 3>(a, j, blockIdx.x, gridDim.x);
+}
+
 template <class A>
 __global__ void __launch_bounds__(kBThreads) k_bp_solve(BArgs a) {
     if (batch_done(a)) return;
@@ -902,8 +924,9 @@ struct sscg_batch {
     int nsys, s, arith, maxit, total_rhs, nitems, grid, graph_ok;
     int persistent;              // one cooperative launch instead of per-phase launches
     int fma_update;              // SSCG_FMA_UPDATE
-    int g_init, g_level, g_level_dia, g_update;  // per-phase grids (CSR and diagonal-form levels)
-    int has_csr, has_dia;                        // which level kernels an outer step launches
+    int g_init, g_level, g_level_dia, g_level_dia27, g_update;  // per-phase grids (CSR, diagonal-form,
+                                                                 // FP64 27-point diagonal-form levels)
+    int has_csr, has_dia, has_dia27;                            // which level kernels an outer step launches
     cudaGraphExec_t step_exec;   // per-phase mode: one outer step
     double tol;
     std::vector<const sscg_mat*> mats;
@@ -1076,6 +1099,7 @@ int launch_step(sscg_batch* b, int tuning, int maxit, cudaStream_t st) {
     for (int j = 0; j < b->s; j++) {
         if (b->has_csr) k_bp_level<A, 1><<<b->g_level, kBThreads, kLevelSmem, st>>>(a, j);
         if (b->has_dia) k_bp_level<A, 2><<<b->g_level_dia, kBThreads, kLevelSmem, st>>>(a, j);
+        if (b->has_dia27) k_bp_level27<A><<<b->g_level_dia27, kBThreads, kLevelSmem, st>>>(a, j);
     }
     k_bp_solve<A><<<std::min(b->nsys, kMaxGrid), kBThreads, 0, st>>>(a);
     k_bp_update<A, SB><<<b->g_update, kBThreads, 0, st>>>(a);
@@ -1123,6 +1147,7 @@ int phase_grids(sscg_batch* b) {
     };
     b->g_level = level_grid(k_bp_level<A, 1>);
     b->g_level_dia = level_grid(k_bp_level<A, 2>);
+    b->g_level_dia27 = level_grid(k_bp_level27<A>);
     b->g_update = grid_of(k_bp_update<A, SB>);
     int per = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<A, SB>, kBThreads, 0);
@@ -1296,7 +1321,7 @@ int run_phases(sscg_batch* b) {
         }
         if (rc) break;
         launched += c;
-        b->last_launches += (int64_t)c * (b->s * (b->has_csr + b->has_dia) + 2);  // levels, solves, update
+        b->last_launches += (int64_t)c * (b->s * (b->has_csr + b->has_dia + b->has_dia27) + 2);  // levels, solves, update
         int fin = 0;
         cudaError_t pe = cudaSuccess;
         const bool got = poll.step(ctx->pinned, &b->d_g->finished, st, &fin, &pe);
@@ -1360,7 +1385,8 @@ int sscg_batch_create(sscg_ctx* ctx, int nsys, const sscg_mat* const* mats, cons
         const bool f64 = opts->arith == SSCG_ARITH_F64;
         if (m->dia) {
             // constant-coefficient diagonal form: masks, offsets, values; D is one constant
-            b->has_dia = 1;
+            if (f64 && m->dia_k == 27 && m->dia_lap && m->dia_cen == 13) b->has_dia27 = 1;
+            else b->has_dia = 1;
             y.dmask = m->dia_mask;
             y.dk = m->dia_k;
             y.dcen = m->dia_cen;
